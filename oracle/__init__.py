@@ -1,0 +1,273 @@
+"""Plain FP64 CPU oracle for the HiRep v2 Wilson-Dirac hot path (arXiv 2503.06721).
+
+TEST INFRASTRUCTURE ONLY.  The arithmetic lives in ``hr_oracle.c`` (plain C,
+FP64, one loop per definition of the paper); this module only compiles it and
+marshals numpy arrays through ctypes.  Only the test suite, the smoke check and
+the benchmark's CPU-baseline leg may import it.  It shares no code with the GPU
+library and never imports it.
+
+Layouts (numpy complex128 unless stated):
+    gauge links U[V, 4, N, N]           lexicographic site, direction mu, row, col
+    represented links UR[V, 4, D, D]    same, in representation R (boundary signs applied)
+    spinors psi[V, 4, D]                lexicographic site, spin, colour
+    half (parity) fields [V/2, 4, D]    index lex // 2 inside the parity
+    force F[V, 4, N*N-1]                float64 Lie-algebra components
+
+Every function below has a "pinned" status recorded in the tests: see
+``tests/test_oracle_*.py`` for the closed forms, invariants and brute-force
+checks that each one is held against.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "hr_oracle.c"
+_HDR = _HERE / "hr_oracle.h"
+_LIBDIR = _HERE / "_build"
+_LIB = _LIBDIR / "liboracle.so"
+
+FUND, ADJ, SYM, ASYM = 0, 1, 2, 3
+REP_NAMES = {"FUND": FUND, "ADJ": ADJ, "SYM": SYM, "ASYM": ASYM, "2AS": ASYM}
+
+
+def build(force: bool = False) -> Path:
+    """Compile hr_oracle.c into oracle/_build/liboracle.so (gcc, -O2, OpenMP)."""
+    _LIBDIR.mkdir(exist_ok=True)
+    stamp = max(_SRC.stat().st_mtime, _HDR.stat().st_mtime)
+    if force or not _LIB.exists() or _LIB.stat().st_mtime < stamp:
+        tmp = _LIBDIR / f"liboracle.{os.getpid()}.so"
+        cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-fPIC", "-shared",
+               "-o", str(tmp), str(_SRC), "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Lat(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("rep", ctypes.c_int),
+                ("dims", ctypes.c_int * 4), ("bc", ctypes.c_int * 4),
+                ("m0", ctypes.c_double)]
+
+
+def lat(N: int, rep, dims, bc=(-1, 1, 1, 1), m0: float = 0.0) -> Lat:
+    """Lattice descriptor.  dims = (T, X, Y, Z); bc[mu] = +1 / -1."""
+    if isinstance(rep, str):
+        rep = REP_NAMES[rep]
+    L = Lat()
+    L.N, L.rep, L.m0 = int(N), int(rep), float(m0)
+    for i in range(4):
+        L.dims[i] = int(dims[i])
+        L.bc[i] = int(bc[i])
+    return L
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(str(build()))
+        P = ctypes.c_void_p
+        I = ctypes.c_int
+        D = ctypes.c_double
+        LP = ctypes.POINTER(Lat)
+        sig = {
+            "or_rep_dim": (I, [I, I]),
+            "or_gamma": (None, [I, P]),
+            "or_generators": (None, [I, P]),
+            "or_rep_basis": (I, [I, I, P]),
+            "or_represent_link": (I, [I, I, P, P]),
+            "or_rep_generators": (None, [I, I, P]),
+            "or_represent_field": (None, [LP, P, P]),
+            "or_dirac_full": (None, [LP, P, P, P, I]),
+            "or_hop_parity": (None, [LP, P, I, P, P, I]),
+            "or_dhat": (None, [LP, P, P, P, I]),
+            "or_sum_naive": (D, [P, ctypes.c_long]),
+            "or_sum_neumaier": (D, [P, ctypes.c_long]),
+            "or_sum_neumaier2": (D, [P, ctypes.c_long]),
+            "or_sum_double_double": (D, [P, ctypes.c_long]),
+            "or_norm2": (D, [P, ctypes.c_long]),
+            "or_cg": (I, [LP, P, I, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]),
+            "or_force": (None, [LP, P, P, P, P]),
+            "or_num_threads": (I, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _c(a, dtype=np.complex128):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def rep_dim(N: int, rep) -> int:
+    rep = REP_NAMES.get(rep, rep) if isinstance(rep, str) else rep
+    return _load().or_rep_dim(N, rep)
+
+
+def num_threads() -> int:
+    return _load().or_num_threads()
+
+
+def gamma(mu: int) -> np.ndarray:
+    g = np.zeros((4, 4), np.complex128)
+    _load().or_gamma(mu, _p(g))
+    return g
+
+
+def generators(N: int) -> np.ndarray:
+    T = np.zeros((N * N - 1, N, N), np.complex128)
+    _load().or_generators(N, _p(T))
+    return T
+
+
+def rep_basis(N: int, rep) -> np.ndarray:
+    rep = REP_NAMES.get(rep, rep) if isinstance(rep, str) else rep
+    D = rep_dim(N, rep)
+    E = np.zeros((max(D, 1), N, N), np.complex128)
+    n = _load().or_rep_basis(N, rep, _p(E))
+    return E[:n]
+
+
+def represent_link(N: int, rep, U) -> np.ndarray:
+    rep = REP_NAMES.get(rep, rep) if isinstance(rep, str) else rep
+    D = rep_dim(N, rep)
+    U = _c(U)
+    R = np.zeros((D, D), np.complex128)
+    _load().or_represent_link(N, rep, _p(U), _p(R))
+    return R
+
+
+def rep_generators(N: int, rep) -> np.ndarray:
+    rep = REP_NAMES.get(rep, rep) if isinstance(rep, str) else rep
+    D = rep_dim(N, rep)
+    TR = np.zeros((N * N - 1, D, D), np.complex128)
+    _load().or_rep_generators(N, rep, _p(TR))
+    return TR
+
+
+def volume(L: Lat) -> int:
+    return L.dims[0] * L.dims[1] * L.dims[2] * L.dims[3]
+
+
+def represent_field(L: Lat, UF) -> np.ndarray:
+    D = rep_dim(L.N, L.rep)
+    UF = _c(UF)
+    assert UF.size == volume(L) * 4 * L.N * L.N
+    UR = np.zeros((volume(L), 4, D, D), np.complex128)
+    _load().or_represent_field(ctypes.byref(L), _p(UF), _p(UR))
+    return UR
+
+
+def dirac_full(L: Lat, UR, psi, dagger: bool = False) -> np.ndarray:
+    UR, psi = _c(UR), _c(psi)
+    out = np.zeros_like(psi)
+    _load().or_dirac_full(ctypes.byref(L), _p(UR), _p(psi), _p(out), int(dagger))
+    return out
+
+
+def hop_parity(L: Lat, UR, out_parity: int, in_half, dagger: bool = False) -> np.ndarray:
+    """D_{p,1-p} in_half: the hopping block of D_m from parity 1-p to parity p."""
+    UR, in_half = _c(UR), _c(in_half)
+    out = np.zeros_like(in_half)
+    _load().or_hop_parity(ctypes.byref(L), _p(UR), int(out_parity), _p(in_half), _p(out),
+                          int(dagger))
+    return out
+
+
+def dhat(L: Lat, UR, in_e, dagger: bool = False) -> np.ndarray:
+    UR, in_e = _c(UR), _c(in_e)
+    out = np.zeros_like(in_e)
+    _load().or_dhat(ctypes.byref(L), _p(UR), _p(in_e), _p(out), int(dagger))
+    return out
+
+
+def _sum(name, a) -> float:
+    a = _c(a, np.float64)
+    return getattr(_load(), name)(_p(a), a.size)
+
+
+def sum_naive(a):
+    return _sum("or_sum_naive", a)
+
+
+def sum_neumaier(a):
+    return _sum("or_sum_neumaier", a)
+
+
+def sum_neumaier2(a):
+    return _sum("or_sum_neumaier2", a)
+
+
+def sum_double_double(a):
+    return _sum("or_sum_double_double", a)
+
+
+def norm2(a) -> float:
+    a = _c(a)
+    return _load().or_norm2(_p(a), a.size)
+
+
+def cg(L: Lat, UR, sys: int, b, x0=None, tol: float = 1e-10, max_iter: int = 10000):
+    """CG on A x = b with A = D^dag D (sys 0, full fields) or Dhat^dag Dhat (sys 1,
+    even half fields).  Returns (x, converged, iterations, true relative residual)."""
+    UR, b = _c(UR), _c(b)
+    x = np.zeros_like(b) if x0 is None else _c(x0).copy()
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    rc = _load().or_cg(ctypes.byref(L), _p(UR), int(sys), _p(b), _p(x), float(tol),
+                       int(max_iter), ctypes.byref(it), ctypes.byref(rr))
+    return x, rc == 0, it.value, rr.value
+
+
+def force(L: Lat, UR, X, Y) -> np.ndarray:
+    """d/de of S = -2 Re <Y, D_m X> along exp(i e T^a) U_F(x, mu); F[V, 4, N*N-1]."""
+    UR, X, Y = _c(UR), _c(X), _c(Y)
+    F = np.zeros((volume(L), 4, L.N * L.N - 1), np.float64)
+    _load().or_force(ctypes.byref(L), _p(UR), _p(X), _p(Y), _p(F))
+    return F
+
+
+# ---- parity helpers (pure index bookkeeping) ----
+
+def parity_of_sites(L: Lat) -> np.ndarray:
+    T, X, Y, Z = (L.dims[i] for i in range(4))
+    t, x, y, z = np.meshgrid(np.arange(T), np.arange(X), np.arange(Y), np.arange(Z),
+                             indexing="ij")
+    return ((t + x + y + z) & 1).reshape(-1)
+
+
+def split(L: Lat, full):
+    """Full lexicographic field -> (even half, odd half), half index lex // 2."""
+    par = parity_of_sites(L)
+    lex = np.arange(volume(L))
+    full = np.asarray(full)
+    e = np.zeros((volume(L) // 2,) + full.shape[1:], full.dtype)
+    o = np.zeros_like(e)
+    e[lex[par == 0] // 2] = full[par == 0]
+    o[lex[par == 1] // 2] = full[par == 1]
+    return e, o
+
+
+def merge(L: Lat, even, odd):
+    par = parity_of_sites(L)
+    lex = np.arange(volume(L))
+    even = np.asarray(even)
+    full = np.zeros((volume(L),) + even.shape[1:], even.dtype)
+    full[par == 0] = even[lex[par == 0] // 2]
+    full[par == 1] = np.asarray(odd)[lex[par == 1] // 2]
+    return full
