@@ -1,0 +1,232 @@
+/*
+ * hr.h -- C ABI of the GB300 (sm_103a) Wilson-Dirac library for fermions in
+ * higher representations of SU(N): the hot path of HiRep v2
+ * (arXiv 2503.06721).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Lattice (Sec. 2.1): dims = {T, X, Y, Z}, mu = 0 is time; every extent even
+ * and >= 2.  Lexicographic site index lex = ((t*X + x)*Y + y)*Z + z.
+ * Even sites have (t+x+y+z) mod 2 == 0 (Sec. 4.3.3).  A parity ("half")
+ * field over V/2 sites is indexed by lex/2 inside its parity.  A FULL field
+ * is the even half followed by the odd half (even sites indexed first, as in
+ * Sec. 3.4.1).
+ *
+ * Spinor fields (Sec. 3.1.2, Table "elementary data types"):
+ *   HR_F64 / HR_F32: [nrhs][nsites][spin 0..3][colour 0..D_R-1] interleaved
+ *     complex (re, im) in double / float.
+ *   HR_F16 / HR_BF16 (reduced storage with one scale per site):
+ *     each right-hand side is a block of hr_field_bytes(..., 1) bytes holding
+ *     [nsites][4][D_R] pairs (re, im) of half / bfloat16 values v/s_x,
+ *     followed, at the next 256-byte boundary, by [nsites] float scales s_x
+ *     (the largest |component| of site x).  The value is  s_x * stored.
+ * Gauge field input (Sec. 3.1.3): U_F[lex][mu][row][col] complex double
+ *   (SU(N) links in the positive directions), device memory.
+ * Force output: F[lex][mu][a] double, a = 0..N*N-2 in the generator order
+ *   of hr_generators() (generalised Gell-Mann matrices / 2).
+ *
+ * Memory and errors: all field pointers are DEVICE pointers owned by the
+ * caller; the library never frees them.  hr_represent_gauge allocates the
+ * internal link storage (freed by hr_gauge_destroy) and each hr_gauge holds
+ * a lazily grown solver workspace.  Every call returns an hr_status and never
+ * exits or throws; hr_last_error() gives a thread-local message for the last
+ * failure.  Calls are asynchronous on the given CUDA stream (a cudaStream_t
+ * passed as void*, NULL = legacy default stream) except where stated.
+ */
+#ifndef HR_H
+#define HR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Supported representations, Table 1 (Sec. 2.3). HR_ASYM is "2AS". */
+typedef enum { HR_FUND = 0, HR_ADJ = 1, HR_SYM = 2, HR_ASYM = 3 } hr_rep;
+
+/* Storage precision of fields and links.  F64 computes in double, the others
+ * in float.  F16/BF16 spinors carry one float scale per site. */
+typedef enum { HR_F64 = 0, HR_F32 = 1, HR_F16 = 2, HR_BF16 = 3 } hr_prec;
+
+/* Output parity / operator selector (Sec. 4.3.3, Eq. dmeo and Eq. deo):
+ *   HR_EVEN        out_e = D_eo in_o   (hopping block, includes the -1/2)
+ *   HR_ODD         out_o = D_oe in_e
+ *   HR_FULL        out   = D_m in      on FULL fields
+ *   HR_EO_PRECOND  out_e = Dhat in_e,  Dhat = (4+m)^2 - D_eo D_oe          */
+typedef enum { HR_EVEN = 0, HR_ODD = 1, HR_FULL = 2, HR_EO_PRECOND = 3 } hr_parity;
+
+typedef enum {
+    HR_OK = 0,
+    HR_ERR_INVALID = -1,        /* bad argument (message in hr_last_error) */
+    HR_ERR_CUDA = -2,           /* a CUDA runtime call failed */
+    HR_ERR_NOMEM = -3,          /* device allocation failed */
+    HR_ERR_NOT_CONVERGED = -4,  /* solver hit max_iter above tolerance */
+    HR_ERR_NONFINITE = -5,      /* NaN/Inf met in a reduction */
+    HR_ERR_TIMEOUT = -6,        /* a bounded device-side wait gave up */
+    HR_ERR_UNSUPPORTED = -7     /* combination not compiled in */
+} hr_status;
+
+/* How the operator kernels obtain U_R (Sec. 3.1.3, represented field):
+ *   HR_LINKS_STORED   read the D_R x D_R represented links kept in HBM
+ *   HR_LINKS_REBUILD  read the N x N fundamental links and rebuild the action
+ *                     of U_R inside the kernel (fewer bytes, more flops) */
+typedef enum { HR_LINKS_STORED = 0, HR_LINKS_REBUILD = 1 } hr_link_mode;
+
+typedef struct {
+    int N;          /* SU(N), 2 <= N <= 4 */
+    hr_rep rep;
+    int dims[4];    /* T, X, Y, Z (all even) */
+    int bc[4];      /* +1 periodic, -1 antiperiodic fermion boundary (Sec. 5.3.1) */
+    double m0;      /* bare mass m of D_m = D + m (Eq. D_m^R) */
+} hr_lattice_desc;
+
+typedef struct hr_gauge hr_gauge;   /* opaque: represented (and/or fund) links */
+
+/* ------------------------------------------------------------------ */
+/* Representation of the gauge field (Sec. 2.3 Eq. U^R = exp(i w T_R),   */
+/* Sec. 3.1.3; boundary signs Sec. 5.3.1)                                */
+/* ------------------------------------------------------------------ */
+/* Builds U_R(x,mu) = R(U_F(x,mu)) for every link and applies the fermion
+ * boundary condition as a -1 on the represented links of the last slice
+ * (x_mu = L_mu - 1) of every antiperiodic direction.
+ *   lat        lattice; copied into the handle.
+ *   U_fund     device, complex double [V][4][N][N]; read only, not retained.
+ *   prec_mask  OR of (1u << hr_prec) for every precision the operator will
+ *              be applied in; links are stored once per precision.
+ *   link_modes OR of (1u << hr_link_mode): STORED keeps D_R x D_R links,
+ *              REBUILD keeps the N x N fundamental links for in-kernel
+ *              rebuilding.  Both may be set (hr_gauge_set_link_mode picks).
+ *   out        receives the new handle (NULL on failure).
+ * Errors: HR_ERR_INVALID (bad N/rep/dims/mask), HR_ERR_NOMEM, HR_ERR_CUDA.
+ * The links are ready once the work queued on `stream` completes. */
+hr_status hr_represent_gauge(const hr_lattice_desc *lat, const void *U_fund,
+                             unsigned prec_mask, unsigned link_modes,
+                             void *stream, hr_gauge **out);
+
+/* Re-represents a new U_F into the existing storage of g (after a gauge
+ * update, Sec. 5.3.1: "only necessary after every gauge update"). */
+hr_status hr_gauge_update(hr_gauge *g, const void *U_fund, void *stream);
+
+/* Chooses STORED or REBUILD links for later operator calls on g.
+ * HR_ERR_INVALID if that storage was not requested at creation. */
+hr_status hr_gauge_set_link_mode(hr_gauge *g, hr_link_mode mode);
+
+/* Frees the link storage and solver workspace (synchronises the device). */
+hr_status hr_gauge_destroy(hr_gauge *g);
+
+/* ------------------------------------------------------------------ */
+/* Field helpers                                                         */
+/* ------------------------------------------------------------------ */
+/* Bytes of a field of nrhs right-hand sides over the sites selected by par
+ * (V/2 for EVEN/ODD/EO_PRECOND, V for FULL) in precision prec. */
+size_t hr_field_bytes(const hr_lattice_desc *lat, hr_parity par, hr_prec prec,
+                      int nrhs);
+
+/* Converts a field between precisions (F64/F32 <-> F16/BF16 computes the
+ * per-site scales).  src and dst must not overlap. */
+hr_status hr_field_convert(const hr_lattice_desc *lat, hr_parity par,
+                           hr_prec src_prec, const void *src,
+                           hr_prec dst_prec, void *dst, int nrhs, void *stream);
+
+/* <a, b> = sum conj(a_i) b_i over each right-hand side, accumulated with
+ * compensated (double-double) sums (Sec. 4.1.1).  out is a HOST array of
+ * 2*nrhs doubles (re, im); the call synchronises the stream. */
+hr_status hr_field_dot(const hr_lattice_desc *lat, hr_parity par, hr_prec prec,
+                       const void *a, const void *b, int nrhs, double *out,
+                       void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Wilson-Dirac operator (Eq. D_m^R in Sec. 2.3; Sec. 4.3.3)              */
+/* ------------------------------------------------------------------ */
+/* D_m psi(x) = (4+m) psi(x) - 1/2 sum_mu [(1 - g_mu) U_R(x,mu) psi(x+mu)
+ *                                  + (1 + g_mu) U_R(x-mu,mu)^dag psi(x-mu)]
+ * with the gamma basis of Sec. 2.2.  out_par selects the block (see
+ * hr_parity).  in and out hold nrhs fields in precision prec; in and out
+ * must not overlap; for HR_EO_PRECOND the handle's workspace holds the
+ * intermediate odd field, so concurrent calls on one handle must be
+ * stream-ordered.
+ * Errors: HR_ERR_INVALID (null pointers, nrhs < 1, prec not in prec_mask). */
+hr_status hr_dirac_apply(const hr_gauge *g, hr_parity out_par, hr_prec prec,
+                         const void *in, void *out, int nrhs, void *stream);
+
+/* The adjoint D_m^dag (= gamma5 D_m gamma5, Eq. Q_m), same blocks and
+ * arguments: EVEN gives (D^dag)_eo = (D_oe)^dag, EO_PRECOND gives Dhat^dag. */
+hr_status hr_dirac_dagger(const hr_gauge *g, hr_parity out_par, hr_prec prec,
+                          const void *in, void *out, int nrhs, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Conjugate gradient on the normal equations (Sec. 4.1.2, Sec. 4.3.3)    */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    double tol_rel;       /* stop when |b - A x| / |b| <= tol_rel (true residual) */
+    int max_iter;         /* total inner iterations allowed */
+    hr_prec inner;        /* HR_F64: plain FP64 CG; F32/F16/BF16: FP64 defect
+                             correction around an inner CG in that precision */
+    double inner_tol;     /* relative reduction asked of each inner solve */
+    int use_initial_guess;/* 1: x holds the start vector; 0: start from 0 */
+} hr_cg_params;
+
+typedef struct {
+    int iters;                 /* inner (or plain) CG iterations */
+    int outer_iters;           /* defect-correction steps (0 for plain FP64) */
+    double true_rel_residual;  /* |b - A x| / |b| recomputed in FP64 */
+    hr_status status;
+} hr_cg_result;
+
+/* Solves A x = b with A = D_m^dag D_m (sys = HR_FULL, FULL fields) or
+ * A = Dhat^dag Dhat (sys = HR_EO_PRECOND, even half fields).  b and x are
+ * FP64 fields of nrhs right-hand sides; res is a HOST array of nrhs results.
+ * The gauge handle must hold F64 links, and the inner precision's links
+ * when params->inner != HR_F64.  BLOCKS the calling thread until every
+ * right-hand side has converged or failed.
+ * Errors: HR_ERR_NOT_CONVERGED (x holds the last iterate),
+ *         HR_ERR_NONFINITE, HR_ERR_INVALID, HR_ERR_NOMEM, HR_ERR_CUDA. */
+hr_status hr_cg_solve(const hr_gauge *g, hr_parity sys, const void *b,
+                      void *x, int nrhs, const hr_cg_params *params,
+                      hr_cg_result *res, void *stream);
+
+/* Solves n_inst independent systems (different lattices, masses and
+ * right-hand-side counts; all with the same N and representation) together:
+ * every iteration of all unconverged instances is one CUDA-graph launch.
+ *   g[i], b[i], x[i], nrhs[i]  as in hr_cg_solve for instance i
+ *   res  HOST array of sum(nrhs) results, instance-major.
+ * BLOCKS until all instances finish. */
+hr_status hr_cg_solve_batched(int n_inst, const hr_gauge *const *g,
+                              hr_parity sys, const void *const *b,
+                              void *const *x, const int *nrhs,
+                              const hr_cg_params *params, hr_cg_result *res,
+                              void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Fermion force (Sec. 2.5)                                              */
+/* ------------------------------------------------------------------ */
+/* F[x][mu][a] += coeff * d/de S(U_F(x,mu) -> exp(i e T^a) U_F(x,mu)) at e=0
+ * with X, Y held fixed, where
+ *   sys = HR_FULL:        S = -2 Re <Y, D_m X>      (X, Y FULL FP64 fields)
+ *   sys = HR_EO_PRECOND:  S = -2 Re <Y, Dhat X>     (X, Y even FP64 fields)
+ * For X = A^{-1} phi and Y = D X (resp. Dhat X) this is the derivative of
+ * S_f = phi^dag A^{-1} phi.  The derivative reaches the fundamental link
+ * through dU_R = i e T_R^a U_R (T_R^a the generators in representation R).
+ * F is a device array of V*4*(N*N-1) doubles. */
+hr_status hr_dirac_force(const hr_gauge *g, hr_parity sys, const void *X,
+                         const void *Y, double coeff, void *F, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Introspection                                                         */
+/* ------------------------------------------------------------------ */
+/* Dimension D_R of a representation (Table 1); -1 if unsupported. */
+int hr_rep_dim(int N, hr_rep rep);
+/* Writes the (N*N-1) generators T^a (Tr T^a T^b = delta/2) as complex double
+ * [(N*N-1)][N][N] into the HOST array T. */
+hr_status hr_generators(int N, double *T);
+const char *hr_status_string(hr_status s);
+const char *hr_last_error(void);
+/* Number of kernel launches this library has issued in this process. */
+unsigned long long hr_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HR_H */

@@ -97,6 +97,7 @@ def _load():
             "or_cg": (I, [LP, P, I, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]),
             "or_force": (None, [LP, P, P, P, P]),
             "or_num_threads": (I, []),
+            "or_hop_sites": (None, [LP, P, I, P, P, ctypes.c_long, P, I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -193,6 +194,18 @@ def dhat(L: Lat, UR, in_e, dagger: bool = False) -> np.ndarray:
     UR, in_e = _c(UR), _c(in_e)
     out = np.zeros_like(in_e)
     _load().or_dhat(ctypes.byref(L), _p(UR), _p(in_e), _p(out), int(dagger))
+    return out
+
+
+def hop_sites(L: Lat, UF, out_parity: int, in_half, sites, dagger: bool = False) -> np.ndarray:
+    """(D_{p,1-p} in_half) at the given half-index sites of parity p, links represented
+    on the fly from the fundamental field UF."""
+    UF, in_half = _c(UF), _c(in_half)
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    D = rep_dim(L.N, L.rep)
+    out = np.zeros((len(sites), 4, D), np.complex128)
+    _load().or_hop_sites(ctypes.byref(L), _p(UF), int(out_parity), _p(in_half), _p(sites),
+                         len(sites), _p(out), int(dagger))
     return out
 
 

@@ -430,6 +430,52 @@ void or_dhat(const or_lat *L, const orc *UR, const orc *in_e, orc *out_e,
     free(tmp_e);
 }
 
+void or_hop_sites(const or_lat *L, const orc *UF, int out_parity,
+                  const orc *in_half, const long *sites, long nsites,
+                  orc *out, int dagger)
+{
+    int N = L->N, D = or_rep_dim(L->N, L->rep);
+    long V = or_volume(L);
+    orc gam[4][16];
+    load_gammas(gam);
+    double sg = dagger ? -1.0 : 1.0;
+#pragma omp parallel for schedule(static)
+    for (long k = 0; k < nsites; k++) {
+        /* the site of parity out_parity with half index sites[k] */
+        long x = -1;
+        for (long cand = 2 * sites[k]; cand <= 2 * sites[k] + 1 && cand < V; cand++)
+            if (or_parity(L, cand) == out_parity) x = cand;
+        orc acc[4 * OR_MAXD], R[OR_MAXD * OR_MAXD], chi[4 * OR_MAXD];
+        for (int q = 0; q < 4 * D; q++) acc[q] = 0;
+        int c[4];
+        or_coords(L, x, c);
+        for (int mu = 0; mu < 4; mu++)
+            for (int dir = +1; dir >= -1; dir -= 2) {
+                long y = or_neighbour(L, x, mu, dir);
+                long owner = dir > 0 ? x : y;   /* the link U(owner, mu) */
+                or_represent_link(N, L->rep, UF + ((size_t)owner * 4 + mu) * N * N, R);
+                int cown = dir > 0 ? c[mu] : (c[mu] - 1 + L->dims[mu]) % L->dims[mu];
+                double sign = (L->bc[mu] == -1 && cown == L->dims[mu] - 1) ? -1.0 : 1.0;
+                const orc *psi = in_half + (size_t)(y / 2) * 4 * D;
+                for (int s = 0; s < 4; s++)
+                    for (int r = 0; r < D; r++) {
+                        orc v = 0;
+                        for (int cc = 0; cc < D; cc++)
+                            v += (dir > 0 ? R[r * D + cc] : conj(R[cc * D + r])) * psi[s * D + cc];
+                        chi[s * D + r] = sign * v;
+                    }
+                double pm = -(double)dir * sg;
+                for (int s = 0; s < 4; s++)
+                    for (int r = 0; r < D; r++) {
+                        orc v = chi[s * D + r];
+                        for (int t = 0; t < 4; t++) v += pm * gam[mu][s * 4 + t] * chi[t * D + r];
+                        acc[s * D + r] += -0.5 * v;
+                    }
+            }
+        for (int q = 0; q < 4 * D; q++) out[(size_t)k * 4 * D + q] = acc[q];
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* Sec. 4.1.1: compensated summation                                     */
 /* ------------------------------------------------------------------ */

@@ -79,6 +79,15 @@ void or_hop_parity(const or_lat *L, const orc *UR, int out_parity,
 void or_dhat(const or_lat *L, const orc *UR, const orc *in_e, orc *out_e,
              int dagger);
 
+/* The same hopping block at a list of output sites only, for checking large
+ * lattices one site at a time: out[k] = (D_{p,1-p} in_half)(site k) where the
+ * sites are given as half indices of parity p.  Links are taken from the
+ * FUNDAMENTAL field UF and represented on the fly (or_represent_link, with the
+ * boundary signs of or_represent_field).  out is [nsites][4][D]. */
+void or_hop_sites(const or_lat *L, const orc *UF, int out_parity,
+                  const orc *in_half, const long *sites, long nsites,
+                  orc *out, int dagger);
+
 /* ---- reductions (Sec. 4.1.1, Algorithms FastTwoSum .. DoubleDoubleSum) ---- */
 void   or_fast_two_sum(double a, double b, double *s, double *c);
 double or_sum_naive(const double *a, long n);

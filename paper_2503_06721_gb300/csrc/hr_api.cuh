@@ -1,0 +1,42 @@
+// hr_api.cuh -- host-side internals shared by hr_api.cu and hr_cg.cu.
+#pragma once
+
+#include <algorithm>
+#include <vector>
+
+#include "hr_blas.cuh"
+#include "hr_gauge.cuh"
+
+namespace hr {
+
+// device scratch for fused reductions and solver state
+struct Scratch {
+    double *partials;   // [nrhs][max_blocks][2]
+    unsigned *counters; // [8 * nrhs] (zero between kernels)
+    CgState *state;     // [nrhs]
+    double *red;        // [nrhs][4]
+    double *carry;      // [nrhs][4]
+    double *sv;         // [nrhs][2] per-rhs scalars
+};
+
+long lat_volume(const hr_lattice_desc &l);
+hr_status check_lattice(const hr_lattice_desc *lat);
+bool pair_supported(int N, int rep);
+Geom make_geom(const hr_lattice_desc &l);
+FieldView make_view(void *ptr, long nsites, int D, int P);
+FieldView half_view(const FieldView &full, int parity, long vh, int D, int P);
+hr_status ws_reserve(const hr_gauge *g, size_t bytes, cudaStream_t stream);
+Scratch carve_scratch(char *&p, int nrhs, long max_blocks);
+size_t scratch_bytes(int nrhs, long max_blocks);
+long max_blocks_for(const hr_gauge *g);
+
+hr_status hop(const hr_gauge *g, int P, int out_parity, int dagger, const FieldView &in, const FieldView &out,
+              const FieldView *diag, double a, double b, int nrhs, cudaStream_t stream, int epi,
+              const Scratch *sc = nullptr, int fin = FIN_WRITE, const double *carry = nullptr,
+              double *red_out = nullptr, const FieldView *r = nullptr, const FieldView *x = nullptr,
+              const FieldView *p = nullptr);
+
+// (T_R^a)_{nm} as complex double [(N*N-1)][D][D] (host)
+void rep_generator_table(int N, int rep, double *out);
+
+}  // namespace hr

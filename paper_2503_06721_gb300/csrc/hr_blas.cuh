@@ -1,0 +1,44 @@
+// hr_blas.cuh -- fused site-parallel linear algebra for the solver
+// (Sec. 3.2 "Linear Combinations" and "Reductions"): each kernel reads and
+// writes every vector once and folds its reductions into the same pass.
+#pragma once
+
+#include "hr_fields.cuh"
+
+namespace hr {
+
+struct BlasParams {
+    long nsites;
+    int nrhs;
+    FieldView a, b, c, d;     // meaning depends on the kernel
+    double s;                 // scalar argument
+    const double *sv;         // per-rhs scalars (device) or nullptr
+    double *partials;         // [nrhs][nblocks][NV]
+    unsigned *counters;       // [nrhs]
+    double *red_out;          // [nrhs][NV]
+    CgState *state;           // [nrhs]
+    double tol2;              // squared relative tolerance for state init
+    int skip_converged;
+};
+
+// a <- convert(b) * (sv ? sv[rhs] : s)            (any precisions)
+hr_status blas_convert(int D, int Pdst, int Psrc, const BlasParams &bp, cudaStream_t st);
+// a(F64) <- b(F64) - c(F64);  reduce |a|^2, |b|^2 into state (rr, b2, stop2 = tol2*b2)
+// and red_out[rhs][0..1]
+hr_status blas_residual_init(int D, const BlasParams &bp, cudaStream_t st);
+// p(c, Pp) <- r(a, compute type of Pp) + beta p   (beta = state[rhs].beta), skips converged
+hr_status blas_xpay_beta(int D, int Pp, const BlasParams &bp, cudaStream_t st);
+// inner start of defect correction with f = sv[rhs]:
+//   a (F32 r_in) <- f * b (F64 r);  c (F32 x_in) <- 0;  d (Pp p) <- a;
+//   reduce |r_in|^2 into state: rr, b2, stop2 = tol2 * rr, converged, iter = 0
+hr_status blas_inner_init(int D, int Pp, const BlasParams &bp, cudaStream_t st);
+// a (F64 x) += sv[rhs] * b (F32 x_in)
+hr_status blas_outer_update(int D, const BlasParams &bp, cudaStream_t st);
+// red_out[rhs][0..1] <- <a, b> (re, im), both in precision P
+hr_status blas_dot(int D, int P, const BlasParams &bp, cudaStream_t st);
+// a(F64) <- x-update for plain CG initial state without guess: a = b, c = 0, reduce |b|^2
+hr_status blas_start_zero(int D, const BlasParams &bp, cudaStream_t st);
+
+constexpr int BLAS_THREADS = 256;
+
+}  // namespace hr

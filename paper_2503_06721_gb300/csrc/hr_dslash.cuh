@@ -1,0 +1,238 @@
+// hr_dslash.cuh -- the Wilson hopping kernel (Eq. D_m^R, Sec. 2.3):
+//
+//   H psi(x) = sum_mu [ (1 - s g_mu) U_R(x,mu) psi(x+mu)
+//                     + (1 + s g_mu) U_R(x-mu,mu)^dag psi(x-mu) ],
+//   s = +1 for D, s = -1 for D^dag (gamma_mu Hermitian),
+//
+// evaluated for all sites of one output parity.  One thread owns one output
+// site (and one right-hand side).  For each of the 8 hops it loads the
+// neighbour spinor (16-byte vector loads, read-only path), projects it to the
+// two-component half spinor h = up + s' e_mu dn, multiplies both components by
+// the link (streamed from the AoSoA link record with evict-first loads, or
+// rebuilt from the fundamental link in registers) and reconstructs the lower
+// spin components as s' e_mu^dag (U h).  The epilogue forms
+//   out = a * H(in) + b * diag
+// and, depending on EPI, stores it, reduces |out|^2, or performs the fused CG
+// update r -= alpha * out, x += alpha * p, |r|^2 without storing out.
+#pragma once
+
+#include "hr_fields.cuh"
+#include "hr_rep.cuh"
+
+namespace hr {
+
+enum { EPI_STORE = 0, EPI_STORE_NORM = 1, EPI_CG_UPDATE = 2 };
+enum { FIN_WRITE = 0, FIN_CG_ALPHA = 1, FIN_CG_BETA = 2 };
+
+struct HopParams {
+    Geom g;
+    int out_parity;
+    int dagger;
+    const void *links;        // link records of the output parity
+    FieldView in;             // opposite parity
+    FieldView out;            // output parity (EPI_STORE*)
+    FieldView diag;           // output parity, may have data == nullptr
+    double a, b;
+    int nrhs;
+    // reductions
+    double *partials;         // [nrhs][nblocks][1]
+    unsigned *counters;       // [nrhs]
+    double *red_out;          // [nrhs]   (FIN_WRITE)
+    const double *carry;      // [nrhs] added to the total before finalising, or nullptr
+    int fin;                  // FIN_WRITE / FIN_CG_ALPHA / FIN_CG_BETA
+    CgState *state;           // [nrhs]   (CG epilogues; skip converged rhs)
+    // fused CG update (compute-type arrays, same layout as the fields)
+    FieldView r, x, p;
+};
+
+// what the last block does with the grid total of a fused reduction
+__device__ __forceinline__ void hop_finalize(const HopParams &prm, int rhs, double tot)
+{
+    if (prm.carry) tot += prm.carry[rhs];
+    if (prm.fin == FIN_WRITE) {
+        prm.red_out[rhs] = tot;
+    } else if (prm.fin == FIN_CG_ALPHA) {
+        CgState &cs = prm.state[rhs];
+        cs.pAp = tot;
+        cs.alpha = cs.rr / tot;
+        if (!isfinite(cs.alpha) || tot <= 0.0) {
+            cs.nonfinite = isfinite(tot) ? 0 : 1;
+            cs.converged = 1;   // breakdown: stop this rhs, the host inspects it
+            cs.alpha = 0;
+        }
+    } else {
+        CgState &cs = prm.state[rhs];
+        cs.iter += 1;
+        if (!isfinite(tot)) {
+            cs.nonfinite = 1;
+            cs.converged = 1;
+        } else {
+            cs.beta = tot / cs.rr;
+            cs.rr = tot;
+            if (tot <= cs.stop2) cs.converged = 1;
+        }
+    }
+}
+
+template <int N, int REP, int P, bool REBUILD, int EPI, int MINB = 1>
+__global__ void __launch_bounds__(128, MINB) hop_kernel(const HopParams prm)
+{
+    using S = St<P>;
+    using R = typename S::R;
+    constexpr int D = rep_dim(N, REP);
+    constexpr bool REAL = rep_real(REP) && !REBUILD;
+    constexpr int NCOMP = REBUILD ? N * N : D * D;
+    using SIO = SpinorIO<P, D>;
+    using LIO = LinkIO<P, REAL, NCOMP>;
+
+    const Geom &g = prm.g;
+    const int rhs = blockIdx.y;
+    if (prm.state && prm.state[rhs].converged) return;   // uniform per block
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < g.vh;
+    const R sg = prm.dagger ? (R)-1 : (R)1;
+
+    cx<R> acc[4][D];
+#pragma unroll
+    for (int s = 0; s < 4; s++)
+#pragma unroll
+        for (int c = 0; c < D; c++) acc[s][c] = {0, 0};
+
+    Site st;
+    if (active) {
+        st = site_of(g, i, prm.out_parity);
+        const long tile = i / HR_TILE;
+        const int lane = (int)(i % HR_TILE);
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const int mu = k & 3;
+            const bool fwd = k < 4;
+            const long nb = neighbour(g, st, mu, fwd ? +1 : -1);
+            // projector (1 + sp gamma_mu): sp = -s forward, +s backward
+            const R sp = fwd ? -sg : sg;
+            cx<R> psi[4][D];
+            SIO::load(prm.in, rhs, nb, psi);
+            cx<R> h[2][D];
+#pragma unroll
+            for (int r = 0; r < 2; r++)
+#pragma unroll
+                for (int c = 0; c < D; c++)
+                    h[r][c] = psi[r][c] + sp * ipow(ephase(mu, r), psi[2 + eperm(mu, r)][c]);
+            cx<R> chi[2][D];
+            const typename LIO::E *lp = LIO::slot_ptr(prm.links, tile, k, lane);
+            if constexpr (REBUILD) {
+                cx<R> F[N][N];
+#pragma unroll
+                for (int a = 0; a < N; a++)
+#pragma unroll
+                    for (int b = 0; b < N; b++) F[a][b] = LIO::ldc(lp, a * N + b);
+                rep_act<N, REP, R>(F, h[0], chi[0]);
+                rep_act<N, REP, R>(F, h[1], chi[1]);
+                // fermion boundary sign on the t = T-1 <-> 0 (etc.) hop
+                const int xc = st.c[mu];
+                const int L = mu == 0 ? g.T : mu == 1 ? g.X : mu == 2 ? g.Y : g.Z;
+                if (g.bc[mu] == -1 && (fwd ? xc == L - 1 : xc == 0)) {
+#pragma unroll
+                    for (int r = 0; r < 2; r++)
+#pragma unroll
+                        for (int c = 0; c < D; c++) chi[r][c] = (R)-1 * chi[r][c];
+                }
+            } else {
+#pragma unroll
+                for (int row = 0; row < D; row++) {
+                    cx<R> s0 = {0, 0}, s1 = {0, 0};
+#pragma unroll
+                    for (int col = 0; col < D; col++) {
+                        if constexpr (REAL) {
+                            R w = LIO::ldr(lp, row * D + col);
+                            rmac(s0, w, h[0][col]);
+                            rmac(s1, w, h[1][col]);
+                        } else {
+                            cx<R> w = LIO::ldc(lp, row * D + col);
+                            cmac(s0, w, h[0][col]);
+                            cmac(s1, w, h[1][col]);
+                        }
+                    }
+                    chi[0][row] = s0;
+                    chi[1][row] = s1;
+                }
+            }
+            // reconstruct: upper += chi, lower_{eperm(r)} += sp i^{-ephase(r)} chi_r
+#pragma unroll
+            for (int r = 0; r < 2; r++)
+#pragma unroll
+                for (int c = 0; c < D; c++) {
+                    acc[r][c] = acc[r][c] + chi[r][c];
+                    acc[2 + eperm(mu, r)][c] = acc[2 + eperm(mu, r)][c] + sp * ipow(4 - ephase(mu, r), chi[r][c]);
+                }
+        }
+        // epilogue: out = a * H + b * diag
+        const R a = (R)prm.a, b = (R)prm.b;
+        if (prm.diag.data) {
+            cx<R> d[4][D];
+            SIO::load(prm.diag, rhs, i, d);
+#pragma unroll
+            for (int s = 0; s < 4; s++)
+#pragma unroll
+                for (int c = 0; c < D; c++) acc[s][c] = a * acc[s][c] + b * d[s][c];
+        } else {
+#pragma unroll
+            for (int s = 0; s < 4; s++)
+#pragma unroll
+                for (int c = 0; c < D; c++) acc[s][c] = a * acc[s][c];
+        }
+    }
+
+    if constexpr (EPI == EPI_STORE) {
+        if (active) SIO::store(prm.out, rhs, i, acc);
+        return;
+    } else if constexpr (EPI == EPI_STORE_NORM) {
+        double v[1] = {0.0};
+        if (active) {
+            SIO::store(prm.out, rhs, i, acc);
+            R n2 = 0;
+#pragma unroll
+            for (int s = 0; s < 4; s++)
+#pragma unroll
+                for (int c = 0; c < D; c++) n2 += acc[s][c].re * acc[s][c].re + acc[s][c].im * acc[s][c].im;
+            v[0] = (double)n2;
+        }
+        double tot[1];
+        if (grid_reduce<1>(v, prm.partials + (size_t)rhs * gridDim.x, prm.counters + rhs, gridDim.x,
+                           blockIdx.x, tot))
+            hop_finalize(prm, rhs, tot[0]);
+    } else {
+        // fused CG update with out = A p:  x += alpha p;  r -= alpha A p;  |r|^2
+        double v[1] = {0.0};
+        if (active) {
+            using CIO = SpinorIO<(P == HR_F64 ? HR_F64 : HR_F32), D>;
+            const R alpha = (R)prm.state[rhs].alpha;
+            cx<R> rr[4][D], xx[4][D], pp[4][D];
+            CIO::load_rw(prm.r, rhs, i, rr);
+            CIO::load_rw(prm.x, rhs, i, xx);
+            SIO::load_rw(prm.p, rhs, i, pp);
+            R n2 = 0;
+#pragma unroll
+            for (int s = 0; s < 4; s++)
+#pragma unroll
+                for (int c = 0; c < D; c++) {
+                    rr[s][c] = rr[s][c] - alpha * acc[s][c];
+                    xx[s][c] = xx[s][c] + alpha * pp[s][c];
+                    n2 += rr[s][c].re * rr[s][c].re + rr[s][c].im * rr[s][c].im;
+                }
+            CIO::store(prm.r, rhs, i, rr);
+            CIO::store(prm.x, rhs, i, xx);
+            v[0] = (double)n2;
+        }
+        double tot[1];
+        if (grid_reduce<1>(v, prm.partials + (size_t)rhs * gridDim.x, prm.counters + rhs, gridDim.x,
+                           blockIdx.x, tot))
+            hop_finalize(prm, rhs, tot[0]);
+    }
+}
+
+// host-side launcher, instantiated per (N, REP, P) in hr_dslash_*.cu
+template <int N, int REP, int P>
+hr_status launch_hop(const HopParams &prm, bool rebuild, int epi, cudaStream_t stream);
+
+}  // namespace hr

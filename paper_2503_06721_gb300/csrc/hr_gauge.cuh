@@ -1,0 +1,66 @@
+// hr_gauge.cuh -- the gauge handle and the per-(N, representation) entry
+// points that the C ABI dispatches to.
+#pragma once
+
+#include <vector>
+
+#include "hr_dslash.cuh"
+
+struct hr_gauge {
+    hr_lattice_desc lat;
+    hr::Geom geom;
+    int D;
+    bool real;            // ADJ: represented links stored as reals
+    unsigned prec_mask;
+    unsigned link_modes;
+    hr_link_mode mode;
+    // link records per [precision][output parity]
+    void *rep[4][2];
+    void *fund[4][2];
+    size_t rep_bytes[4], fund_bytes[4];
+    // T_R^a tables for the force, [(N*N-1)][D][D] complex double
+    double *TR;
+    // solver workspace (grown on demand)
+    char *ws;
+    size_t ws_bytes;
+    void *pinned;         // host staging for solver state (pinned)
+    size_t pinned_bytes;
+    int device;
+};
+
+namespace hr {
+
+struct RepOut {
+    void *rep[4];    // record base for this parity per precision (nullptr = skip)
+    void *fund[4];
+};
+
+// per-(N, REP) instantiated operations (hr_gauge_inst.cu)
+template <int N, int REP>
+hr_status represent_launch(const hr_gauge &g, const double2 *UF, cudaStream_t stream);
+
+struct ForceParams {
+    Geom g;
+    int parity;             // sites of this parity own the links processed
+    const void *links;      // F64 stored records of this parity (U_R with signs)
+    FieldView X_here, Y_here;   // FULL-field views of X, Y at sites of `parity`
+    FieldView X_nb, Y_nb;       // views of the opposite parity
+    const double *TR;
+    double coeff;
+    double *F;              // [V][4][N*N-1] lexicographic
+};
+template <int N, int REP>
+hr_status force_launch(const ForceParams &fp, cudaStream_t stream);
+
+// precision dispatch of the hop kernel for a runtime (N, rep)
+hr_status hop_dispatch(int N, int rep, int P, const HopParams &prm, bool rebuild, int epi, cudaStream_t stream);
+hr_status represent_dispatch(const hr_gauge &g, const double2 *UF, cudaStream_t stream);
+hr_status force_dispatch(const hr_gauge &g, const ForceParams &fp, cudaStream_t stream);
+
+// link record bytes of one parity
+inline size_t link_record_bytes(const Geom &g, int ncomp, size_t elem)
+{
+    return (size_t)g.ntiles * 8 * ncomp * HR_TILE * elem;
+}
+
+}  // namespace hr

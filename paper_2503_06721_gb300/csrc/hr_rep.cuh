@@ -1,0 +1,200 @@
+// hr_rep.cuh -- representation maps of SU(N) written as sparse compile-time
+// structure (Sec. 2.3, Table 1).
+//
+// Generators T^a: generalised Gell-Mann matrices / 2 (Tr T^a T^b = delta/2),
+// ordered: for each pair j<k (lexicographic) the symmetric one
+// (E_jk+E_kj)/2 then the antisymmetric one -i(E_jk-E_kj)/2; then the
+// diagonal ones diag(1,..,1,-l,0,..)/sqrt(2l(l+1)), l = 1..N-1.
+// ADJ coordinates: v_a = 2 Tr(T^a X) for X = sum_a v_a T^a, action X -> U X U^dag.
+// SYM/ASYM basis: e_(ii) = E_ii, e_(ij) = (E_ij +- E_ji)/sqrt(2) (i<j, lex),
+// coordinates v_n = Tr(e_n^dag X), action X -> U X U^T.
+// Hence R(U)_ab = 2 Tr(T^a U T^b U^dag) (ADJ), R(U)_nm = Tr(e_n^dag U e_m U^T).
+#pragma once
+
+#include <type_traits>
+
+#include "hr_internal.cuh"
+
+namespace hr {
+
+__host__ __device__ constexpr int ngen(int N) { return N * N - 1; }
+__host__ __device__ constexpr int noff(int N) { return N * (N - 1); }
+
+// --- generator T^a: number of nonzero entries, their (row, col, value) ---
+__host__ __device__ constexpr int gen_nent(int N, int a) { return a < noff(N) ? 2 : a - noff(N) + 2; }
+__host__ __device__ constexpr int gen_row(int N, int a, int e)
+{
+    return a < noff(N) ? (e == 0 ? pair_j(N, a / 2) : pair_k(N, a / 2)) : e;
+}
+__host__ __device__ constexpr int gen_col(int N, int a, int e)
+{
+    return a < noff(N) ? (e == 0 ? pair_k(N, a / 2) : pair_j(N, a / 2)) : e;
+}
+__host__ __device__ inline double diag_norm(int l)
+{
+    // 1 / sqrt(2 l (l+1)) for l = 1, 2, 3
+    return l == 1 ? 0.5 : l == 2 ? 0.28867513459481288225 : 0.20412414523193150818;
+}
+template <class R>
+__host__ __device__ inline cx<R> gen_val(int N, int a, int e)
+{
+    if (a < noff(N)) {
+        if ((a & 1) == 0) return {(R)0.5, (R)0};
+        return e == 0 ? cx<R>{(R)0, (R)-0.5} : cx<R>{(R)0, (R)0.5};
+    }
+    int l = a - noff(N) + 1;
+    double n = diag_norm(l);
+    return {(R)(e < l ? n : -l * n), (R)0};
+}
+
+// --- SYM / ASYM basis element n ---
+#define HR_RSQRT2 0.70710678118654752440
+__host__ __device__ constexpr int sb_i(int N, int rep, int n) { return sympair_i(N, n, rep == HR_ASYM); }
+__host__ __device__ constexpr int sb_j(int N, int rep, int n) { return sympair_j(N, n, rep == HR_ASYM); }
+__host__ __device__ constexpr int sb_nent(int N, int rep, int n) { return sb_i(N, rep, n) == sb_j(N, rep, n) ? 1 : 2; }
+__host__ __device__ constexpr int sb_row(int N, int rep, int n, int e) { return e == 0 ? sb_i(N, rep, n) : sb_j(N, rep, n); }
+__host__ __device__ constexpr int sb_col(int N, int rep, int n, int e) { return e == 0 ? sb_j(N, rep, n) : sb_i(N, rep, n); }
+__host__ __device__ inline double sb_val(int N, int rep, int n, int e)
+{
+    if (sb_nent(N, rep, n) == 1) return 1.0;
+    return (rep == HR_ASYM && e == 1) ? -HR_RSQRT2 : HR_RSQRT2;
+}
+
+// --- R(U) as a dense D x D matrix (FP64), U given as N x N ---
+template <int N, int REP>
+__host__ __device__ inline void represent(const cx<double> (&U)[N][N], cx<double> (&Rm)[rep_dim(N, REP)][rep_dim(N, REP)])
+{
+    constexpr int D = rep_dim(N, REP);
+    if constexpr (REP == HR_FUND) {
+        for (int i = 0; i < N; i++)
+            for (int j = 0; j < N; j++) Rm[i][j] = U[i][j];
+    } else if constexpr (REP == HR_ADJ) {
+        // R_ab = 2 Re sum_{(i,j,al) in T_a} sum_{(k,l,be) in T_b} al be U_jk conj(U_il)
+        for (int a = 0; a < D; a++)
+            for (int b = 0; b < D; b++) {
+                cx<double> s = {0, 0};
+                for (int e1 = 0; e1 < gen_nent(N, a); e1++) {
+                    int i = gen_row(N, a, e1), j = gen_col(N, a, e1);
+                    cx<double> al = gen_val<double>(N, a, e1);
+                    for (int e2 = 0; e2 < gen_nent(N, b); e2++) {
+                        int k = gen_row(N, b, e2), l = gen_col(N, b, e2);
+                        cx<double> be = gen_val<double>(N, b, e2);
+                        s = s + (al * be) * (U[j][k] * conj(U[i][l]));
+                    }
+                }
+                Rm[a][b] = {2.0 * s.re, 0.0};
+            }
+    } else {
+        // R_nm = sum_{(i,j,w) in e_n} sum_{(k,l,v) in e_m} w v U_ik U_jl
+        for (int n = 0; n < D; n++)
+            for (int m = 0; m < D; m++) {
+                cx<double> s = {0, 0};
+                for (int e1 = 0; e1 < sb_nent(N, REP, n); e1++) {
+                    int i = sb_row(N, REP, n, e1), j = sb_col(N, REP, n, e1);
+                    double w = sb_val(N, REP, n, e1);
+                    for (int e2 = 0; e2 < sb_nent(N, REP, m); e2++) {
+                        int k = sb_row(N, REP, m, e2), l = sb_col(N, REP, m, e2);
+                        double v = sb_val(N, REP, m, e2);
+                        s = s + (w * v) * (U[i][k] * U[j][l]);
+                    }
+                }
+                Rm[n][m] = s;
+            }
+    }
+}
+
+// compile-time loop: f(std::integral_constant<int, I>) for I = B..E-1
+template <int B, int E, class F>
+__host__ __device__ __forceinline__ void static_for(F &&f)
+{
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
+// --- action of R(F) on a colour vector without forming R(F) (in-kernel
+// rebuild): vector -> matrix, conjugate by F, matrix -> vector.  All basis
+// indices are compile-time constants (static_for), so X, Z stay in registers.
+template <int N, int REP, class R>
+__device__ __forceinline__ void rep_act(const cx<R> (&F)[N][N], const cx<R> (&v)[rep_dim(N, REP)],
+                                        cx<R> (&out)[rep_dim(N, REP)])
+{
+    constexpr int D = rep_dim(N, REP);
+    if constexpr (REP == HR_FUND) {
+#pragma unroll
+        for (int i = 0; i < N; i++) {
+            cx<R> s = {0, 0};
+#pragma unroll
+            for (int j = 0; j < N; j++) cmac(s, F[i][j], v[j]);
+            out[i] = s;
+        }
+    } else {
+        cx<R> X[N][N];
+#pragma unroll
+        for (int i = 0; i < N; i++)
+#pragma unroll
+            for (int j = 0; j < N; j++) X[i][j] = {0, 0};
+        if constexpr (REP == HR_ADJ) {
+            static_for<0, D>([&](auto A) {
+                constexpr int a = decltype(A)::value;
+                static_for<0, gen_nent(N, a)>([&](auto EE) {
+                    constexpr int e = decltype(EE)::value;
+                    cmac(X[gen_row(N, a, e)][gen_col(N, a, e)], gen_val<R>(N, a, e), v[a]);
+                });
+            });
+        } else {
+            static_for<0, D>([&](auto NN) {
+                constexpr int n = decltype(NN)::value;
+                static_for<0, sb_nent(N, REP, n)>([&](auto EE) {
+                    constexpr int e = decltype(EE)::value;
+                    rmac(X[sb_row(N, REP, n, e)][sb_col(N, REP, n, e)], (R)sb_val(N, REP, n, e), v[n]);
+                });
+            });
+        }
+        // Z = F X
+        cx<R> Z[N][N];
+#pragma unroll
+        for (int i = 0; i < N; i++)
+#pragma unroll
+            for (int j = 0; j < N; j++) {
+                cx<R> s = {0, 0};
+#pragma unroll
+                for (int k = 0; k < N; k++) cmac(s, F[i][k], X[k][j]);
+                Z[i][j] = s;
+            }
+        if constexpr (REP == HR_ADJ) {
+            // v'_a = 2 sum_{(i,j,al) in T_a} al Y_ji,  Y = Z F^dag: Y_ji = sum_k Z_jk conj(F_ik)
+            static_for<0, D>([&](auto A) {
+                constexpr int a = decltype(A)::value;
+                cx<R> s = {0, 0};
+                static_for<0, gen_nent(N, a)>([&](auto EE) {
+                    constexpr int e = decltype(EE)::value;
+                    constexpr int i = gen_row(N, a, e), j = gen_col(N, a, e);
+                    cx<R> y = {0, 0};
+#pragma unroll
+                    for (int k = 0; k < N; k++) cmac_cj(y, F[i][k], Z[j][k]);
+                    cmac(s, gen_val<R>(N, a, e), y);
+                });
+                out[a] = (R)2 * s;
+            });
+        } else {
+            // v'_n = sum_{(i,j,w) in e_n} w Y_ij,  Y = Z F^T: Y_ij = sum_k Z_ik F_jk
+            static_for<0, D>([&](auto NN) {
+                constexpr int n = decltype(NN)::value;
+                cx<R> s = {0, 0};
+                static_for<0, sb_nent(N, REP, n)>([&](auto EE) {
+                    constexpr int e = decltype(EE)::value;
+                    constexpr int i = sb_row(N, REP, n, e), j = sb_col(N, REP, n, e);
+                    cx<R> y = {0, 0};
+#pragma unroll
+                    for (int k = 0; k < N; k++) cmac(y, Z[i][k], F[j][k]);
+                    rmac(s, (R)sb_val(N, REP, n, e), y);
+                });
+                out[n] = s;
+            });
+        }
+    }
+}
+
+}  // namespace hr

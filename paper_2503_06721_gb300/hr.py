@@ -1,0 +1,292 @@
+"""ctypes binding of libhr (include/hr.h): the same names, argument marshalling
+only.  Every operation runs in the library's CUDA kernels; if libhr.so is
+missing this module raises instead of falling back to anything else.
+
+Tensors are torch CUDA tensors (PyTorch supplies device memory and streams):
+  FP64 fields  complex128 [nrhs, nsites, 4, D] (or [nsites, 4, D])
+  FP32 fields  complex64  of the same shape
+  F16/BF16     uint8 buffers of field_bytes(...) bytes (data + per-site scales)
+  gauge input  complex128 [V, 4, N, N]
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from pathlib import Path
+
+import torch
+
+_LIB_PATH = Path(__file__).resolve().parent / "_lib" / "libhr.so"
+
+FUND, ADJ, SYM, ASYM = 0, 1, 2, 3
+REPS = {"FUND": FUND, "ADJ": ADJ, "SYM": SYM, "ASYM": ASYM, "2AS": ASYM}
+F64, F32, F16, BF16 = 0, 1, 2, 3
+PRECS = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
+EVEN, ODD, FULL, EO_PRECOND = 0, 1, 2, 3
+LINKS_STORED, LINKS_REBUILD = 0, 1
+
+STATUS = {0: "HR_OK", -1: "HR_ERR_INVALID", -2: "HR_ERR_CUDA", -3: "HR_ERR_NOMEM",
+          -4: "HR_ERR_NOT_CONVERGED", -5: "HR_ERR_NONFINITE", -6: "HR_ERR_TIMEOUT",
+          -7: "HR_ERR_UNSUPPORTED"}
+
+# every symbol include/hr.h declares
+EXPORTS = ["hr_represent_gauge", "hr_gauge_update", "hr_gauge_set_link_mode", "hr_gauge_destroy",
+           "hr_field_bytes", "hr_field_convert", "hr_field_dot", "hr_dirac_apply", "hr_dirac_dagger",
+           "hr_cg_solve", "hr_cg_solve_batched", "hr_dirac_force", "hr_rep_dim", "hr_generators",
+           "hr_status_string", "hr_last_error", "hr_launch_count"]
+
+
+class HrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class LatticeDesc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("rep", ctypes.c_int), ("dims", ctypes.c_int * 4),
+                ("bc", ctypes.c_int * 4), ("m0", ctypes.c_double)]
+
+
+class CgParams(ctypes.Structure):
+    _fields_ = [("tol_rel", ctypes.c_double), ("max_iter", ctypes.c_int), ("inner", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("use_initial_guess", ctypes.c_int)]
+
+
+class CgResult(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int),
+                ("true_rel_residual", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib_path() -> Path:
+    return _LIB_PATH
+
+
+def load():
+    """Opens libhr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not _LIB_PATH.exists():
+        raise RuntimeError(f"{_LIB_PATH} is not built; run paper_2503_06721_gb300.build.build()")
+    L = ctypes.CDLL(str(_LIB_PATH))
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    LP = ctypes.POINTER(LatticeDesc)
+    sig = {
+        "hr_represent_gauge": (I, [LP, P, ctypes.c_uint, ctypes.c_uint, P, ctypes.POINTER(P)]),
+        "hr_gauge_update": (I, [P, P, P]),
+        "hr_gauge_set_link_mode": (I, [P, I]),
+        "hr_gauge_destroy": (I, [P]),
+        "hr_field_bytes": (S, [LP, I, I, I]),
+        "hr_field_convert": (I, [LP, I, I, P, I, P, I, P]),
+        "hr_field_dot": (I, [LP, I, I, P, P, I, ctypes.POINTER(D), P]),
+        "hr_dirac_apply": (I, [P, I, I, P, P, I, P]),
+        "hr_dirac_dagger": (I, [P, I, I, P, P, I, P]),
+        "hr_cg_solve": (I, [P, I, P, P, I, ctypes.POINTER(CgParams), ctypes.POINTER(CgResult), P]),
+        "hr_cg_solve_batched": (I, [I, ctypes.POINTER(P), I, ctypes.POINTER(P), ctypes.POINTER(P),
+                                    ctypes.POINTER(I), ctypes.POINTER(CgParams),
+                                    ctypes.POINTER(CgResult), P]),
+        "hr_dirac_force": (I, [P, I, P, P, D, P, P]),
+        "hr_rep_dim": (I, [I, I]),
+        "hr_generators": (I, [I, ctypes.POINTER(D)]),
+        "hr_status_string": (ctypes.c_char_p, [I]),
+        "hr_last_error": (ctypes.c_char_p, []),
+        "hr_launch_count": (ctypes.c_ulonglong, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != 0:
+        raise HrError(status, load().hr_last_error().decode())
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def launch_count() -> int:
+    return int(load().hr_launch_count())
+
+
+def rep_dim(N: int, rep) -> int:
+    return load().hr_rep_dim(N, REPS.get(rep, rep) if isinstance(rep, str) else rep)
+
+
+def generators(N: int):
+    import numpy as np
+    buf = (ctypes.c_double * (2 * (N * N - 1) * N * N))()
+    _check(load().hr_generators(N, buf))
+    a = np.frombuffer(buf, dtype=np.float64).copy()
+    return (a[0::2] + 1j * a[1::2]).reshape(N * N - 1, N, N)
+
+
+@dataclass
+class Lattice:
+    N: int
+    rep: str
+    dims: tuple
+    bc: tuple = (-1, 1, 1, 1)
+    m0: float = 0.0
+
+    @property
+    def D(self) -> int:
+        return rep_dim(self.N, self.rep)
+
+    @property
+    def volume(self) -> int:
+        T, X, Y, Z = self.dims
+        return T * X * Y * Z
+
+    def desc(self) -> LatticeDesc:
+        d = LatticeDesc()
+        d.N = self.N
+        d.rep = REPS[self.rep] if isinstance(self.rep, str) else self.rep
+        for i in range(4):
+            d.dims[i] = self.dims[i]
+            d.bc[i] = self.bc[i]
+        d.m0 = self.m0
+        return d
+
+    def nsites(self, parity: int) -> int:
+        return self.volume if parity == FULL else self.volume // 2
+
+
+def field_bytes(lat: Lattice, parity: int, prec: int, nrhs: int = 1) -> int:
+    d = lat.desc()
+    return int(load().hr_field_bytes(ctypes.byref(d), parity, prec, nrhs))
+
+
+def empty_field(lat: Lattice, parity: int, prec: int, nrhs: int = 1, device="cuda"):
+    ns = lat.nsites(parity)
+    shape = (nrhs, ns, 4, lat.D) if nrhs > 1 else (ns, 4, lat.D)
+    if prec == F64:
+        return torch.empty(shape, dtype=torch.complex128, device=device)
+    if prec == F32:
+        return torch.empty(shape, dtype=torch.complex64, device=device)
+    return torch.empty(field_bytes(lat, parity, prec, nrhs), dtype=torch.uint8, device=device)
+
+
+def field_convert(lat: Lattice, parity: int, src, src_prec: int, dst_prec: int, nrhs: int = 1,
+                  dst=None, stream=None):
+    if dst is None:
+        dst = empty_field(lat, parity, dst_prec, nrhs, src.device)
+    d = lat.desc()
+    _check(load().hr_field_convert(ctypes.byref(d), parity, src_prec, _ptr(src), dst_prec, _ptr(dst),
+                                   nrhs, _stream(stream)))
+    return dst
+
+
+def field_dot(lat: Lattice, parity: int, prec: int, a, b, nrhs: int = 1, stream=None):
+    d = lat.desc()
+    out = (ctypes.c_double * (2 * nrhs))()
+    _check(load().hr_field_dot(ctypes.byref(d), parity, prec, _ptr(a), _ptr(b), nrhs, out,
+                               _stream(stream)))
+    return [complex(out[2 * k], out[2 * k + 1]) for k in range(nrhs)]
+
+
+def _prec_mask(precs) -> int:
+    m = 0
+    for p in precs:
+        m |= 1 << (PRECS[p] if isinstance(p, str) else p)
+    return m
+
+
+class Gauge:
+    """Owns an hr_gauge handle built by hr_represent_gauge."""
+
+    def __init__(self, lat: Lattice, U_fund: torch.Tensor, precs=("f64", "f32"),
+                 stored: bool = True, rebuild: bool = False, stream=None):
+        assert U_fund.is_cuda and U_fund.dtype == torch.complex128
+        assert U_fund.numel() == lat.volume * 4 * lat.N * lat.N
+        self.lat = lat
+        self._desc = lat.desc()
+        self.handle = ctypes.c_void_p(0)
+        modes = (1 << LINKS_STORED if stored else 0) | (1 << LINKS_REBUILD if rebuild else 0)
+        _check(load().hr_represent_gauge(ctypes.byref(self._desc), _ptr(U_fund.contiguous()),
+                                         _prec_mask(precs), modes, _stream(stream),
+                                         ctypes.byref(self.handle)))
+
+    def update(self, U_fund, stream=None):
+        _check(load().hr_gauge_update(self.handle, _ptr(U_fund.contiguous()), _stream(stream)))
+
+    def set_link_mode(self, mode: int):
+        _check(load().hr_gauge_set_link_mode(self.handle, mode))
+
+    def close(self):
+        if self.handle and self.handle.value:
+            load().hr_gauge_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, parity: int, prec: int, x, out=None, nrhs: int = 1, dagger: bool = False,
+              stream=None):
+        out_par = EVEN if parity == EO_PRECOND else parity
+        if out is None:
+            ns = self.lat.nsites(FULL if parity == FULL else EVEN)
+            if prec in (F64, F32):
+                out = torch.empty_like(x)
+            else:
+                out = torch.empty(field_bytes(self.lat, out_par if parity != FULL else FULL, prec, nrhs),
+                                  dtype=torch.uint8, device=x.device)
+        f = load().hr_dirac_dagger if dagger else load().hr_dirac_apply
+        _check(f(self.handle, parity, prec, _ptr(x), _ptr(out), nrhs, _stream(stream)))
+        return out
+
+    def cg_solve(self, sys: int, b, x=None, nrhs: int = 1, tol: float = 1e-10,
+                 max_iter: int = 10000, inner: int = F64, inner_tol: float = 1e-5,
+                 use_initial_guess: bool = False, stream=None, check: bool = True):
+        if x is None:
+            x = torch.zeros_like(b)
+        p = CgParams(tol, max_iter, inner, inner_tol, int(use_initial_guess))
+        res = (CgResult * nrhs)()
+        st = load().hr_cg_solve(self.handle, sys, _ptr(b), _ptr(x), nrhs, ctypes.byref(p), res,
+                                _stream(stream))
+        if check:
+            _check(st)
+        out = [dict(iters=r.iters, outer_iters=r.outer_iters, true_rel_residual=r.true_rel_residual,
+                    status=STATUS.get(r.status, r.status)) for r in res]
+        return x, out, st
+
+    def force(self, sys: int, X, Y, coeff: float = 1.0, F=None, stream=None):
+        if F is None:
+            F = torch.zeros((self.lat.volume, 4, self.lat.N ** 2 - 1), dtype=torch.float64,
+                            device=X.device)
+        _check(load().hr_dirac_force(self.handle, sys, _ptr(X), _ptr(Y), coeff, _ptr(F),
+                                     _stream(stream)))
+        return F
+
+
+def cg_solve_batched(gauges, sys: int, bs, xs, nrhs, tol=1e-10, max_iter=10000, inner=F32,
+                     inner_tol=1e-5, stream=None, check=True):
+    n = len(gauges)
+    P = ctypes.c_void_p
+    g_arr = (P * n)(*[g.handle.value for g in gauges])
+    b_arr = (P * n)(*[b.data_ptr() for b in bs])
+    x_arr = (P * n)(*[x.data_ptr() for x in xs])
+    n_arr = (ctypes.c_int * n)(*nrhs)
+    p = CgParams(tol, max_iter, inner, inner_tol, 0)
+    res = (CgResult * sum(nrhs))()
+    st = load().hr_cg_solve_batched(n, g_arr, sys, b_arr, x_arr, n_arr, ctypes.byref(p), res,
+                                    _stream(stream))
+    if check:
+        _check(st)
+    return [dict(iters=r.iters, outer_iters=r.outer_iters, true_rel_residual=r.true_rel_residual,
+                 status=STATUS.get(r.status, r.status)) for r in res], st

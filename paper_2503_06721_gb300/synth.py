@@ -101,6 +101,34 @@ def gaussian_hermitian(count: int, N: int, seed: int, stream: int, device="cpu")
     return H - tr[:, None, None] * torch.eye(N, dtype=H.dtype, device=device)
 
 
+def expm_small(A: torch.Tensor, squarings: int = 6, order: int = 12) -> torch.Tensor:
+    """exp(A) for a batch of small matrices: scaling and squaring with a
+    truncated Taylor series (batched matmuls only, fast on any device)."""
+    B = A * (1.0 / (1 << squarings))
+    eye = torch.eye(A.shape[-1], dtype=A.dtype, device=A.device).expand_as(A)
+    # Horner: I + B (I + B/2 (I + B/3 (...)))
+    acc = eye.clone()
+    for k in range(order, 0, -1):
+        acc = eye + (B @ acc) * (1.0 / k)
+    for _ in range(squarings):
+        acc = acc @ acc
+    return acc
+
+
+def det_small(M: torch.Tensor) -> torch.Tensor:
+    """determinant of a batch of N x N matrices (N <= 4) by cofactor expansion."""
+    n = M.shape[-1]
+    if n == 1:
+        return M[..., 0, 0]
+    if n == 2:
+        return M[..., 0, 0] * M[..., 1, 1] - M[..., 0, 1] * M[..., 1, 0]
+    d = torch.zeros(M.shape[:-2], dtype=M.dtype, device=M.device)
+    for j in range(n):
+        minor = torch.cat([M[..., 1:, :j], M[..., 1:, j + 1:]], dim=-1)
+        d = d + ((-1) ** j) * M[..., 0, j] * det_small(minor)
+    return d
+
+
 def random_links(volume: int, N: int, eps: float, seed: int, device="cpu",
                  chunk: int = 1 << 21) -> torch.Tensor:
     """Gauge field U[V, 4, N, N] = exp(i eps H), complex128."""
@@ -116,7 +144,7 @@ def random_links(volume: int, N: int, eps: float, seed: int, device="cpu",
         H = 0.5 * (G + G.conj().transpose(-1, -2))
         tr = torch.diagonal(H, dim1=-2, dim2=-1).sum(-1) / N
         H = H - tr[:, None, None] * torch.eye(N, dtype=H.dtype, device=device)
-        out[s:e] = torch.linalg.matrix_exp(1j * eps * H)
+        out[s:e] = expm_small(1j * eps * H)
     return out.reshape(volume, 4, N, N)
 
 
@@ -143,10 +171,17 @@ def haar_su_n(count: int, N: int, seed: int, stream: int = STREAM_GAUGE_TRANSFOR
     """count Haar-random SU(N) matrices."""
     g = normals(count * N * N * 2, seed, stream, device).reshape(count, N, N, 2)
     Z = torch.complex(g[..., 0], g[..., 1]) * math.sqrt(0.5)
-    Q, R = torch.linalg.qr(Z)
-    d = torch.diagonal(R, dim1=-2, dim2=-1)
-    Q = Q * (d / d.abs())[:, None, :]
-    det = torch.linalg.det(Q)
+    # Gram-Schmidt on the columns = QR with a positive real diagonal of R,
+    # which is the phase fix that makes Q Haar-distributed in U(N)
+    cols = []
+    for j in range(N):
+        v = Z[:, :, j]
+        for q in cols:
+            v = v - (q.conj() * v).sum(-1, keepdim=True) * q
+        v = v / torch.sqrt((v.conj() * v).real.sum(-1, keepdim=True))
+        cols.append(v)
+    Q = torch.stack(cols, dim=-1)
+    det = det_small(Q)
     phase = torch.exp(-1j * torch.angle(det) / N)
     return Q * phase[:, None, None]
 

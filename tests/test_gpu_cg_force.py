@@ -1,0 +1,145 @@
+"""GPU parity of the CG solver (plain FP64 and FP64 defect correction around
+FP32 / F16 / BF16 inner solves) and of the fermion force, against the oracle.
+
+Solver checks use what is unique: the oracle recomputes the true residual
+|b - A x_gpu| / |b| of the GPU solution, which must meet the requested
+tolerance, and the GPU solution must agree with the oracle's own CG solution
+within the conditioning bound of the two residuals."""
+import numpy as np
+import pytest
+import torch
+
+from tests import _helpers as H
+from tests import gpu_common as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hr():
+    from paper_2503_06721_gb300 import build, hr
+    build.build()
+    hr.load()
+    return hr
+
+
+def _normal_apply(oracle_mod, L, UR, sys, x):
+    if sys == 2:   # FULL, library layout
+        full = G.from_eo_full(oracle_mod, L, x)
+        y = oracle_mod.dirac_full(L, UR, oracle_mod.dirac_full(L, UR, full), dagger=True)
+        return G.eo_full(oracle_mod, L, y)
+    return oracle_mod.dhat(L, UR, oracle_mod.dhat(L, UR, x), dagger=True)
+
+
+# the 8^4 SU(2) adjoint correctness configuration: m0 = -0.2, links exp(i 0.3 H),
+# antiperiodic in time
+CFG1 = dict(N=2, rep="ADJ", dims=(8, 8, 8, 8), m0=-0.2, eps=0.3, seed=2503067211)
+
+
+@pytest.fixture(scope="module")
+def cfg1(hr, oracle_mod):
+    c = CFG1
+    lat = hr.Lattice(c["N"], c["rep"], c["dims"], (-1, 1, 1, 1), c["m0"])
+    L = oracle_mod.lat(c["N"], c["rep"], c["dims"], (-1, 1, 1, 1), c["m0"])
+    from paper_2503_06721_gb300 import synth
+    UF = synth.random_links(lat.volume, c["N"], c["eps"], c["seed"]).numpy()
+    UR = oracle_mod.represent_field(L, UF)
+    g = hr.Gauge(lat, G.to_gpu(UF), precs=("f64", "f32", "f16", "bf16"), stored=True, rebuild=True)
+    return lat, L, UF, UR, g
+
+
+@pytest.mark.parametrize("sys", [3, 2], ids=["eo", "full"])
+@pytest.mark.parametrize("inner", [0, 1, 2, 3], ids=["f64", "f32", "f16", "bf16"])
+def test_cg_cfg1(hr, oracle_mod, cfg1, sys, inner):
+    lat, L, UF, UR, g = cfg1
+    ns = lat.nsites(sys if sys == hr.FULL else hr.EVEN)
+    b = H.spinor(ns, lat.D, 17)
+    tol = 1e-10
+    x, res, st = g.cg_solve(sys, G.to_gpu(b), tol=tol, max_iter=5000, inner=inner, inner_tol=1e-4)
+    assert st == 0, res
+    xs = x.cpu().numpy()
+    r = b - _normal_apply(oracle_mod, L, UR, sys, xs)
+    true_rel = np.linalg.norm(r) / np.linalg.norm(b)
+    assert true_rel <= tol * 1.001, true_rel
+    assert abs(res[0]["true_rel_residual"] - true_rel) <= 0.05 * true_rel + 1e-15
+    # oracle solution for the same system (Hestenes-Stiefel CG, Neumaier sums)
+    if sys == hr.FULL:
+        bo = G.from_eo_full(oracle_mod, L, b)
+        xo, ok, it, rr = oracle_mod.cg(L, UR, 0, bo, tol=1e-12)
+        xo = G.eo_full(oracle_mod, L, xo)
+    else:
+        xo, ok, it, rr = oracle_mod.cg(L, UR, 1, b, tol=1e-12)
+    assert ok
+    assert np.linalg.norm(xs - xo) / np.linalg.norm(xo) < 1e-6
+    if inner == 0:
+        # plain FP64 CG takes about as many iterations as the oracle's at the same tolerance
+        if sys == hr.FULL:
+            _, _, it, _ = oracle_mod.cg(L, UR, 0, G.from_eo_full(oracle_mod, L, b), tol=tol)
+        else:
+            _, _, it, _ = oracle_mod.cg(L, UR, 1, b, tol=tol)
+        assert abs(res[0]["iters"] - it) <= 0.05 * it + 2
+
+
+def test_cfg1_one_apply_and_50_iterations(hr, oracle_mod, cfg1):
+    """The correctness configuration as stated: one D_w apply plus 50 CG
+    iterations on D^dag D; the 50-iteration iterate matches the oracle's."""
+    lat, L, UF, UR, g = cfg1
+    V = lat.volume
+    psi = H.spinor(V, lat.D, 19)
+    y = g.apply(hr.FULL, hr.F64, G.to_gpu(G.eo_full(oracle_mod, L, psi)))
+    want = G.eo_full(oracle_mod, L, oracle_mod.dirac_full(L, UR, psi))
+    assert G.rel(y.cpu().numpy(), want) <= 1e-13
+    b = G.eo_full(oracle_mod, L, psi)
+    x, res, st = g.cg_solve(hr.FULL, G.to_gpu(b), tol=1e-30, max_iter=50, check=False)
+    assert res[0]["iters"] == 50 and st == -4
+    xo, ok, it, rr = oracle_mod.cg(L, UR, 0, G.from_eo_full(oracle_mod, L, b), tol=1e-30, max_iter=50)
+    assert it == 50
+    assert G.rel(x.cpu().numpy(), G.eo_full(oracle_mod, L, xo)) < 1e-9
+
+
+def test_cg_multi_rhs_and_zero_rhs(hr, oracle_mod, cfg1):
+    lat, L, UF, UR, g = cfg1
+    b = H.spinor(lat.volume // 2, lat.D, 23, nrhs=3)
+    b[1] = 0.0   # an all-zero right-hand side converges at once with x = 0
+    x, res, st = g.cg_solve(hr.EO_PRECOND, G.to_gpu(b), nrhs=3, tol=1e-10, inner=hr.F32)
+    assert st == 0
+    xs = x.cpu().numpy()
+    assert np.abs(xs[1]).max() == 0
+    for k in (0, 2):
+        r = b[k] - _normal_apply(oracle_mod, L, UR, 3, xs[k])
+        assert np.linalg.norm(r) / np.linalg.norm(b[k]) <= 1e-10 * 1.001
+
+
+def test_cg_not_converged_and_nonfinite(hr, oracle_mod, cfg1):
+    lat, L, UF, UR, g = cfg1
+    b = H.spinor(lat.volume // 2, lat.D, 29)
+    x, res, st = g.cg_solve(hr.EO_PRECOND, G.to_gpu(b), tol=1e-10, max_iter=3, check=False)
+    assert st == -4 and res[0]["status"] == "HR_ERR_NOT_CONVERGED"
+    b[5, 1, 0] = np.nan
+    x, res, st = g.cg_solve(hr.EO_PRECOND, G.to_gpu(b), tol=1e-10, check=False)
+    assert st == -5
+
+
+@pytest.mark.parametrize("N,rep", [(3, "SYM"), (2, "ADJ"), (4, "ASYM"), (3, "FUND")])
+def test_force_parity(hr, oracle_mod, N, rep):
+    dims = (4, 4, 2, 6)
+    lat = hr.Lattice(N, rep, dims, (-1, 1, 1, 1), -0.1)
+    L = oracle_mod.lat(N, rep, dims, (-1, 1, 1, 1), -0.1)
+    UF = H.links(dims, N, 0.6, seed=37)
+    UR = oracle_mod.represent_field(L, UF)
+    g = hr.Gauge(lat, G.to_gpu(UF), precs=("f64",))
+    V = lat.volume
+    X = H.spinor(V, lat.D, 41)
+    Y = H.spinor(V, lat.D, 43)
+    Fo = oracle_mod.force(L, UR, X, Y)
+    F = g.force(hr.FULL, G.to_gpu(G.eo_full(oracle_mod, L, X)), G.to_gpu(G.eo_full(oracle_mod, L, Y)),
+                coeff=1.0)
+    np.testing.assert_allclose(F.cpu().numpy(), Fo, atol=1e-12 * np.abs(Fo).max())
+    # even/odd system: S = -2 Re <Y_e, Dhat X_e>  ->  minus the full formula on
+    # X' = (X_e, D_oe X_e), Y' = (Y_e, (D^dag)_oe Y_e)
+    Xe, Ye = X[: V // 2], Y[: V // 2]
+    Xp = oracle_mod.merge(L, Xe, oracle_mod.hop_parity(L, UR, 1, Xe))
+    Yp = oracle_mod.merge(L, Ye, oracle_mod.hop_parity(L, UR, 1, Ye, dagger=True))
+    Fo = -oracle_mod.force(L, UR, Xp, Yp)
+    F = g.force(hr.EO_PRECOND, G.to_gpu(Xe), G.to_gpu(Ye), coeff=2.0)
+    np.testing.assert_allclose(F.cpu().numpy(), 2.0 * Fo, atol=1e-12 * np.abs(Fo).max())

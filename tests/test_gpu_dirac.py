@@ -1,0 +1,132 @@
+"""GPU parity of the Wilson-Dirac operator against the FP64 oracle, through
+the C ABI: represent (stored and in-kernel rebuilt links), D_eo / D_oe, the
+full D_m, the even/odd preconditioned Dhat and all their adjoints, in every
+compiled (N, representation) pair and storage precision, on lattices whose
+half volume spans several 32-site tiles and ends in a ragged tail."""
+import numpy as np
+import pytest
+import torch
+
+from tests import _helpers as H
+from tests import gpu_common as G
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (6, 4, 2, 6)   # V = 288, V/2 = 144 = 4.5 tiles of 32
+
+
+@pytest.fixture(scope="module")
+def hr():
+    from paper_2503_06721_gb300 import build, hr
+    build.build()
+    hr.load()
+    return hr
+
+
+def _setup(hr, oracle_mod, N, rep, dims=DIMS, m0=-0.23, eps=0.7, bc=(-1, 1, 1, -1), seed=5,
+           precs=("f64", "f32", "f16", "bf16")):
+    lat = hr.Lattice(N, rep, dims, bc, m0)
+    L = oracle_mod.lat(N, rep, dims, bc, m0)
+    UF = H.links(dims, N, eps, seed=seed)
+    g = hr.Gauge(lat, G.to_gpu(UF), precs=precs, stored=True, rebuild=True)
+    UR = oracle_mod.represent_field(L, UF)
+    return lat, L, UF, UR, g
+
+
+def _oracle_apply(oracle_mod, L, UR, par, x_host, dagger):
+    """oracle for each hr_parity selector, on library-layout host fields."""
+    if par in (0, 1):
+        return oracle_mod.hop_parity(L, UR, par, x_host, dagger)
+    if par == 2:
+        full = G.from_eo_full(oracle_mod, L, x_host)
+        return G.eo_full(oracle_mod, L, oracle_mod.dirac_full(L, UR, full, dagger))
+    return oracle_mod.dhat(L, UR, x_host, dagger)
+
+
+@pytest.mark.parametrize("N,rep", G.PAIRS)
+@pytest.mark.parametrize("prec", [0, 1, 2, 3], ids=["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("mode", [0, 1], ids=["stored", "rebuild"])
+def test_operator_parity(hr, oracle_mod, N, rep, prec, mode):
+    lat, L, UF, UR, g = _setup(hr, oracle_mod, N, rep)
+    g.set_link_mode(mode)
+    D = lat.D
+    V = lat.volume
+    psi = H.spinor(V, D, 7)
+    half = psi[: V // 2]
+    for par in (hr.EVEN, hr.ODD, hr.FULL, hr.EO_PRECOND):
+        x = G.to_gpu(psi if par == hr.FULL else half)
+        in_par = hr.FULL if par == hr.FULL else hr.EVEN
+        xin = G.prec_fields(hr, lat, in_par, x, prec)
+        xh = G.oracle_input(hr, lat, in_par, x, prec)
+        for dagger in (False, True):
+            y = g.apply(par, prec, xin, dagger=dagger)
+            torch.cuda.synchronize()
+            got = G.back_to_f64(hr, lat, in_par, y, prec).cpu().numpy()
+            want = _oracle_apply(oracle_mod, L, UR, par, xh, dagger)
+            err = G.rel(got, want)
+            assert err <= G.TOL[prec], (par, dagger, err)
+    g.close()
+
+
+def test_rebuild_equals_stored_f64(hr, oracle_mod):
+    lat, L, UF, UR, g = _setup(hr, oracle_mod, 3, "ADJ", dims=(4, 4, 4, 8))
+    x = G.to_gpu(H.spinor(lat.volume // 2, lat.D, 9))
+    a = g.apply(hr.EVEN, hr.F64, x)
+    g.set_link_mode(hr.LINKS_REBUILD)
+    b = g.apply(hr.EVEN, hr.F64, x)
+    assert G.rel(b.cpu().numpy(), a.cpu().numpy()) < 1e-14
+
+
+def test_free_field_plane_wave_gpu(hr, oracle_mod):
+    """U = 1: D psi = [m + sum(1 - cos p) + i sum gamma sin p] psi on the GPU too."""
+    dims = (8, 4, 4, 6)
+    N, rep, m0 = 3, "SYM", -0.37
+    lat = hr.Lattice(N, rep, dims, (-1, 1, 1, 1), m0)
+    L = oracle_mod.lat(N, rep, dims, (-1, 1, 1, 1), m0)
+    g = hr.Gauge(lat, G.to_gpu(H.unit_links(dims, N)), precs=("f64",))
+    x = H.coords(dims)
+    p = np.array([3 * np.pi / 8, 2 * np.pi / 4, 0.0, 2 * np.pi / 6])
+    gam = [oracle_mod.gamma(mu) for mu in range(4)]
+    chi = (np.arange(24).reshape(4, 6) + 1j * np.arange(24)[::-1].reshape(4, 6)) / 10
+    psi = np.exp(1j * x @ p)[:, None, None] * chi[None]
+    Dp = (m0 + np.sum(1 - np.cos(p))) * np.eye(4) + 1j * sum(gam[mu] * np.sin(p[mu]) for mu in range(4))
+    want = np.exp(1j * x @ p)[:, None, None] * (Dp @ chi)[None]
+    y = g.apply(hr.FULL, hr.F64, G.to_gpu(G.eo_full(oracle_mod, L, psi)))
+    got = G.from_eo_full(oracle_mod, L, y.cpu().numpy())
+    assert np.abs(got - want).max() < 1e-13
+
+
+def test_multi_rhs_apply(hr, oracle_mod):
+    lat, L, UF, UR, g = _setup(hr, oracle_mod, 4, "ASYM", precs=("f64", "f32"))
+    nrhs = 3
+    xs = H.spinor(lat.volume // 2, lat.D, 11, nrhs=nrhs)
+    for prec, dt in ((hr.F64, torch.complex128), (hr.F32, torch.complex64)):
+        x = G.to_gpu(xs, dt)
+        y = g.apply(hr.EO_PRECOND, prec, x, nrhs=nrhs).to(torch.complex128).cpu().numpy()
+        for k in range(nrhs):
+            xin = xs[k].astype(np.complex64 if prec == hr.F32 else np.complex128).astype(np.complex128)
+            assert G.rel(y[k], oracle_mod.dhat(L, UR, xin)) <= G.TOL[prec]
+
+
+def test_field_dot_and_convert(hr, oracle_mod):
+    lat = hr.Lattice(3, "SYM", DIMS)
+    a = H.spinor(lat.volume // 2, lat.D, 13, nrhs=2)
+    ga = G.to_gpu(a)
+    d = hr.field_dot(lat, hr.EVEN, hr.F64, ga, ga.flip(0).contiguous(), nrhs=2)
+    for k in range(2):
+        want = np.vdot(a[k].ravel(), a[1 - k].ravel())
+        assert abs(d[k] - want) <= 1e-13 * abs(want)
+    # F16 round trip keeps every component within half an ulp of its site scale
+    h = hr.field_convert(lat, hr.EVEN, ga, hr.F64, hr.F16, 2)
+    back = G.back_to_f64(hr, lat, hr.EVEN, h, hr.F16, 2).cpu().numpy()
+    scale = np.abs(np.stack([a.real, a.imag])).max(axis=(0, 3, 4))
+    err = np.maximum(np.abs(back.real - a.real), np.abs(back.imag - a.imag)).max(axis=(2, 3))
+    assert (err <= scale * 2.0 ** -11 * 1.0001).all()
+
+
+def test_invalid_precision_rejected(hr, oracle_mod):
+    lat, L, UF, UR, g = _setup(hr, oracle_mod, 3, "SYM", precs=("f64",))
+    x = G.to_gpu(H.spinor(lat.volume // 2, lat.D, 3)).to(torch.complex64)
+    with pytest.raises(hr.HrError) as e:
+        g.apply(hr.EVEN, hr.F32, x)
+    assert e.value.status == -1

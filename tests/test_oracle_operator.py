@@ -204,3 +204,21 @@ def test_antiperiodic_sign_slice(oracle_mod):
     for mu in range(4):
         sign = np.where((t == 3) & (mu == 0), -1.0, 1.0)
         np.testing.assert_allclose(UR[:, mu, 0, 0].real, sign)
+
+
+@pytest.mark.parametrize("N,rep", [(3, "SYM"), (2, "ADJ"), (4, "ASYM")])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_hop_sites_matches_full(oracle_mod, N, rep, dagger):
+    """The sampled-site evaluator reproduces the whole-lattice hopping block."""
+    dims = (4, 2, 4, 6)
+    L = oracle_mod.lat(N, rep, dims, (-1, 1, 1, -1), 0.1)
+    D = oracle_mod.rep_dim(N, rep)
+    V = int(np.prod(dims))
+    UF = H.links(dims, N, 0.7, seed=81)
+    UR = oracle_mod.represent_field(L, UF)
+    psi = H.spinor(V // 2, D, 83)
+    for p in (0, 1):
+        full = oracle_mod.hop_parity(L, UR, p, psi, dagger)
+        sites = np.arange(V // 2)[::3]
+        np.testing.assert_allclose(oracle_mod.hop_sites(L, UF, p, psi, sites, dagger), full[sites],
+                                   atol=1e-14)
