@@ -98,6 +98,7 @@ def _load():
             "or_force": (None, [LP, P, P, P, P]),
             "or_num_threads": (I, []),
             "or_hop_sites": (None, [LP, P, I, P, P, ctypes.c_long, P, I]),
+            "or_hop_local": (None, [LP, P, P, P, P, I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -206,6 +207,22 @@ def hop_sites(L: Lat, UF, out_parity: int, in_half, sites, dagger: bool = False)
     out = np.zeros((len(sites), 4, D), np.complex128)
     _load().or_hop_sites(ctypes.byref(L), _p(UF), int(out_parity), _p(in_half), _p(sites),
                          len(sites), _p(out), int(dagger))
+    return out
+
+
+def hop_local(L: Lat, coords, Ulinks, psi, dagger: bool = False) -> np.ndarray:
+    """Hopping term at output sites from gathered data: coords[n, 4] (t,x,y,z),
+    Ulinks[n, 8, N, N] fundamental links U(x,mu) / U(x-mu,mu), psi[n, 8, 4, D]
+    neighbour spinors.  Returns [n, 4, D]."""
+    coords = np.ascontiguousarray(coords, dtype=np.int32)
+    Ulinks, psi = _c(Ulinks), _c(psi)
+    D = rep_dim(L.N, L.rep)
+    n = coords.shape[0]
+    out = np.zeros((n, 4, D), np.complex128)
+    f = _load().or_hop_local
+    for k in range(n):
+        f(ctypes.byref(L), coords[k].ctypes.data_as(ctypes.c_void_p), _p(Ulinks[k]), _p(psi[k]),
+          out[k].ctypes.data_as(ctypes.c_void_p), int(dagger))
     return out
 
 

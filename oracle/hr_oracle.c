@@ -476,6 +476,38 @@ void or_hop_sites(const or_lat *L, const orc *UF, int out_parity,
     }
 }
 
+void or_hop_local(const or_lat *L, const int c[4], const orc *Ulinks,
+                  const orc *psi, orc *out, int dagger)
+{
+    int N = L->N, D = or_rep_dim(L->N, L->rep);
+    orc gam[4][16];
+    load_gammas(gam);
+    double sg = dagger ? -1.0 : 1.0;
+    orc R[OR_MAXD * OR_MAXD], chi[4 * OR_MAXD];
+    for (int q = 0; q < 4 * D; q++) out[q] = 0;
+    for (int k = 0; k < 8; k++) {
+        int mu = k & 3, dir = k < 4 ? +1 : -1;
+        or_represent_link(N, L->rep, Ulinks + (size_t)k * N * N, R);
+        int cown = dir > 0 ? c[mu] : (c[mu] - 1 + L->dims[mu]) % L->dims[mu];
+        double sign = (L->bc[mu] == -1 && cown == L->dims[mu] - 1) ? -1.0 : 1.0;
+        const orc *p = psi + (size_t)k * 4 * D;
+        for (int s = 0; s < 4; s++)
+            for (int r = 0; r < D; r++) {
+                orc v = 0;
+                for (int cc = 0; cc < D; cc++)
+                    v += (dir > 0 ? R[r * D + cc] : conj(R[cc * D + r])) * p[s * D + cc];
+                chi[s * D + r] = sign * v;
+            }
+        double pm = -(double)dir * sg;
+        for (int s = 0; s < 4; s++)
+            for (int r = 0; r < D; r++) {
+                orc v = chi[s * D + r];
+                for (int t = 0; t < 4; t++) v += pm * gam[mu][s * 4 + t] * chi[t * D + r];
+                out[s * D + r] += -0.5 * v;
+            }
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* Sec. 4.1.1: compensated summation                                     */
 /* ------------------------------------------------------------------ */

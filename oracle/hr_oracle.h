@@ -88,6 +88,16 @@ void or_hop_sites(const or_lat *L, const orc *UF, int out_parity,
                   const orc *in_half, const long *sites, long nsites,
                   orc *out, int dagger);
 
+/* One output site from gathered data, for lattices too large to hold on the
+ * host: c = coordinates (t,x,y,z) of the output site x; Ulinks[8][N][N] the
+ * FUNDAMENTAL links U(x, mu) (k = mu < 4) and U(x - mu, mu) (k = 4 + mu);
+ * psi[8][4][D] the neighbour spinors psi(x + mu) (k < 4), psi(x - mu) (k >= 4).
+ * out[4][D] = -1/2 sum_mu [ (1 -+ g_mu) U_R(x,mu) psi(x+mu)
+ *                         + (1 +- g_mu) U_R(x-mu,mu)^dag psi(x-mu) ]
+ * with the boundary signs of or_represent_field; lower signs for dagger. */
+void or_hop_local(const or_lat *L, const int c[4], const orc *Ulinks,
+                  const orc *psi, orc *out, int dagger);
+
 /* ---- reductions (Sec. 4.1.1, Algorithms FastTwoSum .. DoubleDoubleSum) ---- */
 void   or_fast_two_sum(double a, double b, double *s, double *c);
 double or_sum_naive(const double *a, long n);

@@ -198,6 +198,32 @@ size_t scratch_bytes(int nrhs, long max_blocks)
            align_up(sizeof(double) * 2 * nrhs * (size_t)max_blocks, 256);
 }
 
+hr_status scratch_reserve(const hr_gauge *cg, int nrhs, cudaStream_t stream, Scratch *out)
+{
+    hr_gauge *g = const_cast<hr_gauge *>(cg);
+    const long mb = max_blocks_for(g);
+    const size_t need = scratch_bytes(nrhs, mb);
+    if (g->scr_bytes < need) {
+        if (g->scr) {
+            HR_CUDA_CHECK(cudaStreamSynchronize(stream));
+            HR_CUDA_CHECK(cudaDeviceSynchronize());
+            HR_CUDA_CHECK(cudaFree(g->scr));
+            g->scr = nullptr;
+            g->scr_bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&g->scr, need);
+        if (e != cudaSuccess) {
+            g->scr = nullptr;
+            return cuda_fail(e, "scratch cudaMalloc");
+        }
+        HR_CUDA_CHECK(cudaMemsetAsync(g->scr, 0, need, stream));
+        g->scr_bytes = need;
+    }
+    char *p = g->scr;
+    *out = carve_scratch(p, nrhs, mb);
+    return HR_OK;
+}
+
 long max_blocks_for(const hr_gauge *g)
 {
     const long V = 2 * g->geom.vh;
@@ -390,6 +416,7 @@ hr_status hr_gauge_destroy(hr_gauge *g)
         }
     if (g->TR) cudaFree(g->TR);
     if (g->ws) cudaFree(g->ws);
+    if (g->scr) cudaFree(g->scr);
     if (g->pinned) cudaFreeHost(g->pinned);
     delete g;
     return HR_OK;

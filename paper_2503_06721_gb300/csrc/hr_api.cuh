@@ -29,6 +29,8 @@ hr_status ws_reserve(const hr_gauge *g, size_t bytes, cudaStream_t stream);
 Scratch carve_scratch(char *&p, int nrhs, long max_blocks);
 size_t scratch_bytes(int nrhs, long max_blocks);
 long max_blocks_for(const hr_gauge *g);
+// the handle's reduction scratch for nrhs right-hand sides (grown and zeroed on demand)
+hr_status scratch_reserve(const hr_gauge *g, int nrhs, cudaStream_t stream, Scratch *out);
 
 hr_status hop(const hr_gauge *g, int P, int out_parity, int dagger, const FieldView &in, const FieldView &out,
               const FieldView *diag, double a, double b, int nrhs, cudaStream_t stream, int epi,

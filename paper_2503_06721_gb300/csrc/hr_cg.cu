@@ -156,6 +156,14 @@ hr_status true_residual(const Ctx &c, const FieldView &b, const FieldView &x, co
 
 constexpr int CHECK_EVERY = 8;
 
+// |r| / |b| from the squared norms; NaN whenever either is not finite, and
+// 0 for b = 0 (then x = 0 is exact)
+double rel_residual(double rr, double b2)
+{
+    if (!std::isfinite(rr) || !std::isfinite(b2)) return NAN;
+    return b2 > 0 ? std::sqrt(rr / b2) : 0.0;
+}
+
 // run CG iterations until every rhs converged or the budget is used up
 hr_status run_iterations(const Ctx &c, const Vecs &v, int budget, std::vector<CgState> &stt, int *done_iters)
 {
@@ -199,11 +207,11 @@ hr_status cg_solve_impl(const hr_gauge *g, hr_parity sys, const void *b, void *x
     const bool mixed = prm->inner != HR_F64;
     const int Pin = prm->inner;
 
-    // workspace: scratch | r64 | q64 | q2_64 | t64 | [r32 | x32 | pP | qP | tP]
-    const long mb = max_blocks_for(g);
+    // field workspace: r64 | q64 | q2_64 | t64 | [p64] | [r32 | x32 | pP | qP | tP];
+    // reductions and solver state live in the separate scratch buffer
     const size_t f64 = field_rhs_bytes(c.ns, D, HR_F64) * nrhs;
     const size_t t64 = field_rhs_bytes(c.vh, D, HR_F64) * nrhs;
-    size_t need = scratch_bytes(nrhs, mb) + 3 * f64 + t64 + 4096;
+    size_t need = 3 * f64 + t64 + 4096;
     size_t f32 = 0, fP = 0, tP = 0;
     if (mixed) {
         f32 = field_rhs_bytes(c.ns, D, HR_F32) * nrhs;
@@ -215,8 +223,9 @@ hr_status cg_solve_impl(const hr_gauge *g, hr_parity sys, const void *b, void *x
     }
     hr_status st = ws_reserve(g, need, s);
     if (st != HR_OK) return st;
+    st = scratch_reserve(g, nrhs, s, &c.sc);
+    if (st != HR_OK) return st;
     char *p = g->ws;
-    c.sc = carve_scratch(p, nrhs, mb);
     c.sc_ns = c.sc;
     c.sc_ns.state = nullptr;
     auto take = [&](size_t bytes) { char *q = p; p += align_up(bytes, 256); return q; };
@@ -269,7 +278,7 @@ hr_status cg_solve_impl(const hr_gauge *g, hr_parity sys, const void *b, void *x
             if (st != HR_OK) return st;
             bool all_ok = true, any_bad = false;
             for (int k = 0; k < nrhs; k++) {
-                double rel = red[2 * k + 1] > 0 ? std::sqrt(red[2 * k] / red[2 * k + 1]) : 0.0;
+                double rel = rel_residual(red[2 * k], red[2 * k + 1]);
                 res[k].true_rel_residual = rel;
                 res[k].iters = iters[k];
                 if (!std::isfinite(rel)) any_bad = true;
@@ -296,7 +305,7 @@ hr_status cg_solve_impl(const hr_gauge *g, hr_parity sys, const void *b, void *x
             double worst = 0;
             for (int k = 0; k < nrhs; k++) {
                 const double rr = red[2 * k], b2 = red[2 * k + 1];
-                const double rel = b2 > 0 ? std::sqrt(rr / b2) : 0.0;
+                const double rel = rel_residual(rr, b2);
                 res[k].true_rel_residual = rel;
                 res[k].outer_iters = outer;
                 if (!std::isfinite(rel)) any_bad = true;

@@ -20,9 +20,13 @@ struct hr_gauge {
     size_t rep_bytes[4], fund_bytes[4];
     // T_R^a tables for the force, [(N*N-1)][D][D] complex double
     double *TR;
-    // solver workspace (grown on demand)
+    // field workspace (operator/force temporaries, solver vectors; grown on demand)
     char *ws;
     size_t ws_bytes;
+    // reduction tickets, partial sums and solver state -- kept apart from ws so
+    // that no field temporary ever overwrites the zeroed tickets
+    char *scr;
+    size_t scr_bytes;
     void *pinned;         // host staging for solver state (pinned)
     size_t pinned_bytes;
     int device;

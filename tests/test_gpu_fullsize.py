@@ -1,0 +1,166 @@
+"""Parity at the workloads' full sizes, in the launch configuration the
+benchmark times: sampled output sites are recomputed one by one by the
+oracle from gathered links and neighbour spinors, and whole-lattice
+identities (gamma5-hermiticity of Dhat, the solver's true residual) are
+checked with the library's own compensated dot products."""
+import gc
+
+import numpy as np
+import pytest
+import torch
+
+from tests import gpu_common as G
+
+pytestmark = pytest.mark.gpu
+
+NSAMPLE = 4096
+
+
+@pytest.fixture(scope="module")
+def hr():
+    from paper_2503_06721_gb300 import build, hr
+    build.build()
+    hr.load()
+    return hr
+
+
+def _free():
+    gc.collect()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
+def _sampled_check(hr, oracle_mod, wl, U, x_in, y_out, parity, dagger, tol, seed=0):
+    """compare y_out (half field of `parity`, any precision promoted to FP64)
+    with the oracle at NSAMPLE random sites; x_in is the input half field."""
+    T, X, Y, Z = wl.dims
+    V = T * X * Y * Z
+    dev = U.device
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    i = torch.randint(0, V // 2, (NSAMPLE,), generator=gen).to(dev)
+    # the site of parity `parity` with half index i is 2i or 2i+1
+    lex = 2 * i
+
+    def coords(l):
+        z = l % Z
+        y = (l // Z) % Y
+        x = (l // (Y * Z)) % X
+        t = l // (X * Y * Z)
+        return torch.stack([t, x, y, z], -1)
+
+    c = coords(lex)
+    lex = torch.where((c.sum(-1) & 1) == parity, lex, lex + 1)
+    c = coords(lex)
+    dims = torch.tensor(wl.dims, device=dev)
+    Ul = torch.empty((NSAMPLE, 8, wl.N, wl.N), dtype=torch.complex128, device=dev)
+    ps = torch.empty((NSAMPLE, 8) + tuple(x_in.shape[1:]), dtype=torch.complex128, device=dev)
+    for k in range(8):
+        mu, d = k & 3, (1 if k < 4 else -1)
+        cn = c.clone()
+        cn[:, mu] = (cn[:, mu] + d) % dims[mu]
+        nb = ((cn[:, 0] * X + cn[:, 1]) * Y + cn[:, 2]) * Z + cn[:, 3]
+        owner = lex if k < 4 else nb
+        Ul[:, k] = U[owner, mu]
+        ps[:, k] = x_in[nb // 2].to(torch.complex128)
+    L = oracle_mod.lat(wl.N, wl.rep, wl.dims, wl.bc, wl.m0)
+    ref = oracle_mod.hop_local(L, c.cpu().numpy(), Ul.cpu().numpy(), ps.cpu().numpy(), dagger)
+    got = y_out[i].to(torch.complex128).cpu().numpy()
+    err = G.rel(got, ref)
+    assert err <= tol, err
+    return err
+
+
+def _dhat_hermiticity(hr, lat, g, prec, dt, seed):
+    """<phi, Dhat psi> = <Dhat^dag phi, psi> on the whole lattice (any size)."""
+    from paper_2503_06721_gb300 import synth
+    vh = lat.volume // 2
+    phi = synth.gaussian_spinor(vh, lat.D, seed, device="cuda").to(dt)
+    psi = synth.gaussian_spinor(vh, lat.D, seed + 1, device="cuda").to(dt)
+    a = hr.field_dot(lat, hr.EVEN, prec, phi, g.apply(hr.EO_PRECOND, prec, psi))[0]
+    b = hr.field_dot(lat, hr.EVEN, prec, g.apply(hr.EO_PRECOND, prec, phi, dagger=True), psi)[0]
+    return abs(a - b) / abs(a)
+
+
+def test_sym_32x32x32x64_deo(hr, oracle_mod):
+    """SU(3) sextet 32^3 x 64: D_eo and D_oe (and adjoints) in FP64 and FP32."""
+    from paper_2503_06721_gb300 import synth
+    wl = synth.WORKLOADS["su3_sym_64x32x32x32"]
+    lat = hr.Lattice(wl.N, wl.rep, wl.dims, wl.bc, wl.m0)
+    U = wl.links(device="cuda")
+    g = hr.Gauge(lat, U, precs=("f64", "f32"), stored=True)
+    x = synth.gaussian_spinor(lat.volume // 2, lat.D, 5, device="cuda")
+    for prec, dt in ((hr.F64, torch.complex128), (hr.F32, torch.complex64)):
+        xin = x.to(dt)
+        for parity, dagger in ((0, False), (1, True)):
+            y = g.apply(parity, prec, xin, dagger=dagger)
+            _sampled_check(hr, oracle_mod, wl, U, xin, y, parity, dagger, G.TOL[prec], seed=parity)
+        rel = _dhat_hermiticity(hr, lat, g, prec, dt, 11)
+        assert rel < (1e-12 if prec == hr.F64 else 1e-5), rel
+    g.close()
+    del U, x
+    _free()
+
+
+def test_adj_64x64x64x128_stored_and_rebuilt(hr, oracle_mod):
+    """SU(3) adjoint 64^3 x 128 (FP32 spinors): D_eo with stored 8x8 links and
+    with links rebuilt in the kernel from the stored fundamental 3x3 links."""
+    from paper_2503_06721_gb300 import synth
+    wl = synth.WORKLOADS["su3_adj_128x64x64x64"]
+    lat = hr.Lattice(wl.N, wl.rep, wl.dims, wl.bc, wl.m0)
+    U = wl.links(device="cuda")
+    g = hr.Gauge(lat, U, precs=("f32",), stored=True, rebuild=True)
+    x = synth.gaussian_spinor(lat.volume // 2, lat.D, 7, device="cuda").to(torch.complex64)
+    for mode in (hr.LINKS_STORED, hr.LINKS_REBUILD):
+        g.set_link_mode(mode)
+        y = g.apply(hr.EVEN, hr.F32, x)
+        _sampled_check(hr, oracle_mod, wl, U, x, y, 0, False, G.TOL[hr.F32], seed=mode)
+        del y
+    g.close()
+    del U, x
+    _free()
+
+
+@pytest.mark.parametrize("name", ["su4_fund_48x24x24x24", "su4_asym_48x24x24x24"])
+def test_su4_24x24x24x48_deo(hr, oracle_mod, name):
+    from paper_2503_06721_gb300 import synth
+    wl = synth.WORKLOADS[name]
+    lat = hr.Lattice(wl.N, wl.rep, wl.dims, wl.bc, wl.m0)
+    U = wl.links(device="cuda")
+    g = hr.Gauge(lat, U, precs=("f32", "f16"), stored=True)
+    x = synth.gaussian_spinor(lat.volume // 2, lat.D, 9, device="cuda")
+    y = g.apply(hr.EVEN, hr.F32, x.to(torch.complex64))
+    _sampled_check(hr, oracle_mod, wl, U, x.to(torch.complex64), y, 0, False, G.TOL[hr.F32])
+    xh = hr.field_convert(lat, hr.EVEN, x, hr.F64, hr.F16)
+    yh = g.apply(hr.EVEN, hr.F16, xh)
+    x16 = G.back_to_f64(hr, lat, hr.EVEN, xh, hr.F16)
+    y16 = G.back_to_f64(hr, lat, hr.ODD, yh, hr.F16)
+    _sampled_check(hr, oracle_mod, wl, U, x16, y16, 0, False, G.TOL[hr.F16])
+    g.close()
+    del U, x
+    _free()
+
+
+def test_sym_32x32x32x64_mixed_cg(hr, oracle_mod):
+    """Mixed-precision (FP32 inner) CG on Dhat^dag Dhat reaches 1e-10; the true
+    residual is recomputed in FP64 by the library and cross-checked at sampled
+    sites of Dhat x by the oracle's hopping term."""
+    from paper_2503_06721_gb300 import synth
+    wl = synth.WORKLOADS["su3_sym_64x32x32x32"]
+    lat = hr.Lattice(wl.N, wl.rep, wl.dims, wl.bc, wl.m0)
+    U = wl.links(device="cuda")
+    g = hr.Gauge(lat, U, precs=("f64", "f32"), stored=True)
+    b = synth.gaussian_spinor(lat.volume // 2, lat.D, 13, device="cuda")
+    x, res, st = g.cg_solve(hr.EO_PRECOND, b, tol=1e-10, inner=hr.F32, inner_tol=1e-5)
+    assert st == 0 and res[0]["true_rel_residual"] <= 1e-10
+    # independent residual: A x - b with A applied hop by hop and |.| by field_dot
+    t = g.apply(hr.EO_PRECOND, hr.F64, x)
+    Ax = g.apply(hr.EO_PRECOND, hr.F64, t, dagger=True)
+    r = Ax - b
+    rr = hr.field_dot(lat, hr.EVEN, hr.F64, r, r)[0].real
+    bb = hr.field_dot(lat, hr.EVEN, hr.F64, b, b)[0].real
+    assert (rr / bb) ** 0.5 <= 1.01e-10
+    # the odd intermediate of Dhat x at sampled sites
+    xo = g.apply(hr.ODD, hr.F64, x)
+    _sampled_check(hr, oracle_mod, wl, U, x, xo, 1, False, G.TOL[hr.F64], seed=3)
+    g.close()
+    _free()

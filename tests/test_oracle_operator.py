@@ -222,3 +222,33 @@ def test_hop_sites_matches_full(oracle_mod, N, rep, dagger):
         sites = np.arange(V // 2)[::3]
         np.testing.assert_allclose(oracle_mod.hop_sites(L, UF, p, psi, sites, dagger), full[sites],
                                    atol=1e-14)
+
+
+def test_hop_local_matches_full(oracle_mod):
+    """The gathered-data single-site evaluator reproduces the hopping block."""
+    dims = (4, 2, 4, 6)
+    N, rep = 3, "SYM"
+    L = oracle_mod.lat(N, rep, dims, (-1, 1, -1, 1), 0.0)
+    D = oracle_mod.rep_dim(N, rep)
+    V = int(np.prod(dims))
+    UF = H.links(dims, N, 0.7, seed=91)
+    UR = oracle_mod.represent_field(L, UF)
+    psi = H.spinor(V, D, 93)
+    full = oracle_mod.dirac_full(L, UR, psi) - (4 + 0.0) * psi
+    xs = np.arange(0, V, 5)
+    coords = H.coords(dims)[xs]
+    Ul = np.zeros((len(xs), 8, N, N), np.complex128)
+    ps = np.zeros((len(xs), 8, 4, D), np.complex128)
+    for n, x in enumerate(xs):
+        for k in range(8):
+            mu = k & 3
+            nb = oracle_mod_neighbour(dims, x, mu, +1 if k < 4 else -1)
+            Ul[n, k] = UF[x if k < 4 else nb, mu]
+            ps[n, k] = psi[nb]
+    np.testing.assert_allclose(oracle_mod.hop_local(L, coords, Ul, ps), full[xs], atol=1e-14)
+
+
+def oracle_mod_neighbour(dims, lex, mu, d):
+    c = list(np.unravel_index(lex, dims))
+    c[mu] = (c[mu] + d) % dims[mu]
+    return int(np.ravel_multi_index(c, dims))
