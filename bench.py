@@ -383,6 +383,43 @@ def run_reference(args, rank, world):
     return out
 
 
+def run_deo(args, local_rank):
+    """D_eo applications only (for profiler captures): W untimed + K timed."""
+    import torch
+    from paper_2503_06721_gb300 import build, hr, synth
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    build.build()
+    wl = synth.WORKLOADS[args.workload]
+    lat = hr.Lattice(wl.N, wl.rep, wl.dims, wl.bc, wl.m0)
+    prec = {"f64": hr.F64, "f32": hr.F32, "f16": hr.F16, "bf16": hr.BF16}[args.prec]
+    g = hr.Gauge(lat, wl.links(device=dev), precs=(args.prec,), stored=not args.rebuild,
+                 rebuild=args.rebuild)
+    vh = lat.volume // 2
+    x = synth.gaussian_spinor(vh, lat.D, 3, device=dev)
+    x = x if prec == hr.F64 else (x.to(torch.complex64) if prec == hr.F32 else
+                                  hr.field_convert(lat, hr.EVEN, x, hr.F64, prec))
+    y = g.apply(hr.EVEN, prec, x)
+    for _ in range(args.warmup):
+        g.apply(hr.EVEN, prec, x, out=y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        g.apply(hr.EVEN, prec, x, out=y)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    if args.rebuild:
+        cb = [16, 8, 4, 4][prec]
+        byts = vh * (8 * wl.N * wl.N * cb + 2 * (4 * lat.D * cb + (4 if prec >= 2 else 0)))
+    else:
+        byts = hop_bytes(lat.D, wl.rep == "ADJ", prec, vh)
+    print(json.dumps({"mode": "deo", "workload": args.workload, "prec": args.prec,
+                      "links": "rebuild" if args.rebuild else "stored", "ms": round(ms, 4),
+                      "GBs": round(byts / (ms * 1e-3) / 1e9, 1), "bytes_per_launch": byts}))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -395,16 +432,22 @@ def main():
     ap.add_argument("--no-cg-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--mode", choices=["step", "deo"], default="step",
+                    help="deo: only D_eo applications (profiler captures)")
+    ap.add_argument("--prec", choices=["f64", "f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--rebuild", action="store_true", help="deo mode: rebuild links in-kernel")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per D_eo launch, when known for the current kernel")
     args = ap.parse_args()
-    if args.warmup < 3:
+    if args.warmup < 3 and args.mode == "step":
         ap.error("--warmup must be >= 3")
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.mode == "deo":
+        run_deo(args, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 
