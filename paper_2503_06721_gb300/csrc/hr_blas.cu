@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(BLAS_THREADS) k_residual_init(const BlasParams
             cs.nonfinite = !(isfinite(tot[0]) && isfinite(tot[1]));
             cs.converged = (tot[0] <= cs.stop2) || cs.nonfinite;
             cs.alpha = cs.beta = 0;
+            cs.cap = bp.cap;
         }
     }
 }
@@ -103,6 +104,7 @@ __global__ void __launch_bounds__(BLAS_THREADS) k_start_zero(const BlasParams bp
             cs.nonfinite = !isfinite(tot[0]);
             cs.converged = (tot[0] <= cs.stop2) || cs.nonfinite;
             cs.alpha = cs.beta = 0;
+            cs.cap = bp.cap;
         }
     }
 }
@@ -111,7 +113,7 @@ template <int D, int PP>
 __global__ void __launch_bounds__(BLAS_THREADS) k_xpay_beta(const BlasParams bp)
 {
     const int rhs = blockIdx.y;
-    if (bp.state[rhs].converged) return;
+    if (cg_idle(bp.state[rhs])) return;
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= bp.nsites) return;
     constexpr int PW = work_prec(PP);
@@ -168,6 +170,7 @@ __global__ void __launch_bounds__(BLAS_THREADS) k_inner_init(const BlasParams bp
         cs.nonfinite = !isfinite(tot[0]);
         cs.converged = (tot[0] <= cs.stop2) || cs.nonfinite || bp.sv[rhs] == 0.0;
         cs.alpha = cs.beta = 0;
+        cs.cap = bp.cap;
     }
 }
 

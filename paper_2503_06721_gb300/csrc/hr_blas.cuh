@@ -18,7 +18,7 @@ struct BlasParams {
     double *red_out;          // [nrhs][NV]
     CgState *state;           // [nrhs]
     double tol2;              // squared relative tolerance for state init
-    int skip_converged;
+    int cap;                  // iteration cap written into the state by init kernels
 };
 
 // a <- convert(b) * (sv ? sv[rhs] : s)            (any precisions)

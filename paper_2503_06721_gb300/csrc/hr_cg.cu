@@ -1,6 +1,7 @@
 // hr_cg.cu -- conjugate gradient on the normal equations (Sec. 4.1.2) with
 // even/odd preconditioning (Sec. 4.3.3), plain FP64 or as FP64 defect
-// correction around an inner CG in FP32 / FP16 / BF16.
+// correction around an inner CG in FP32 / FP16 / BF16, for one system or for
+// a batch of independent systems (different lattices, masses, rhs counts).
 //
 // Per iteration (even/odd system, A = Dhat^dag Dhat):
 //   t  = D_oe p                                   hop, store
@@ -9,9 +10,13 @@
 //   Ap = (4+m)^2 q - (D^dag)_eo t    fused: x += alpha p, r -= alpha Ap,
 //                                    |r|^2 -> beta, convergence flag
 //   p  = r + beta p
-// Scalars never leave the device; the host reads the per-rhs state every few
-// iterations to decide when to stop.  Compensated (double-double) grid sums
-// carry the reductions (Sec. 4.1.1).
+// Scalars never leave the device.  The inner iterations of every instance
+// are one CUDA graph: a WHILE conditional node whose body runs K iterations
+// of all instances on parallel branches and then a one-thread check kernel
+// that keeps the loop going while any right-hand side is neither converged
+// nor at its iteration cap (cudaGraphSetConditional).  The host only steps
+// in for the FP64 true residual between inner solves.  Compensated
+// (double-double) grid sums carry the reductions (Sec. 4.1.1).
 #include <cmath>
 #include <cstring>
 
@@ -20,6 +25,9 @@
 namespace hr {
 
 namespace {
+
+constexpr int MAX_INST = 16;
+constexpr int BODY_ITERS = 4;
 
 struct Ctx {
     const hr_gauge *g;
@@ -37,6 +45,16 @@ struct Vecs {
     FieldView x, r, p, q, t;   // t is an odd half field (even/odd system only)
     int P;                     // operator precision of p, q, t
     int PW;                    // precision of r and x
+};
+
+struct Inst {
+    Ctx c;
+    FieldView vb, vx, r64, q64, q2, t64;
+    FieldView r32, x32;        // mixed only
+    Vecs v;                    // the vectors the (inner) iterations run on
+    hr_cg_result *res;
+    std::vector<int> iters;
+    bool done;
 };
 
 hr_status apply_A(const Ctx &c, int P, const FieldView &v, const FieldView &out, const FieldView &q,
@@ -107,54 +125,27 @@ hr_status cg_iteration(const Ctx &c, const Vecs &v)
     return blas_xpay_beta(D, P, bp, c.s);
 }
 
-hr_status read_states(const Ctx &c, std::vector<CgState> &out)
-{
-    hr_gauge *g = const_cast<hr_gauge *>(c.g);
-    const size_t need = sizeof(CgState) * c.nrhs + sizeof(double) * 4 * c.nrhs;
-    if (g->pinned_bytes < need) {
-        if (g->pinned) cudaFreeHost(g->pinned);
-        g->pinned = nullptr;
-        g->pinned_bytes = 0;
-        HR_CUDA_CHECK(cudaMallocHost(&g->pinned, need));
-        g->pinned_bytes = need;
-    }
-    HR_CUDA_CHECK(cudaMemcpyAsync(g->pinned, c.sc.state, sizeof(CgState) * c.nrhs, cudaMemcpyDeviceToHost, c.s));
-    HR_CUDA_CHECK(cudaStreamSynchronize(c.s));
-    out.resize(c.nrhs);
-    memcpy(out.data(), g->pinned, sizeof(CgState) * c.nrhs);
-    return HR_OK;
-}
-
-hr_status read_red(const Ctx &c, std::vector<double> &out, int n)
-{
-    out.resize(n);
-    HR_CUDA_CHECK(cudaMemcpyAsync(out.data(), c.sc.red, sizeof(double) * n, cudaMemcpyDeviceToHost, c.s));
-    HR_CUDA_CHECK(cudaStreamSynchronize(c.s));
-    return HR_OK;
-}
-
 // r = b - A x (FP64) with |r|^2, |b|^2 into red[2 rhs], state initialised with tol
-hr_status true_residual(const Ctx &c, const FieldView &b, const FieldView &x, const FieldView &r,
-                        const FieldView &q, const FieldView &q2, const FieldView &t, double tol)
+hr_status true_residual(const Inst &in, double tol, int cap)
 {
-    hr_status st = apply_A(c, HR_F64, x, q2, q, t);
+    const Ctx &c = in.c;
+    hr_status st = apply_A(c, HR_F64, in.vx, in.q2, in.q64, in.t64);
     if (st != HR_OK) return st;
     BlasParams bp;
     memset(&bp, 0, sizeof bp);
     bp.nsites = c.ns;
     bp.nrhs = c.nrhs;
-    bp.a = r;
-    bp.b = b;
-    bp.c = q2;
+    bp.a = in.r64;
+    bp.b = in.vb;
+    bp.c = in.q2;
     bp.partials = c.sc.partials;
     bp.counters = c.sc.counters;
     bp.red_out = c.sc.red;
     bp.state = c.sc.state;
     bp.tol2 = tol * tol;
+    bp.cap = cap;
     return blas_residual_init(c.D, bp, c.s);
 }
-
-constexpr int CHECK_EVERY = 8;
 
 // |r| / |b| from the squared norms; NaN whenever either is not finite, and
 // 0 for b = 0 (then x = 0 is exact)
@@ -164,37 +155,131 @@ double rel_residual(double rr, double b2)
     return b2 > 0 ? std::sqrt(rr / b2) : 0.0;
 }
 
-// run CG iterations until every rhs converged or the budget is used up
-hr_status run_iterations(const Ctx &c, const Vecs &v, int budget, std::vector<CgState> &stt, int *done_iters)
+// ------------------------------ the inner graph -----------------------------
+
+struct CheckArgs {
+    const CgState *st[MAX_INST];
+    int nrhs[MAX_INST];
+    int n;
+    unsigned *bodies;   // number of loop bodies run (statistics)
+};
+
+__global__ void k_loop_check(cudaGraphConditionalHandle h, const CheckArgs a)
 {
-    int it = 0;
-    hr_status st = read_states(c, stt);
-    if (st != HR_OK) return st;
-    auto all_done = [&]() {
-        for (auto &s : stt)
-            if (!s.converged) return false;
-        return true;
-    };
-    while (!all_done() && it < budget) {
-        int k = std::min(CHECK_EVERY, budget - it);
-        for (int j = 0; j < k; j++) {
-            st = cg_iteration(c, v);
-            if (st != HR_OK) return st;
-        }
-        it += k;
-        st = read_states(c, stt);
-        if (st != HR_OK) return st;
+    if (threadIdx.x != 0) return;
+    bool any = false;
+    for (int i = 0; i < a.n; i++)
+        for (int k = 0; k < a.nrhs[i]; k++) any |= !cg_idle(a.st[i][k]);
+    *a.bodies += 1;
+    cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
+cudaStream_t branch_stream(int i)
+{
+    static std::vector<cudaStream_t> pool;
+    while ((int)pool.size() <= i) {
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+        pool.push_back(s);
     }
-    *done_iters = it;
+    return pool[i];
+}
+
+struct InnerGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned *bodies = nullptr;   // device counter
+    ~InnerGraph()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (bodies) cudaFree(bodies);
+    }
+
+    hr_status build(std::vector<Inst> &ins)
+    {
+        HR_CUDA_CHECK(cudaMalloc(&bodies, sizeof(unsigned)));
+        HR_CUDA_CHECK(cudaGraphCreate(&graph, 0));
+        cudaGraphConditionalHandle h;
+        HR_CUDA_CHECK(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        HR_CUDA_CHECK(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np));
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        const int n = (int)ins.size();
+        cudaStream_t cap = branch_stream(0);
+        if (!cap) { set_error("cudaStreamCreate failed"); return HR_ERR_CUDA; }
+        std::vector<cudaStream_t> br(n);
+        for (int i = 0; i < n; i++) {
+            br[i] = branch_stream(i + 1);
+            if (!br[i]) { set_error("cudaStreamCreate failed"); return HR_ERR_CUDA; }
+        }
+        std::vector<cudaEvent_t> ev(n + 1);
+        for (auto &e : ev) HR_CUDA_CHECK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        HR_CUDA_CHECK(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        hr_status st = HR_OK;
+        cudaError_t e = cudaEventRecord(ev[n], cap);
+        for (int i = 0; i < n && e == cudaSuccess; i++) e = cudaStreamWaitEvent(br[i], ev[n], 0);
+        if (e != cudaSuccess) st = cuda_fail(e, "graph fork");
+        for (int k = 0; k < BODY_ITERS && st == HR_OK; k++)
+            for (int i = 0; i < n && st == HR_OK; i++) {
+                Ctx c = ins[i].c;
+                c.s = br[i];
+                st = cg_iteration(c, ins[i].v);
+            }
+        for (int i = 0; i < n && st == HR_OK; i++) {
+            e = cudaEventRecord(ev[i], br[i]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, ev[i], 0);
+            if (e != cudaSuccess) st = cuda_fail(e, "graph join");
+        }
+        if (st == HR_OK) {
+            CheckArgs a;
+            memset(&a, 0, sizeof a);
+            a.n = n;
+            for (int i = 0; i < n; i++) {
+                a.st[i] = ins[i].c.sc.state;
+                a.nrhs[i] = ins[i].c.nrhs;
+            }
+            a.bodies = bodies;
+            k_loop_check<<<1, 32, 0, cap>>>(h, a);
+            count_launch();
+            e = cudaGetLastError();
+            if (e != cudaSuccess) st = cuda_fail(e, "k_loop_check");
+        }
+        cudaGraph_t out = nullptr;
+        e = cudaStreamEndCapture(cap, &out);
+        for (auto &x : ev) cudaEventDestroy(x);
+        if (st != HR_OK) return st;
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        HR_CUDA_CHECK(cudaGraphInstantiate(&exec, graph, 0));
+        return HR_OK;
+    }
+
+    hr_status run(cudaStream_t s)
+    {
+        HR_CUDA_CHECK(cudaMemsetAsync(bodies, 0, sizeof(unsigned), s));
+        HR_CUDA_CHECK(cudaGraphLaunch(exec, s));
+        count_launch();
+        return HR_OK;
+    }
+};
+
+hr_status read_states(const Inst &in, std::vector<CgState> &out)
+{
+    out.resize(in.c.nrhs);
+    HR_CUDA_CHECK(cudaMemcpyAsync(out.data(), in.c.sc.state, sizeof(CgState) * in.c.nrhs, cudaMemcpyDeviceToHost,
+                                  in.c.s));
     return HR_OK;
 }
 
-}  // namespace
-
-hr_status cg_solve_impl(const hr_gauge *g, hr_parity sys, const void *b, void *x, int nrhs, const hr_cg_params *prm,
-                        hr_cg_result *res, cudaStream_t s)
+// carve the instance's vectors out of its handle's workspace
+hr_status prepare(Inst &in, const hr_gauge *g, hr_parity sys, const void *b, void *x, int nrhs, int Pin,
+                  hr_cg_result *res, cudaStream_t s)
 {
-    Ctx c;
+    Ctx &c = in.c;
     c.g = g;
     c.sys = sys;
     c.nrhs = nrhs;
@@ -204,164 +289,210 @@ hr_status cg_solve_impl(const hr_gauge *g, hr_parity sys, const void *b, void *x
     c.D = g->D;
     c.m4 = 4.0 + g->lat.m0;
     const int D = c.D;
-    const bool mixed = prm->inner != HR_F64;
-    const int Pin = prm->inner;
-
-    // field workspace: r64 | q64 | q2_64 | t64 | [p64] | [r32 | x32 | pP | qP | tP];
-    // reductions and solver state live in the separate scratch buffer
+    const bool mixed = Pin != HR_F64;
     const size_t f64 = field_rhs_bytes(c.ns, D, HR_F64) * nrhs;
     const size_t t64 = field_rhs_bytes(c.vh, D, HR_F64) * nrhs;
-    size_t need = 3 * f64 + t64 + 4096;
+    size_t need = 4 * f64 + t64 + 8192;
     size_t f32 = 0, fP = 0, tP = 0;
     if (mixed) {
         f32 = field_rhs_bytes(c.ns, D, HR_F32) * nrhs;
         fP = field_rhs_bytes(c.ns, D, Pin) * nrhs;
         tP = field_rhs_bytes(c.vh, D, Pin) * nrhs;
         need += 2 * f32 + 2 * fP + tP + 4096;
-    } else {
-        need += f64;   // p
     }
     hr_status st = ws_reserve(g, need, s);
     if (st != HR_OK) return st;
     st = scratch_reserve(g, nrhs, s, &c.sc);
     if (st != HR_OK) return st;
-    char *p = g->ws;
     c.sc_ns = c.sc;
     c.sc_ns.state = nullptr;
+    char *p = g->ws;
     auto take = [&](size_t bytes) { char *q = p; p += align_up(bytes, 256); return q; };
-    FieldView vb = make_view(const_cast<void *>(b), c.ns, D, HR_F64);
-    FieldView vx = make_view(x, c.ns, D, HR_F64);
-    FieldView r64 = make_view(take(f64), c.ns, D, HR_F64);
-    FieldView q64 = make_view(take(f64), c.ns, D, HR_F64);
-    FieldView q2 = make_view(take(f64), c.ns, D, HR_F64);
-    FieldView t64v = make_view(take(t64), c.vh, D, HR_F64);
-
+    in.vb = make_view(const_cast<void *>(b), c.ns, D, HR_F64);
+    in.vx = make_view(x, c.ns, D, HR_F64);
+    in.r64 = make_view(take(f64), c.ns, D, HR_F64);
+    in.q64 = make_view(take(f64), c.ns, D, HR_F64);
+    in.q2 = make_view(take(f64), c.ns, D, HR_F64);
+    in.t64 = make_view(take(t64), c.vh, D, HR_F64);
+    FieldView p64 = make_view(take(f64), c.ns, D, HR_F64);
+    if (mixed) {
+        in.r32 = make_view(take(f32), c.ns, D, HR_F32);
+        in.x32 = make_view(take(f32), c.ns, D, HR_F32);
+        FieldView pP = make_view(take(fP), c.ns, D, Pin);
+        FieldView qP = make_view(take(fP), c.ns, D, Pin);
+        FieldView tPv = make_view(take(tP), c.vh, D, Pin);
+        in.v = Vecs{in.x32, in.r32, pP, qP, tPv, Pin, HR_F32};
+    } else {
+        in.v = Vecs{in.vx, in.r64, p64, in.q64, in.t64, HR_F64, HR_F64};
+    }
+    in.res = res;
+    in.iters.assign(nrhs, 0);
+    in.done = false;
     for (int k = 0; k < nrhs; k++) {
         res[k].iters = 0;
         res[k].outer_iters = 0;
         res[k].true_rel_residual = NAN;
         res[k].status = HR_ERR_NOT_CONVERGED;
     }
+    return HR_OK;
+}
+
+}  // namespace
+
+// the outer loop shared by plain and mixed CG, single and batched
+hr_status solve_all(std::vector<Inst> &ins, const hr_cg_params *prm, cudaStream_t s)
+{
+    const bool mixed = prm->inner != HR_F64;
     const double tol = prm->tol_rel;
-    std::vector<CgState> stt;
-    std::vector<double> red;
+    for (auto &in : ins)
+        if (!prm->use_initial_guess)
+            HR_CUDA_CHECK(cudaMemsetAsync(in.vx.data, 0, in.vx.rhs_stride * in.c.nrhs, s));
+    InnerGraph ig;
+    hr_status st = ig.build(ins);
+    if (st != HR_OK) return st;
     int total = 0;
-
-    if (!prm->use_initial_guess) HR_CUDA_CHECK(cudaMemsetAsync(x, 0, f64, s));
-
-    if (!mixed) {
-        FieldView p64 = make_view(take(f64), c.ns, D, HR_F64);
-        Vecs v{vx, r64, p64, q64, t64v, HR_F64, HR_F64};
-        std::vector<int> iters(nrhs, 0);
-        for (int restart = 0; restart < 100; restart++) {
-            st = true_residual(c, vb, vx, r64, q64, q2, t64v, tol);
+    std::vector<std::vector<double>> red(ins.size());
+    std::vector<std::vector<CgState>> stt(ins.size());
+    for (int outer = 0; outer < 10000; outer++) {
+        const int cap = std::max(1, prm->max_iter - total);
+        for (auto &in : ins) {
+            if (in.done) continue;
+            st = true_residual(in, tol, cap);
             if (st != HR_OK) return st;
-            // p = r
+        }
+        for (size_t i = 0; i < ins.size(); i++) {
+            if (ins[i].done) continue;
+            red[i].resize(2 * ins[i].c.nrhs);
+            HR_CUDA_CHECK(cudaMemcpyAsync(red[i].data(), ins[i].c.sc.red, sizeof(double) * 2 * ins[i].c.nrhs,
+                                          cudaMemcpyDeviceToHost, s));
+        }
+        HR_CUDA_CHECK(cudaStreamSynchronize(s));
+        bool any_active = false;
+        double worst = 0;
+        for (size_t i = 0; i < ins.size(); i++) {
+            Inst &in = ins[i];
+            if (in.done) continue;
+            bool all_ok = true, bad = false;
+            for (int k = 0; k < in.c.nrhs; k++) {
+                const double rel = rel_residual(red[i][2 * k], red[i][2 * k + 1]);
+                in.res[k].true_rel_residual = rel;
+                in.res[k].outer_iters = mixed ? outer : 0;
+                if (!std::isfinite(rel)) bad = true;
+                if (!(rel <= tol)) {
+                    all_ok = false;
+                    if (std::isfinite(rel)) worst = std::max(worst, tol / rel);
+                }
+            }
+            in.done = all_ok || bad || total >= prm->max_iter;
+            any_active |= !in.done;
+        }
+        if (!any_active) break;
+        // start the inner (or plain) iterations of every active instance
+        const double itol = std::max(prm->inner_tol, 0.5 * worst);
+        for (size_t i = 0; i < ins.size(); i++) {
+            Inst &in = ins[i];
+            if (in.done) continue;
+            const Ctx &c = in.c;
             BlasParams bp;
             memset(&bp, 0, sizeof bp);
             bp.nsites = c.ns;
-            bp.nrhs = nrhs;
-            bp.a = p64;
-            bp.b = r64;
-            bp.s = 1.0;
-            st = blas_convert(D, HR_F64, HR_F64, bp, s);
-            if (st != HR_OK) return st;
-            int done = 0;
-            st = run_iterations(c, v, prm->max_iter - total, stt, &done);
-            if (st != HR_OK) return st;
-            for (int k = 0; k < nrhs; k++) iters[k] += stt[k].iter;
-            total += done;
-            // verify with the true residual
-            st = true_residual(c, vb, vx, r64, q64, q2, t64v, tol);
-            if (st != HR_OK) return st;
-            st = read_red(c, red, 2 * nrhs);
-            if (st != HR_OK) return st;
-            bool all_ok = true, any_bad = false;
-            for (int k = 0; k < nrhs; k++) {
-                double rel = rel_residual(red[2 * k], red[2 * k + 1]);
-                res[k].true_rel_residual = rel;
-                res[k].iters = iters[k];
-                if (!std::isfinite(rel)) any_bad = true;
-                if (!(rel <= tol)) all_ok = false;
+            bp.nrhs = c.nrhs;
+            if (!mixed) {
+                // p = r; the state already holds |r|^2, |b|^2 and stop2 = tol^2 |b|^2
+                bp.a = in.v.p;
+                bp.b = in.r64;
+                bp.s = 1.0;
+                st = blas_convert(c.D, HR_F64, HR_F64, bp, s);
+            } else {
+                std::vector<double> sv(2 * c.nrhs);
+                for (int k = 0; k < c.nrhs; k++) {
+                    const double rr = red[i][2 * k];
+                    const bool ok = in.res[k].true_rel_residual <= tol;
+                    sv[k] = (ok || !(rr > 0) || !std::isfinite(rr)) ? 0.0 : 1.0 / std::sqrt(rr);
+                    sv[c.nrhs + k] = sv[k] == 0.0 ? 0.0 : std::sqrt(rr);
+                }
+                HR_CUDA_CHECK(cudaMemcpyAsync(c.sc.sv, sv.data(), sizeof(double) * 2 * c.nrhs, cudaMemcpyHostToDevice,
+                                              s));
+                bp.a = in.r32;
+                bp.b = in.r64;
+                bp.c = in.x32;
+                bp.d = in.v.p;
+                bp.sv = c.sc.sv;
+                bp.partials = c.sc.partials;
+                bp.counters = c.sc.counters;
+                bp.state = c.sc.state;
+                bp.tol2 = itol * itol;
+                bp.cap = cap;
+                st = blas_inner_init(c.D, in.v.P, bp, s);
             }
-            if (all_ok || any_bad || total >= prm->max_iter) break;
+            if (st != HR_OK) return st;
         }
-    } else {
-        FieldView r32 = make_view(take(f32), c.ns, D, HR_F32);
-        FieldView x32 = make_view(take(f32), c.ns, D, HR_F32);
-        FieldView pP = make_view(take(fP), c.ns, D, Pin);
-        FieldView qP = make_view(take(fP), c.ns, D, Pin);
-        FieldView tPv = make_view(take(tP), c.vh, D, Pin);
-        Vecs v{x32, r32, pP, qP, tPv, Pin, HR_F32};
-        std::vector<double> sv(2 * nrhs);
-        std::vector<int> iters(nrhs, 0);
-        int outer = 0;
-        for (; outer < 1000; outer++) {
-            st = true_residual(c, vb, vx, r64, q64, q2, t64v, tol);
+        st = ig.run(s);
+        if (st != HR_OK) return st;
+        int ran = 0;
+        for (size_t i = 0; i < ins.size(); i++) {
+            st = read_states(ins[i], stt[i]);
             if (st != HR_OK) return st;
-            st = read_red(c, red, 2 * nrhs);
-            if (st != HR_OK) return st;
-            bool all_ok = true, any_bad = false;
-            double worst = 0;
-            for (int k = 0; k < nrhs; k++) {
-                const double rr = red[2 * k], b2 = red[2 * k + 1];
-                const double rel = rel_residual(rr, b2);
-                res[k].true_rel_residual = rel;
-                res[k].outer_iters = outer;
-                if (!std::isfinite(rel)) any_bad = true;
-                const bool ok = rel <= tol;
-                if (!ok) all_ok = false;
-                sv[k] = (ok || !std::isfinite(rel) || rr <= 0) ? 0.0 : 1.0 / std::sqrt(rr);
-                sv[nrhs + k] = sv[k] == 0.0 ? 0.0 : std::sqrt(rr);
-                if (!ok && std::isfinite(rel)) worst = std::max(worst, tol / rel);
+        }
+        HR_CUDA_CHECK(cudaStreamSynchronize(s));
+        for (size_t i = 0; i < ins.size(); i++) {
+            Inst &in = ins[i];
+            if (in.done) continue;
+            for (int k = 0; k < in.c.nrhs; k++) {
+                in.iters[k] += stt[i][k].iter;
+                ran = std::max(ran, stt[i][k].iter);
             }
-            if (all_ok || any_bad || total >= prm->max_iter) break;
-            HR_CUDA_CHECK(cudaMemcpyAsync(c.sc.sv, sv.data(), sizeof(double) * 2 * nrhs, cudaMemcpyHostToDevice, s));
-            const double itol = std::max(prm->inner_tol, 0.5 * worst);
-            BlasParams bp;
-            memset(&bp, 0, sizeof bp);
-            bp.nsites = c.ns;
-            bp.nrhs = nrhs;
-            bp.a = r32;
-            bp.b = r64;
-            bp.c = x32;
-            bp.d = pP;
-            bp.sv = c.sc.sv;
-            bp.partials = c.sc.partials;
-            bp.counters = c.sc.counters;
-            bp.state = c.sc.state;
-            bp.tol2 = itol * itol;
-            st = blas_inner_init(D, Pin, bp, s);
-            if (st != HR_OK) return st;
-            int done = 0;
-            st = run_iterations(c, v, prm->max_iter - total, stt, &done);
-            if (st != HR_OK) return st;
-            for (int k = 0; k < nrhs; k++) iters[k] += stt[k].iter;
-            total += done;
-            memset(&bp, 0, sizeof bp);
-            bp.nsites = c.ns;
-            bp.nrhs = nrhs;
-            bp.a = vx;
-            bp.b = x32;
-            bp.sv = c.sc.sv + nrhs;
-            st = blas_outer_update(D, bp, s);
-            if (st != HR_OK) return st;
-            HR_CUDA_CHECK(cudaStreamSynchronize(s));   // sv is rewritten next round
+            if (mixed) {
+                BlasParams bp;
+                memset(&bp, 0, sizeof bp);
+                bp.nsites = in.c.ns;
+                bp.nrhs = in.c.nrhs;
+                bp.a = in.vx;
+                bp.b = in.x32;
+                bp.sv = in.c.sc.sv + in.c.nrhs;
+                st = blas_outer_update(in.c.D, bp, s);
+                if (st != HR_OK) return st;
+            }
         }
-        for (int k = 0; k < nrhs; k++) {
-            res[k].iters = iters[k];
-            res[k].outer_iters = outer;
-        }
+        total += ran;
+        if (mixed) HR_CUDA_CHECK(cudaStreamSynchronize(s));   // sv is rewritten next round
     }
     hr_status overall = HR_OK;
-    for (int k = 0; k < nrhs; k++) {
-        const double rel = res[k].true_rel_residual;
-        res[k].status = !std::isfinite(rel) ? HR_ERR_NONFINITE : (rel <= tol ? HR_OK : HR_ERR_NOT_CONVERGED);
-        if (res[k].status != HR_OK && overall == HR_OK) overall = res[k].status;
-    }
+    for (auto &in : ins)
+        for (int k = 0; k < in.c.nrhs; k++) {
+            const double rel = in.res[k].true_rel_residual;
+            in.res[k].iters = in.iters[k];
+            in.res[k].status = !std::isfinite(rel) ? HR_ERR_NONFINITE : (rel <= tol ? HR_OK : HR_ERR_NOT_CONVERGED);
+            if (in.res[k].status != HR_OK && overall == HR_OK) overall = in.res[k].status;
+        }
     if (overall == HR_ERR_NOT_CONVERGED) set_error("CG stopped above tolerance after %d iterations", total);
     if (overall == HR_ERR_NONFINITE) set_error("CG met a non-finite reduction");
     return overall;
+}
+
+static hr_status check_params(const hr_gauge *g, hr_parity sys, const hr_cg_params *params)
+{
+    if (sys != HR_FULL && sys != HR_EO_PRECOND) {
+        set_error("CG: sys must be HR_FULL or HR_EO_PRECOND");
+        return HR_ERR_INVALID;
+    }
+    if (!(params->tol_rel > 0) || params->max_iter < 1) {
+        set_error("CG: tol_rel must be > 0 and max_iter >= 1");
+        return HR_ERR_INVALID;
+    }
+    if (!(g->prec_mask & (1u << HR_F64))) {
+        set_error("CG: the gauge handle must hold FP64 links");
+        return HR_ERR_INVALID;
+    }
+    if (params->inner < HR_F64 || params->inner > HR_BF16 || !(g->prec_mask & (1u << params->inner))) {
+        set_error("CG: inner precision %d not stored in the handle", (int)params->inner);
+        return HR_ERR_INVALID;
+    }
+    if (params->inner != HR_F64 && !(params->inner_tol > 0 && params->inner_tol < 1)) {
+        set_error("CG: inner_tol must be in (0, 1)");
+        return HR_ERR_INVALID;
+    }
+    return HR_OK;
 }
 
 }  // namespace hr
@@ -375,34 +506,46 @@ extern "C" hr_status hr_cg_solve(const hr_gauge *g, hr_parity sys, const void *b
         set_error("hr_cg_solve: NULL argument or nrhs < 1");
         return HR_ERR_INVALID;
     }
-    if (sys != HR_FULL && sys != HR_EO_PRECOND) {
-        set_error("hr_cg_solve: sys must be HR_FULL or HR_EO_PRECOND");
-        return HR_ERR_INVALID;
-    }
     if (b == x) { set_error("hr_cg_solve: b and x must not overlap"); return HR_ERR_INVALID; }
-    if (!(params->tol_rel > 0) || params->max_iter < 1) {
-        set_error("hr_cg_solve: tol_rel must be > 0 and max_iter >= 1");
-        return HR_ERR_INVALID;
-    }
-    if (!(g->prec_mask & (1u << HR_F64))) {
-        set_error("hr_cg_solve: the gauge handle must hold FP64 links");
-        return HR_ERR_INVALID;
-    }
-    if (params->inner < HR_F64 || params->inner > HR_BF16 || !(g->prec_mask & (1u << params->inner))) {
-        set_error("hr_cg_solve: inner precision %d not stored in the handle", (int)params->inner);
-        return HR_ERR_INVALID;
-    }
-    if (params->inner != HR_F64 && !(params->inner_tol > 0 && params->inner_tol < 1)) {
-        set_error("hr_cg_solve: inner_tol must be in (0, 1)");
-        return HR_ERR_INVALID;
-    }
-    return cg_solve_impl(g, sys, b, x, nrhs, params, res, reinterpret_cast<cudaStream_t>(stream));
+    hr_status st = check_params(g, sys, params);
+    if (st != HR_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<Inst> ins(1);
+    st = prepare(ins[0], g, sys, b, x, nrhs, params->inner, res, s);
+    if (st != HR_OK) return st;
+    return solve_all(ins, params, s);
 }
 
 extern "C" hr_status hr_cg_solve_batched(int n_inst, const hr_gauge *const *g, hr_parity sys, const void *const *b,
                                          void *const *x, const int *nrhs, const hr_cg_params *params,
                                          hr_cg_result *res, void *stream)
 {
-    set_error("hr_cg_solve_batched: not built yet");
-    return HR_ERR_UNSUPPORTED;
+    if (n_inst < 1 || n_inst > MAX_INST || !g || !b || !x || !nrhs || !params || !res) {
+        set_error("hr_cg_solve_batched: bad arguments (1 <= n_inst <= %d)", MAX_INST);
+        return HR_ERR_INVALID;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<Inst> ins(n_inst);
+    size_t off = 0;
+    for (int i = 0; i < n_inst; i++) {
+        if (!g[i] || !b[i] || !x[i] || nrhs[i] < 1 || b[i] == x[i]) {
+            set_error("hr_cg_solve_batched: instance %d has a NULL pointer, nrhs < 1 or b == x", i);
+            return HR_ERR_INVALID;
+        }
+        for (int j = 0; j < i; j++)
+            if (g[j] == g[i]) {
+                set_error("hr_cg_solve_batched: instances %d and %d share a gauge handle", j, i);
+                return HR_ERR_INVALID;
+            }
+        if (g[i]->lat.N != g[0]->lat.N || g[i]->lat.rep != g[0]->lat.rep) {
+            set_error("hr_cg_solve_batched: all instances must share N and the representation");
+            return HR_ERR_INVALID;
+        }
+        hr_status st = check_params(g[i], sys, params);
+        if (st != HR_OK) return st;
+        st = prepare(ins[i], g[i], sys, b[i], x[i], nrhs[i], params->inner, res + off, s);
+        if (st != HR_OK) return st;
+        off += nrhs[i];
+    }
+    return solve_all(ins, params, s);
 }

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const HopParams prm)
 
     const Geom &g = prm.g;
     const int rhs = blockIdx.y;
-    if (prm.state && prm.state[rhs].converged) return;   // uniform per block
+    if (prm.state && cg_idle(prm.state[rhs])) return;   // uniform per block
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < g.vh;
     const R sg = prm.dagger ? (R)-1 : (R)1;

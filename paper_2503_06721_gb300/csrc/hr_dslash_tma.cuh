@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) hop_tma_kernel(const HopParams 
 
     const Geom &g = prm.g;
     const int rhs = blockIdx.y;
-    if (prm.state && prm.state[rhs].converged) return;
+    if (prm.state && cg_idle(prm.state[rhs])) return;
 
     const long first = (long)blockIdx.x * WARPS + warp;
     const long step = (long)gridDim.x * WARPS;

@@ -372,9 +372,12 @@ struct CgState {
     double b2;        // |b|^2
     int converged;
     int nonfinite;
-    int iter;
-    int pad;
+    int iter;         // iterations done in the current (inner) solve
+    int cap;          // iteration cap of the current (inner) solve
 };
+
+// a right-hand side takes no further iteration once it converged or hit its cap
+__host__ __device__ __forceinline__ bool cg_idle(const CgState &s) { return s.converged || s.iter >= s.cap; }
 
 // ---------------------------------------------------------------------------
 // host-side helpers
