@@ -136,6 +136,24 @@ hr_status hr_field_dot(const hr_lattice_desc *lat, hr_parity par, hr_prec prec,
                        const void *a, const void *b, int nrhs, double *out,
                        void *stream);
 
+/* hr_field_dot without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory
+ * -- e.g. when another allocator owns the device memory, or on a path that
+ * cannot take the implicit synchronisation of cudaMalloc/cudaFree -- while
+ * hr_field_dot takes its reduction scratch from cudaMallocAsync.
+ * Same arguments and result as hr_field_dot; additionally nrhs must be
+ * 1..16 (HR_ERR_INVALID otherwise).  Its scratch is a fixed ~312 KB array in
+ * device memory, present on every GPU that loads the library until the
+ * process exits; every call shares it and it keeps the last call's contents
+ * (each call zeroes the tickets it needs first).  Calls that overlap on the
+ * GPU race on that array, so order them on one stream.  The first call on a
+ * device looks up the array's device address with that device current; make
+ * that first call before any stream capture on the device.
+ * Synchronises the stream. */
+hr_status hr_field_dot_static(const hr_lattice_desc *lat, hr_parity par,
+                              hr_prec prec, const void *a, const void *b,
+                              int nrhs, double *out, void *stream);
+
 /* ------------------------------------------------------------------ */
 /* Wilson-Dirac operator (Eq. D_m^R in Sec. 2.3; Sec. 4.3.3)              */
 /* ------------------------------------------------------------------ */

@@ -31,7 +31,8 @@ STATUS = {0: "HR_OK", -1: "HR_ERR_INVALID", -2: "HR_ERR_CUDA", -3: "HR_ERR_NOMEM
 
 # every symbol include/hr.h declares
 EXPORTS = ["hr_represent_gauge", "hr_gauge_update", "hr_gauge_set_link_mode", "hr_gauge_destroy",
-           "hr_field_bytes", "hr_field_convert", "hr_field_dot", "hr_dirac_apply", "hr_dirac_dagger",
+           "hr_field_bytes", "hr_field_convert", "hr_field_dot", "hr_field_dot_static",
+           "hr_dirac_apply", "hr_dirac_dagger",
            "hr_cg_solve", "hr_cg_solve_batched", "hr_dirac_force", "hr_rep_dim", "hr_generators",
            "hr_status_string", "hr_last_error", "hr_launch_count"]
 
@@ -82,6 +83,7 @@ def load():
         "hr_field_bytes": (S, [LP, I, I, I]),
         "hr_field_convert": (I, [LP, I, I, P, I, P, I, P]),
         "hr_field_dot": (I, [LP, I, I, P, P, I, ctypes.POINTER(D), P]),
+        "hr_field_dot_static": (I, [LP, I, I, P, P, I, ctypes.POINTER(D), P]),
         "hr_dirac_apply": (I, [P, I, I, P, P, I, P]),
         "hr_dirac_dagger": (I, [P, I, I, P, P, I, P]),
         "hr_cg_solve": (I, [P, I, P, P, I, ctypes.POINTER(CgParams), ctypes.POINTER(CgResult), P]),
