@@ -151,17 +151,28 @@ def run_ours(args, rank, world, local_rank):
     deo_ms = []
     work = {"bytes": 0}
 
+    pev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    phases = {"represent": 0.0, "deo": 0.0, "cg": 0.0, "force": 0.0}
+
     def step(phi_dev, U_dev):
+        pev[0].record(stream)
         g.update(U_dev)
+        pev[1].record(stream)
         for k in range(n_deo):
             ev[2 * k].record(stream)
             g.apply(hr.EVEN, hr.F32, x32, out=y32)
             ev[2 * k + 1].record(stream)
         g.apply(hr.EVEN, hr.F64, phi_dev, out=y64)
+        pev[2].record(stream)
         x, res, st = g.cg_solve(hr.EO_PRECOND, phi_dev, tol=TOL, max_iter=20000, inner=hr.F32,
                                 inner_tol=1e-5)
+        pev[3].record(stream)
         Y = g.apply(hr.EO_PRECOND, hr.F64, x)
         F = g.force(hr.EO_PRECOND, x, Y, coeff=-1.0)
+        pev[4].record(stream)
+        torch.cuda.synchronize()
+        for name, a, b in (("represent", 0, 1), ("deo", 1, 2), ("cg", 2, 3), ("force", 3, 4)):
+            phases[name] += pev[a].elapsed_time(pev[b])
         r = res[0]
         # hop launches of this step by precision
         h32 = n_deo + 4 * r["iters"]
@@ -174,8 +185,8 @@ def run_ours(args, rank, world, local_rank):
         step(phi, U)
     torch.cuda.synchronize()
     work["bytes"] = 0
-    for e in ev:
-        pass
+    for k in phases:
+        phases[k] = 0.0
     clocks = Clocks(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
     clocks.start()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -203,6 +214,7 @@ def run_ours(args, rank, world, local_rank):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
     ms_per_step = ms / args.steps
+    phase_ms = {k: round(v / args.steps, 2) for k, v in phases.items()}
     value = world * step_bytes / (ms_per_step * 1e-3) / 1e9
     deo_ms_avg = sum(deo_times) / len(deo_times)
     deo_bytes = hop_bytes(D, real, hr.F32, vh)
@@ -286,6 +298,7 @@ def run_ours(args, rank, world, local_rank):
                          "traffic": args.traffic, "deo_ms": round(deo_ms_avg, 4),
                          "bytes_per_launch": deo_bytes},
             "gpu_launches": int(launches),
+            "phases_ms": phase_ms,
             "clocks": ck,
             "e2e": e2e,
             "cg": cg,

@@ -12,7 +12,7 @@
 namespace hr {
 
 static thread_local std::string g_last_error;
-static std::atomic<unsigned long long> g_launches{0};
+static std::atomic<long long> g_launches{0};
 
 void set_error(const char *fmt, ...)
 {
@@ -30,7 +30,8 @@ hr_status cuda_fail(cudaError_t e, const char *what)
     return e == cudaErrorMemoryAllocation ? HR_ERR_NOMEM : HR_ERR_CUDA;
 }
 
-void count_launch(unsigned n) { g_launches += n; }
+void count_launch(long long n) { g_launches += n; }
+long long launch_counter() { return g_launches.load(); }
 
 // --------------------------- dispatch --------------------------------------
 #define HR_PAIRS(X) X(2, HR_FUND) X(2, HR_ADJ) X(2, HR_SYM) X(3, HR_FUND) X(3, HR_ADJ) X(3, HR_SYM) \
@@ -293,7 +294,7 @@ const char *hr_status_string(hr_status s)
 
 const char *hr_last_error(void) { return g_last_error.c_str(); }
 
-unsigned long long hr_launch_count(void) { return g_launches.load(); }
+unsigned long long hr_launch_count(void) { return (unsigned long long)g_launches.load(); }
 
 int hr_rep_dim(int N, hr_rep rep)
 {
@@ -352,8 +353,7 @@ hr_status hr_represent_gauge(const hr_lattice_desc *lat, const void *U_fund, uns
     for (int P = 0; P < 4; P++) {
         if (!(prec_mask & (1u << P))) continue;
         if (link_modes & (1u << HR_LINKS_STORED)) {
-            size_t elem = g->real ? prec_rbytes(P) : prec_cbytes(P);
-            size_t b = link_record_bytes(g->geom, g->D * g->D, elem);
+            size_t b = link_record_bytes(g->geom, P, g->real, g->D * g->D);
             g->rep_bytes[P] = b;
             for (int par = 0; par < 2; par++) {
                 cudaError_t e = cudaMalloc(&g->rep[P][par], b);
@@ -363,7 +363,7 @@ hr_status hr_represent_gauge(const hr_lattice_desc *lat, const void *U_fund, uns
             }
         }
         if (link_modes & (1u << HR_LINKS_REBUILD)) {
-            size_t b = link_record_bytes(g->geom, lat->N * lat->N, prec_cbytes(P));
+            size_t b = link_record_bytes(g->geom, P, false, lat->N * lat->N);
             g->fund_bytes[P] = b;
             for (int par = 0; par < 2; par++) {
                 cudaError_t e = cudaMalloc(&g->fund[P][par], b);

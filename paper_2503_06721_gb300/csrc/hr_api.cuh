@@ -38,6 +38,9 @@ hr_status hop(const hr_gauge *g, int P, int out_parity, int dagger, const FieldV
               double *red_out = nullptr, const FieldView *r = nullptr, const FieldView *x = nullptr,
               const FieldView *p = nullptr);
 
+// number of kernel launches counted so far (graph contents counted when they run)
+long long launch_counter();
+
 // (T_R^a)_{nm} as complex double [(N*N-1)][D][D] (host)
 void rep_generator_table(int N, int rep, double *out);
 

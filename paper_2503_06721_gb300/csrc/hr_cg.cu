@@ -189,6 +189,7 @@ struct InnerGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     unsigned *bodies = nullptr;   // device counter
+    long long per_body = 0;       // kernels in one loop body
     ~InnerGraph()
     {
         if (exec) cudaGraphExecDestroy(exec);
@@ -220,6 +221,7 @@ struct InnerGraph {
         std::vector<cudaEvent_t> ev(n + 1);
         for (auto &e : ev) HR_CUDA_CHECK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         HR_CUDA_CHECK(cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        const long long before = launch_counter();
         hr_status st = HR_OK;
         cudaError_t e = cudaEventRecord(ev[n], cap);
         for (int i = 0; i < n && e == cudaSuccess; i++) e = cudaStreamWaitEvent(br[i], ev[n], 0);
@@ -251,6 +253,9 @@ struct InnerGraph {
         }
         cudaGraph_t out = nullptr;
         e = cudaStreamEndCapture(cap, &out);
+        // captured launches are counted when the graph runs, not here
+        per_body = launch_counter() - before;
+        count_launch(-per_body);
         for (auto &x : ev) cudaEventDestroy(x);
         if (st != HR_OK) return st;
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
@@ -262,7 +267,14 @@ struct InnerGraph {
     {
         HR_CUDA_CHECK(cudaMemsetAsync(bodies, 0, sizeof(unsigned), s));
         HR_CUDA_CHECK(cudaGraphLaunch(exec, s));
-        count_launch();
+        return HR_OK;
+    }
+    // after the stream has synchronised: count the kernels the loop ran
+    hr_status account(cudaStream_t s)
+    {
+        unsigned n = 0;
+        HR_CUDA_CHECK(cudaMemcpy(&n, bodies, sizeof(unsigned), cudaMemcpyDeviceToHost));
+        count_launch((long long)n * per_body);
         return HR_OK;
     }
 };
@@ -435,6 +447,8 @@ hr_status solve_all(std::vector<Inst> &ins, const hr_cg_params *prm, cudaStream_
             if (st != HR_OK) return st;
         }
         HR_CUDA_CHECK(cudaStreamSynchronize(s));
+        st = ig.account(s);
+        if (st != HR_OK) return st;
         for (size_t i = 0; i < ins.size(); i++) {
             Inst &in = ins[i];
             if (in.done) continue;

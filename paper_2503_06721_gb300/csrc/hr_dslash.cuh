@@ -119,13 +119,15 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const HopParams prm)
                 for (int c = 0; c < D; c++)
                     h[r][c] = psi[r][c] + sp * ipow(ephase(mu, r), psi[2 + eperm(mu, r)][c]);
             cx<R> chi[2][D];
-            const typename LIO::E *lp = LIO::slot_ptr(prm.links, tile, k, lane);
+            const uint4 *lp = LIO::slot_ptr(prm.links, tile, k, lane);
             if constexpr (REBUILD) {
+                cx<R> Wf[N * N];
+                LIO::load(lp, Wf);
                 cx<R> F[N][N];
 #pragma unroll
                 for (int a = 0; a < N; a++)
 #pragma unroll
-                    for (int b = 0; b < N; b++) F[a][b] = LIO::ldc(lp, a * N + b);
+                    for (int b = 0; b < N; b++) F[a][b] = Wf[a * N + b];
                 rep_act<N, REP, R>(F, h[0], chi[0]);
                 rep_act<N, REP, R>(F, h[1], chi[1]);
                 // fermion boundary sign on the t = T-1 <-> 0 (etc.) hop
@@ -137,21 +139,30 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const HopParams prm)
 #pragma unroll
                         for (int c = 0; c < D; c++) chi[r][c] = (R)-1 * chi[r][c];
                 }
-            } else {
+            } else if constexpr (REAL) {
+                R W[D * D];
+                LIO::load(lp, W);
 #pragma unroll
                 for (int row = 0; row < D; row++) {
                     cx<R> s0 = {0, 0}, s1 = {0, 0};
 #pragma unroll
                     for (int col = 0; col < D; col++) {
-                        if constexpr (REAL) {
-                            R w = LIO::ldr(lp, row * D + col);
-                            rmac(s0, w, h[0][col]);
-                            rmac(s1, w, h[1][col]);
-                        } else {
-                            cx<R> w = LIO::ldc(lp, row * D + col);
-                            cmac(s0, w, h[0][col]);
-                            cmac(s1, w, h[1][col]);
-                        }
+                        rmac(s0, W[row * D + col], h[0][col]);
+                        rmac(s1, W[row * D + col], h[1][col]);
+                    }
+                    chi[0][row] = s0;
+                    chi[1][row] = s1;
+                }
+            } else {
+                cx<R> W[D * D];
+                LIO::load(lp, W);
+#pragma unroll
+                for (int row = 0; row < D; row++) {
+                    cx<R> s0 = {0, 0}, s1 = {0, 0};
+#pragma unroll
+                    for (int col = 0; col < D; col++) {
+                        cmac(s0, W[row * D + col], h[0][col]);
+                        cmac(s1, W[row * D + col], h[1][col]);
                     }
                     chi[0][row] = s0;
                     chi[1][row] = s1;

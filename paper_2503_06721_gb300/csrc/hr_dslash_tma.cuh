@@ -24,8 +24,8 @@ struct TmaShape {
     static constexpr int D = rep_dim(N, REP);
     static constexpr bool REAL = rep_real(REP);
     static constexpr int NCOMP = D * D;
-    static constexpr int ELEM = REAL ? (int)prec_rbytes(P) : (int)prec_cbytes(P);
-    static constexpr int LINK_BYTES = NCOMP * HR_TILE * ELEM;                    // one slot record
+    static constexpr int NCHUNK = link_nchunk(P, REAL, NCOMP);
+    static constexpr int LINK_BYTES = NCHUNK * HR_TILE * 16;                     // one slot record
     static constexpr int SPIN_BYTES = 4 * D * (int)prec_cbytes(P);               // one site
     // per-lane stride: a multiple of 16 bytes that is an odd multiple of 16,
     // so 16-byte reads of eight consecutive lanes hit distinct banks
@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) hop_tma_kernel(const HopParams 
     constexpr int D = Sh::D;
     constexpr bool REAL = Sh::REAL;
     using SIO = SpinorIO<P, D>;
-    using E = typename std::conditional<REAL, typename S::Rs, typename S::C>::type;
+    using LIO = LinkIO<P, REAL, D * D>;
 
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) hop_tma_kernel(const HopParams 
         if (lane == 0) {
             fence_proxy_async();
             mbar_arrive_expect_tx(&bars[warp][s], Sh::LINK_BYTES);
-            const E *src = reinterpret_cast<const E *>(prm.links) + ((size_t)tile * 8 + slot) * Sh::NCOMP * HR_TILE;
+            const uint4 *src = reinterpret_cast<const uint4 *>(prm.links) + ((size_t)tile * 8 + slot) * Sh::NCHUNK * HR_TILE;
             bulk_g2s(sb, src, Sh::LINK_BYTES, &bars[warp][s], pol);
         }
         const long i = tile * HR_TILE + lane;
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) hop_tma_kernel(const HopParams 
                 const long nb = neighbour(g, st, slot & 3, slot < 4 ? +1 : -1);
                 sc = (R)SIO::ld_scale(prm.in, rhs, nb);
             }
-            const E *W = reinterpret_cast<const E *>(sb) + lane;
+            const uint4 *Wp = reinterpret_cast<const uint4 *>(sb) + lane;
             // unrolled over the 8 slot values so mu and the projector are constants
             static_for<0, 8>([&](auto KK) {
                 constexpr int k = decltype(KK)::value;
@@ -163,13 +163,14 @@ __global__ void __launch_bounds__(WARPS * 32, 1) hop_tma_kernel(const HopParams 
                     cx<R> s0 = {0, 0}, s1 = {0, 0};
 #pragma unroll
                     for (int col = 0; col < D; col++) {
-                        const E w = W[(row * D + col) * HR_TILE];
+                        const int cc = row * D + col;
+                        const uint4 w = Wp[(cc / LIO::VPC) * HR_TILE];
                         if constexpr (REAL) {
-                            const R wr = S::ldr(w);
+                            const R wr = LIO::runpack(w, cc % LIO::VPC);
                             rmac(s0, wr, h[0][col]);
                             rmac(s1, wr, h[1][col]);
                         } else {
-                            const cx<R> wc = S::ld(w);
+                            const cx<R> wc = LIO::cunpack(w, cc % LIO::VPC);
                             cmac(s0, wc, h[0][col]);
                             cmac(s1, wc, h[1][col]);
                         }

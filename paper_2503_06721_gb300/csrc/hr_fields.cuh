@@ -135,34 +135,89 @@ struct SpinorIO {
     }
 };
 
-// Link records: AoSoA [tile][slot 0..7][component][lane 0..31].
+// Link records: AoSoA [tile][slot 0..7][chunk][lane 0..31] of 16-byte chunks.
+// Chunk j of a lane holds the slot's components j*VPC .. j*VPC+VPC-1 (VPC =
+// 16 bytes / component bytes; the last chunk is zero-padded), so a warp reads
+// 512 contiguous bytes per load instruction whatever the precision.
+__host__ __device__ constexpr int link_elem_bytes(int P, bool real) { return real ? (int)prec_rbytes(P) : (int)prec_cbytes(P); }
+__host__ __device__ constexpr int link_vpc(int P, bool real) { return 16 / link_elem_bytes(P, real); }
+__host__ __device__ constexpr int link_nchunk(int P, bool real, int ncomp)
+{
+    return (ncomp + link_vpc(P, real) - 1) / link_vpc(P, real);
+}
+// byte offset of component c of (tile, slot, lane) in a record of ncomp components
+__host__ __device__ inline size_t link_offset(int P, bool real, int ncomp, long tile, int slot, int lane, int c)
+{
+    const int vpc = link_vpc(P, real), nch = link_nchunk(P, real, ncomp);
+    return ((((size_t)tile * 8 + slot) * nch + c / vpc) * HR_TILE + lane) * 16 + (size_t)(c % vpc) * link_elem_bytes(P, real);
+}
+
 template <int P, bool REAL, int NCOMP>
 struct LinkIO {
     using S = St<P>;
     using R = typename S::R;
-    using E = typename std::conditional<REAL, typename S::Rs, typename S::C>::type;
-    static constexpr size_t SLOT_ELEMS = (size_t)NCOMP * HR_TILE;
-    static constexpr size_t TILE_ELEMS = 8 * SLOT_ELEMS;
+    static constexpr int VPC = link_vpc(P, REAL);
+    static constexpr int NCHUNK = link_nchunk(P, REAL, NCOMP);
+    static constexpr size_t SLOT_CHUNKS = (size_t)NCHUNK * HR_TILE;
 
-    __device__ __forceinline__ static const E *slot_ptr(const void *base, long tile, int slot, int lane)
+    __device__ __forceinline__ static const uint4 *slot_ptr(const void *base, long tile, int slot, int lane)
     {
-        return reinterpret_cast<const E *>(base) + (size_t)tile * TILE_ELEMS + (size_t)slot * SLOT_ELEMS + lane;
+        return reinterpret_cast<const uint4 *>(base) + ((size_t)tile * 8 + slot) * SLOT_CHUNKS + lane;
     }
-    // streaming load (each link is read exactly once per operator application)
-    __device__ __forceinline__ static cx<R> ldc(const E *p, int comp)
+    __device__ __forceinline__ static unsigned word(const uint4 &v, int k)
     {
-        E v = __ldcs(p + (size_t)comp * HR_TILE);
-        if constexpr (REAL)
-            return {S::ldr(v), (R)0};
-        else
-            return S::ld(v);
+        return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
     }
-    __device__ __forceinline__ static R ldr(const E *p, int comp)
+    // complex component k of a chunk
+    __device__ __forceinline__ static cx<R> cunpack(const uint4 &v, int k)
     {
-        if constexpr (REAL)
-            return S::ldr(__ldcs(p + (size_t)comp * HR_TILE));
-        else
-            return (R)0;
+        if constexpr (P == HR_F64) {
+            return {__hiloint2double((int)v.y, (int)v.x), __hiloint2double((int)v.w, (int)v.z)};
+        } else if constexpr (P == HR_F32) {
+            return {__uint_as_float(word(v, 2 * k)), __uint_as_float(word(v, 2 * k + 1))};
+        } else {
+            const unsigned w = word(v, k);
+            typename S::C h;
+            memcpy(&h, &w, 4);
+            return S::ld(h);
+        }
+    }
+    // real component k of a chunk
+    __device__ __forceinline__ static R runpack(const uint4 &v, int k)
+    {
+        if constexpr (P == HR_F64) {
+            return k == 0 ? __hiloint2double((int)v.y, (int)v.x) : __hiloint2double((int)v.w, (int)v.z);
+        } else if constexpr (P == HR_F32) {
+            return __uint_as_float(word(v, k));
+        } else {
+            const unsigned w = word(v, k >> 1);
+            const unsigned short hbits = (k & 1) ? (unsigned short)(w >> 16) : (unsigned short)(w & 0xFFFF);
+            typename S::Rs h;
+            memcpy(&h, &hbits, 2);
+            return S::ldr(h);
+        }
+    }
+    // the whole slot, streamed with evict-first loads (each link is read once
+    // per operator application)
+    __device__ __forceinline__ static void load(const uint4 *p, cx<R> (&W)[NCOMP])
+    {
+#pragma unroll
+        for (int j = 0; j < NCHUNK; j++) {
+            const uint4 v = __ldcs(p + (size_t)j * HR_TILE);
+#pragma unroll
+            for (int k = 0; k < VPC; k++)
+                if (j * VPC + k < NCOMP) W[j * VPC + k] = cunpack(v, k);
+        }
+    }
+    __device__ __forceinline__ static void load(const uint4 *p, R (&W)[NCOMP])
+    {
+#pragma unroll
+        for (int j = 0; j < NCHUNK; j++) {
+            const uint4 v = __ldcs(p + (size_t)j * HR_TILE);
+#pragma unroll
+            for (int k = 0; k < VPC; k++)
+                if (j * VPC + k < NCOMP) W[j * VPC + k] = runpack(v, k);
+        }
     }
 };
 

@@ -61,10 +61,10 @@ hr_status hop_dispatch(int N, int rep, int P, const HopParams &prm, bool rebuild
 hr_status represent_dispatch(const hr_gauge &g, const double2 *UF, cudaStream_t stream);
 hr_status force_dispatch(const hr_gauge &g, const ForceParams &fp, cudaStream_t stream);
 
-// link record bytes of one parity
-inline size_t link_record_bytes(const Geom &g, int ncomp, size_t elem)
+// link record bytes of one parity: ntiles x 8 slots x chunks x 32 lanes x 16 B
+inline size_t link_record_bytes(const Geom &g, int P, bool real, int ncomp)
 {
-    return (size_t)g.ntiles * 8 * ncomp * HR_TILE * elem;
+    return (size_t)g.ntiles * 8 * link_nchunk(P, real, ncomp) * HR_TILE * 16;
 }
 
 }  // namespace hr

@@ -5,6 +5,23 @@
 
 namespace hr {
 
+// one link entry in precision P (real: the real part only)
+__device__ inline void store_entry(int P, bool real, char *dst, cx<double> v)
+{
+    if (real) {
+        if (P == HR_F64) *reinterpret_cast<double *>(dst) = v.re;
+        if (P == HR_F32) *reinterpret_cast<float *>(dst) = (float)v.re;
+        if (P == HR_F16) *reinterpret_cast<__half *>(dst) = __double2half(v.re);
+        if (P == HR_BF16) *reinterpret_cast<__nv_bfloat16 *>(dst) = __double2bfloat16(v.re);
+    } else {
+        if (P == HR_F64) *reinterpret_cast<double2 *>(dst) = make_double2(v.re, v.im);
+        if (P == HR_F32) *reinterpret_cast<float2 *>(dst) = make_float2((float)v.re, (float)v.im);
+        if (P == HR_F16) *reinterpret_cast<__half2 *>(dst) = __halves2half2(__double2half(v.re), __double2half(v.im));
+        if (P == HR_BF16)
+            *reinterpret_cast<__nv_bfloat162 *>(dst) = __halves2bfloat162(__double2bfloat16(v.re), __double2bfloat16(v.im));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // represent: one thread per (tile, slot, lane) so the record writes coalesce.
 // slot k < 4 : U_R(x, mu)        with -1 if bc_mu = -1 and x_mu = L_mu - 1
@@ -41,44 +58,32 @@ __global__ void __launch_bounds__(128) represent_kernel(const double2 *__restric
                 U[b][a] = {v.x, -v.y};   // dagger
         }
     const bool neg = g.bc[mu] == -1 && (fwd ? s.c[mu] == L[mu] - 1 : s.c[mu] == 0);
-    const size_t base = ((size_t)tile * 8 + slot);
     bool any_rep = false;
     for (int p = 0; p < 4; p++) any_rep |= o.rep[p] != nullptr;
+    constexpr bool REAL = rep_real(REP);
     if (any_rep) {
         cx<double> Rm[D][D];
         represent<N, REP>(U, Rm);
         const double sg = neg ? -1.0 : 1.0;
         for (int r = 0; r < D; r++)
             for (int q = 0; q < D; q++) {
-                const size_t idx = (base * D * D + (size_t)(r * D + q)) * HR_TILE + lane;
+                const int c = r * D + q;
                 const cx<double> v = sg * Rm[r][q];
-                if (rep_real(REP)) {
-                    if (o.rep[HR_F64]) reinterpret_cast<double *>(o.rep[HR_F64])[idx] = v.re;
-                    if (o.rep[HR_F32]) reinterpret_cast<float *>(o.rep[HR_F32])[idx] = (float)v.re;
-                    if (o.rep[HR_F16]) reinterpret_cast<__half *>(o.rep[HR_F16])[idx] = __double2half(v.re);
-                    if (o.rep[HR_BF16]) reinterpret_cast<__nv_bfloat16 *>(o.rep[HR_BF16])[idx] = __double2bfloat16(v.re);
-                } else {
-                    if (o.rep[HR_F64]) reinterpret_cast<double2 *>(o.rep[HR_F64])[idx] = make_double2(v.re, v.im);
-                    if (o.rep[HR_F32]) reinterpret_cast<float2 *>(o.rep[HR_F32])[idx] = make_float2((float)v.re, (float)v.im);
-                    if (o.rep[HR_F16])
-                        reinterpret_cast<__half2 *>(o.rep[HR_F16])[idx] = __halves2half2(__double2half(v.re), __double2half(v.im));
-                    if (o.rep[HR_BF16])
-                        reinterpret_cast<__nv_bfloat162 *>(o.rep[HR_BF16])[idx] =
-                            __halves2bfloat162(__double2bfloat16(v.re), __double2bfloat16(v.im));
+                for (int P = 0; P < 4; P++) {
+                    if (!o.rep[P]) continue;
+                    char *dst = reinterpret_cast<char *>(o.rep[P]) + link_offset(P, REAL, D * D, tile, slot, lane, c);
+                    store_entry(P, REAL, dst, v);
                 }
             }
     }
     for (int r = 0; r < N; r++)
         for (int q = 0; q < N; q++) {
-            const size_t idx = (base * N * N + (size_t)(r * N + q)) * HR_TILE + lane;
-            const cx<double> v = U[r][q];
-            if (o.fund[HR_F64]) reinterpret_cast<double2 *>(o.fund[HR_F64])[idx] = make_double2(v.re, v.im);
-            if (o.fund[HR_F32]) reinterpret_cast<float2 *>(o.fund[HR_F32])[idx] = make_float2((float)v.re, (float)v.im);
-            if (o.fund[HR_F16])
-                reinterpret_cast<__half2 *>(o.fund[HR_F16])[idx] = __halves2half2(__double2half(v.re), __double2half(v.im));
-            if (o.fund[HR_BF16])
-                reinterpret_cast<__nv_bfloat162 *>(o.fund[HR_BF16])[idx] =
-                    __halves2bfloat162(__double2bfloat16(v.re), __double2bfloat16(v.im));
+            const int c = r * N + q;
+            for (int P = 0; P < 4; P++) {
+                if (!o.fund[P]) continue;
+                char *dst = reinterpret_cast<char *>(o.fund[P]) + link_offset(P, false, N * N, tile, slot, lane, c);
+                store_entry(P, false, dst, U[r][q]);
+            }
         }
 }
 
@@ -153,10 +158,19 @@ __global__ void __launch_bounds__(128) force_kernel(const ForceParams fp)
     // U_R(x, mu): slot mu of this site's record (carries the boundary sign)
     const long tile = i / HR_TILE;
     const int lane = (int)(i % HR_TILE);
-    const typename LIO::E *lp = LIO::slot_ptr(fp.links, tile, mu, lane);
+    const uint4 *lp = LIO::slot_ptr(fp.links, tile, mu, lane);
     cx<double> U[D][D];
-    for (int a = 0; a < D; a++)
-        for (int b = 0; b < D; b++) U[a][b] = LIO::ldc(lp, a * D + b);
+    if constexpr (REAL) {
+        double W[D * D];
+        LIO::load(lp, W);
+        for (int a = 0; a < D; a++)
+            for (int b = 0; b < D; b++) U[a][b] = {W[a * D + b], 0.0};
+    } else {
+        cx<double> W[D * D];
+        LIO::load(lp, W);
+        for (int a = 0; a < D; a++)
+            for (int b = 0; b < D; b++) U[a][b] = W[a * D + b];
+    }
     // M = U A - B U^dag
     cx<double> M[D][D];
     for (int a = 0; a < D; a++)

@@ -384,7 +384,7 @@ __host__ __device__ __forceinline__ bool cg_idle(const CgState &s) { return s.co
 // ---------------------------------------------------------------------------
 void set_error(const char *fmt, ...);
 hr_status cuda_fail(cudaError_t e, const char *what);
-void count_launch(unsigned n = 1);
+void count_launch(long long n = 1);
 
 #define HR_CUDA_CHECK(call)                                        \
     do {                                                           \

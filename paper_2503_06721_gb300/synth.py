@@ -262,6 +262,9 @@ WORKLOADS = {
     # SU(3) sextet 32^4: the same kernel on a lattice small enough for profiler captures
     "su3_sym_32x32x32x32": Workload("su3_sym_32x32x32x32", 3, "SYM", (32, 32, 32, 32), -0.3,
                                     0.4, haar=True, seed=2503067212),
+    # SU(3) adjoint 32^4: profiler-sized lattice of the adjoint kernels
+    "su3_adj_32x32x32x32": Workload("su3_adj_32x32x32x32", 3, "ADJ", (32, 32, 32, 32), -0.35, 0.5,
+                                    seed=2503067215),
     # SU(3) adjoint 64^3 x 128, stored vs rebuilt links
     "su3_adj_128x64x64x64": Workload("su3_adj_128x64x64x64", 3, "ADJ", (128, 64, 64, 64),
                                      -0.35, 0.5, seed=2503067215),
