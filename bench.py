@@ -409,26 +409,30 @@ def run_deo(args, local_rank):
     g = hr.Gauge(lat, wl.links(device=dev), precs=(args.prec,), stored=not args.rebuild,
                  rebuild=args.rebuild)
     vh = lat.volume // 2
-    x = synth.gaussian_spinor(vh, lat.D, 3, device=dev)
+    n = args.nrhs
+    x = synth.gaussian_spinor(vh, lat.D, 3, device=dev, nrhs=n)
     x = x if prec == hr.F64 else (x.to(torch.complex64) if prec == hr.F32 else
-                                  hr.field_convert(lat, hr.EVEN, x, hr.F64, prec))
-    y = g.apply(hr.EVEN, prec, x)
+                                  hr.field_convert(lat, hr.EVEN, x, hr.F64, prec, n))
+    y = g.apply(hr.EVEN, prec, x, nrhs=n)
     for _ in range(args.warmup):
-        g.apply(hr.EVEN, prec, x, out=y)
+        g.apply(hr.EVEN, prec, x, out=y, nrhs=n)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
-        g.apply(hr.EVEN, prec, x, out=y)
+        g.apply(hr.EVEN, prec, x, out=y, nrhs=n)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
+    cb = [16, 8, 4, 4][prec]
+    sp = 4 * lat.D * cb + (4 if prec >= 2 else 0)
     if args.rebuild:
-        cb = [16, 8, 4, 4][prec]
-        byts = vh * (8 * wl.N * wl.N * cb + 2 * (4 * lat.D * cb + (4 if prec >= 2 else 0)))
+        lp = wl.N * wl.N * cb
     else:
-        byts = hop_bytes(lat.D, wl.rep == "ADJ", prec, vh)
-    print(json.dumps({"mode": "deo", "workload": args.workload, "prec": args.prec,
+        lp = lat.D * lat.D * (cb // 2 if wl.rep == "ADJ" else cb)
+    # compulsory bytes: every link once, every input and output spinor once
+    byts = vh * (8 * lp + 2 * n * sp)
+    print(json.dumps({"mode": "deo", "workload": args.workload, "prec": args.prec, "nrhs": n,
                       "links": "rebuild" if args.rebuild else "stored", "ms": round(ms, 4),
                       "GBs": round(byts / (ms * 1e-3) / 1e9, 1), "bytes_per_launch": byts}))
 
@@ -449,6 +453,7 @@ def main():
                     help="deo: only D_eo applications (profiler captures)")
     ap.add_argument("--prec", choices=["f64", "f32", "f16", "bf16"], default="f32")
     ap.add_argument("--rebuild", action="store_true", help="deo mode: rebuild links in-kernel")
+    ap.add_argument("--nrhs", type=int, default=1, help="deo mode: right-hand sides per application")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per D_eo launch, when known for the current kernel")
     args = ap.parse_args()

@@ -218,21 +218,24 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const HopParams prm)
         if (active) {
             using CIO = SpinorIO<(P == HR_F64 ? HR_F64 : HR_F32), D>;
             const R alpha = (R)prm.state[rhs].alpha;
-            cx<R> rr[4][D], xx[4][D], pp[4][D];
-            CIO::load_rw(prm.r, rhs, i, rr);
-            CIO::load_rw(prm.x, rhs, i, xx);
-            SIO::load_rw(prm.p, rhs, i, pp);
+            const R psc = (R)SIO::ld_scale(prm.p, rhs, i);
             R n2 = 0;
+            // one spin component at a time keeps r, x, p out of the register budget
 #pragma unroll
-            for (int s = 0; s < 4; s++)
+            for (int s = 0; s < 4; s++) {
+                cx<R> rr[D], xx[D], pp[D];
+                CIO::load_spin(prm.r, rhs, i, s, (R)1, rr);
+                CIO::load_spin(prm.x, rhs, i, s, (R)1, xx);
+                SIO::load_spin(prm.p, rhs, i, s, psc, pp);
 #pragma unroll
                 for (int c = 0; c < D; c++) {
-                    rr[s][c] = rr[s][c] - alpha * acc[s][c];
-                    xx[s][c] = xx[s][c] + alpha * pp[s][c];
-                    n2 += rr[s][c].re * rr[s][c].re + rr[s][c].im * rr[s][c].im;
+                    rr[c] = rr[c] - alpha * acc[s][c];
+                    xx[c] = xx[c] + alpha * pp[c];
+                    n2 += rr[c].re * rr[c].re + rr[c].im * rr[c].im;
                 }
-            CIO::store(prm.r, rhs, i, rr);
-            CIO::store(prm.x, rhs, i, xx);
+                CIO::store_spin(prm.r, rhs, i, s, rr);
+                CIO::store_spin(prm.x, rhs, i, s, xx);
+            }
             v[0] = (double)n2;
         }
         double tot[1];
@@ -242,8 +245,10 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const HopParams prm)
     }
 }
 
-// host-side launcher, instantiated per (N, REP, P) in hr_dslash_*.cu
+// host-side launchers, instantiated per (N, REP, P) in hr_dslash_inst.cu
 template <int N, int REP, int P>
 hr_status launch_hop(const HopParams &prm, bool rebuild, int epi, cudaStream_t stream);
+template <int N, int REP, int P>
+hr_status launch_hop_mrhs(const HopParams &prm, int epi, int *err, cudaStream_t stream);
 
 }  // namespace hr

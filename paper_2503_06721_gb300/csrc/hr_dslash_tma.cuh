@@ -210,21 +210,23 @@ __global__ void __launch_bounds__(WARPS * 32, 1) hop_tma_kernel(const HopParams 
             } else {
                 using CIO = SpinorIO<(P == HR_F64 ? HR_F64 : HR_F32), D>;
                 const R alpha = (R)prm.state[rhs].alpha;
-                cx<R> rr[4][D], xx[4][D], pp[4][D];
-                CIO::load_rw(prm.r, rhs, i, rr);
-                CIO::load_rw(prm.x, rhs, i, xx);
-                SIO::load_rw(prm.p, rhs, i, pp);
+                const R psc = (R)SIO::ld_scale(prm.p, rhs, i);
                 R n2 = 0;
 #pragma unroll
-                for (int q = 0; q < 4; q++)
+                for (int q = 0; q < 4; q++) {
+                    cx<R> rr[D], xx[D], pp[D];
+                    CIO::load_spin(prm.r, rhs, i, q, (R)1, rr);
+                    CIO::load_spin(prm.x, rhs, i, q, (R)1, xx);
+                    SIO::load_spin(prm.p, rhs, i, q, psc, pp);
 #pragma unroll
                     for (int c = 0; c < D; c++) {
-                        rr[q][c] = rr[q][c] - alpha * acc[q][c];
-                        xx[q][c] = xx[q][c] + alpha * pp[q][c];
-                        n2 += rr[q][c].re * rr[q][c].re + rr[q][c].im * rr[q][c].im;
+                        rr[c] = rr[c] - alpha * acc[q][c];
+                        xx[c] = xx[c] + alpha * pp[c];
+                        n2 += rr[c].re * rr[c].re + rr[c].im * rr[c].im;
                     }
-                CIO::store(prm.r, rhs, i, rr);
-                CIO::store(prm.x, rhs, i, xx);
+                    CIO::store_spin(prm.r, rhs, i, q, rr);
+                    CIO::store_spin(prm.x, rhs, i, q, xx);
+                }
                 red += (double)n2;
             }
         }

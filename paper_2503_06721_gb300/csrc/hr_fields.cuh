@@ -90,6 +90,39 @@ struct SpinorIO {
             }
     }
 
+    // one spin component (D complex numbers) of a site; sc = the site's scale
+    // for F16/BF16 (ignored otherwise)
+    __device__ __forceinline__ static void load_spin(const FieldView &f, int rhs, long i, int s, R sc,
+                                                     cx<R> (&v)[D])
+    {
+        const char *b = f.data + (size_t)rhs * f.rhs_stride + (size_t)i * BYTES + (size_t)s * D * prec_cbytes(P);
+#pragma unroll
+        for (int c = 0; c < D; c++) {
+            if constexpr (P == HR_F64) {
+                const double2 d = *reinterpret_cast<const double2 *>(b + 16 * c);
+                v[c] = {d.x, d.y};
+            } else if constexpr (P == HR_F32) {
+                const float2 d = *reinterpret_cast<const float2 *>(b + 8 * c);
+                v[c] = {d.x, d.y};
+            } else {
+                v[c] = sc * S::ld(*reinterpret_cast<const typename S::C *>(b + 4 * c));
+            }
+        }
+    }
+    // one spin component of an unscaled (F64 / F32) site
+    __device__ __forceinline__ static void store_spin(const FieldView &f, int rhs, long i, int s, const cx<R> (&v)[D])
+    {
+        static_assert(!S::scaled, "per-spin stores need an unscaled precision");
+        char *b = f.data + (size_t)rhs * f.rhs_stride + (size_t)i * BYTES + (size_t)s * D * prec_cbytes(P);
+#pragma unroll
+        for (int c = 0; c < D; c++) {
+            if constexpr (P == HR_F64)
+                *reinterpret_cast<double2 *>(b + 16 * c) = make_double2(v[c].re, v[c].im);
+            else
+                *reinterpret_cast<float2 *>(b + 8 * c) = make_float2(v[c].re, v[c].im);
+        }
+    }
+
     __device__ __forceinline__ static void store(const FieldView &f, int rhs, long i, const cx<R> (&psi)[4][D])
     {
         uint4 raw[NV];

@@ -27,6 +27,7 @@ struct hr_gauge {
     // that no field temporary ever overwrites the zeroed tickets
     char *scr;
     size_t scr_bytes;
+    int *err;             // device flag set by a bounded wait that gave up
     void *pinned;         // host staging for solver state (pinned)
     size_t pinned_bytes;
     int device;

@@ -108,9 +108,76 @@ hr_status represent_launch(const hr_gauge &gg, const double2 *UF, cudaStream_t s
 // fermion force (Sec. 2.5): for the link U(x, mu) owned by site x,
 //   A = sum_s [(1 - g_mu) X(x+mu)]_s Y_s(x)^dag,
 //   B = sum_s X_s(x) [(1 + g_mu) Y(x+mu)]_s^dag,
-//   M = U_R A - B U_R^dag,   F^a += coeff * Re tr(i T_R^a M) = -coeff Im tr(T_R^a M).
-// One thread per (site of `parity`, mu); X, Y read in FP64.
+//   F^a += coeff * Re tr(i T_R^a (U_R A - B U_R^dag)).
+// The projectors leave two independent spin components, so
+//   A = sum_{r=0,1} hX_r z_r^dag,  B = sum_r w_r hY_r^dag   with
+//   hX = upper[(1 - g_mu) X(x+mu)],  z = upper[(1 - g_mu) Y(x)],
+//   hY = upper[(1 + g_mu) Y(x+mu)],  w = upper[(1 + g_mu) X(x)],
+// and U A - B U^dag = K = sum_r (U hX_r) z_r^dag - w_r (U hY_r)^dag needs four
+// matrix-vector products.  tr(T_R^a K) is pulled back to the fundamental,
+// tr(T_R^a K) = tr(T^a P), by differentiating the sparse representation
+// formulas (the same ones the represent kernel evaluates), so only the
+// N x N matrix P meets the generators.
+// One thread per (site of `parity`, mu); FP64 throughout.
 // ---------------------------------------------------------------------------
+// Kf(m, n) returns the entry K_mn (computed on demand, so K is never stored)
+template <int N, int REP, class KF>
+__device__ __forceinline__ void pullback(KF &&Kf, cx<double> (&P)[N][N])
+{
+    constexpr int D = rep_dim(N, REP);
+#pragma unroll
+    for (int i = 0; i < N; i++)
+#pragma unroll
+        for (int j = 0; j < N; j++) P[i][j] = {0, 0};
+    if constexpr (REP == HR_FUND) {
+        // tr(T K) = sum T_ik K_ki  ->  P = K
+#pragma unroll
+        for (int i = 0; i < N; i++)
+#pragma unroll
+            for (int j = 0; j < N; j++) P[i][j] = Kf(i, j);
+    } else if constexpr (REP == HR_ADJ) {
+        // (T_R)_nm = 2 sum be ga [T_jk d_il - d_jk T_li]  (T Hermitian)
+        static_for<0, D>([&](auto NN) {
+            constexpr int n = decltype(NN)::value;
+            static_for<0, D>([&](auto MM) {
+                constexpr int m = decltype(MM)::value;
+                const cx<double> kmn = Kf(m, n);
+                static_for<0, gen_nent(N, n)>([&](auto E1) {
+                    constexpr int e1 = decltype(E1)::value;
+                    constexpr int i = gen_row(N, n, e1), j = gen_col(N, n, e1);
+                    static_for<0, gen_nent(N, m)>([&](auto E2) {
+                        constexpr int e2 = decltype(E2)::value;
+                        constexpr int k = gen_row(N, m, e2), l = gen_col(N, m, e2);
+                        const cx<double> c = 2.0 * (gen_val<double>(N, n, e1) * gen_val<double>(N, m, e2)) * kmn;
+                        if constexpr (i == l) P[k][j] = P[k][j] + c;   // T_jk P_kj
+                        if constexpr (j == k) P[i][l] = P[i][l] - c;   // T_li P_il
+                    });
+                });
+            });
+        });
+    } else {
+        // (T_R)_nm = sum w v [T_ik d_jl + d_ik T_jl]
+        static_for<0, D>([&](auto NN) {
+            constexpr int n = decltype(NN)::value;
+            static_for<0, D>([&](auto MM) {
+                constexpr int m = decltype(MM)::value;
+                const cx<double> kmn = Kf(m, n);
+                static_for<0, sb_nent(N, REP, n)>([&](auto E1) {
+                    constexpr int e1 = decltype(E1)::value;
+                    constexpr int i = sb_row(N, REP, n, e1), j = sb_col(N, REP, n, e1);
+                    static_for<0, sb_nent(N, REP, m)>([&](auto E2) {
+                        constexpr int e2 = decltype(E2)::value;
+                        constexpr int k = sb_row(N, REP, m, e2), l = sb_col(N, REP, m, e2);
+                        const cx<double> c = (sb_val(N, REP, n, e1) * sb_val(N, REP, m, e2)) * kmn;
+                        if constexpr (j == l) P[k][i] = P[k][i] + c;   // T_ik P_ki
+                        if constexpr (i == k) P[l][j] = P[l][j] + c;   // T_jl P_lj
+                    });
+                });
+            });
+        });
+    }
+}
+
 template <int N, int REP>
 __global__ void __launch_bounds__(128) force_kernel(const ForceParams fp)
 {
@@ -120,87 +187,93 @@ __global__ void __launch_bounds__(128) force_kernel(const ForceParams fp)
     using SIO = SpinorIO<HR_F64, D>;
     using LIO = LinkIO<HR_F64, REAL, D * D>;
     const Geom &g = fp.g;
+    // two threads per link (adjacent lanes): spin component r = 0, 1 of the projections
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long i = t >> 2;
-    const int mu = (int)(t & 3);
-    if (i >= g.vh) return;
-    Site s = site_of(g, i, fp.parity);
-    const long nb = neighbour(g, s, mu, +1);
-    cx<double> Xn[4][D], Yn[4][D], Xh[4][D], Yh[4][D];
-    SIO::load(fp.X_nb, 0, nb, Xn);
-    SIO::load(fp.Y_nb, 0, nb, Yn);
-    SIO::load(fp.X_here, 0, i, Xh);
-    SIO::load(fp.Y_here, 0, i, Yh);
-    // PX = (1 - g_mu) X(x+mu), PY = (1 + g_mu) Y(x+mu) via the e_mu structure:
-    // (1 + sp g) psi = [up + sp e dn ; dn + sp e^dag up]
-    cx<double> PX[4][D], PY[4][D];
-    for (int c = 0; c < D; c++) {
-        for (int r = 0; r < 2; r++) {
-            const int q = eperm(mu, r), ph = ephase(mu, r);
-            PX[r][c] = Xn[r][c] + (-1.0) * ipow(ph, Xn[2 + q][c]);
-            PY[r][c] = Yn[r][c] + ipow(ph, Yn[2 + q][c]);
-            // lower row q gets conj(e_{r q}) times the upper component r
-            PX[2 + q][c] = Xn[2 + q][c] + (-1.0) * ipow(4 - ph, Xn[r][c]);
-            PY[2 + q][c] = Yn[2 + q][c] + ipow(4 - ph, Yn[r][c]);
+    const int r = (int)(t & 1);
+    const long link = t >> 1;
+    const long i = link >> 2;
+    const int mu = (int)(link & 3);
+    const bool active = i < g.vh;   // both lanes of a pair agree
+    cx<double> P[N][N];
+    if (active) {
+        Site s = site_of(g, i, fp.parity);
+        const long nb = neighbour(g, s, mu, +1);
+        const int q = 2 + eperm(mu, r), ph = ephase(mu, r);
+        auto ld = [&](const FieldView &f, long site, int sp, int c) {
+            const uint4 v = __ldg(SIO::site_ptr(f, 0, site) + (sp * D + c));
+            return cx<double>{__hiloint2double((int)v.y, (int)v.x), __hiloint2double((int)v.w, (int)v.z)};
+        };
+        // upper component r of (1 -+ g_mu) psi: psi_r -+ i^{ph} psi_q
+        cx<double> hX[D], hY[D], z[D], w[D];
+        for (int c = 0; c < D; c++) {
+            hX[c] = ld(fp.X_nb, nb, r, c) + (-1.0) * ipow(ph, ld(fp.X_nb, nb, q, c));
+            hY[c] = ld(fp.Y_nb, nb, r, c) + ipow(ph, ld(fp.Y_nb, nb, q, c));
+            z[c] = ld(fp.Y_here, i, r, c) + (-1.0) * ipow(ph, ld(fp.Y_here, i, q, c));
+            w[c] = ld(fp.X_here, i, r, c) + ipow(ph, ld(fp.X_here, i, q, c));
         }
-    }
-    cx<double> A[D][D], B[D][D];
-    for (int a = 0; a < D; a++)
-        for (int b = 0; b < D; b++) {
-            cx<double> sa = {0, 0}, sb = {0, 0};
-            for (int sp = 0; sp < 4; sp++) {
-                cmac(sa, PX[sp][a], conj(Yh[sp][b]));
-                cmac(sb, Xh[sp][a], conj(PY[sp][b]));
+        // u = U hX, v = U hY with U_R(x, mu) (slot mu, boundary sign included), row by row
+        const long tile = i / HR_TILE;
+        const int lane = (int)(i % HR_TILE);
+        const uint4 *lp = LIO::slot_ptr(fp.links, tile, mu, lane);
+        cx<double> u[D], v[D];
+        for (int a = 0; a < D; a++) {
+            cx<double> su = {0, 0}, sv = {0, 0};
+            for (int b = 0; b < D; b++) {
+                const int cc = a * D + b;
+                const uint4 ch = __ldg(lp + (size_t)(cc / LIO::VPC) * HR_TILE);
+                cx<double> uab;
+                if constexpr (REAL)
+                    uab = {LIO::runpack(ch, cc % LIO::VPC), 0.0};
+                else
+                    uab = LIO::cunpack(ch, 0);
+                cmac(su, uab, hX[b]);
+                cmac(sv, uab, hY[b]);
             }
-            A[a][b] = sa;
-            B[a][b] = sb;
+            u[a] = su;
+            v[a] = sv;
         }
-    // U_R(x, mu): slot mu of this site's record (carries the boundary sign)
-    const long tile = i / HR_TILE;
-    const int lane = (int)(i % HR_TILE);
-    const uint4 *lp = LIO::slot_ptr(fp.links, tile, mu, lane);
-    cx<double> U[D][D];
-    if constexpr (REAL) {
-        double W[D * D];
-        LIO::load(lp, W);
-        for (int a = 0; a < D; a++)
-            for (int b = 0; b < D; b++) U[a][b] = {W[a * D + b], 0.0};
+        // K_r = u z^dag - w v^dag, pulled back entry by entry
+        pullback<N, REP>(
+            [&](int a, int b) {
+                cx<double> k = {0, 0};
+                cmac(k, u[a], conj(z[b]));
+                cmac(k, (-1.0) * w[a], conj(v[b]));
+                return k;
+            },
+            P);
     } else {
-        cx<double> W[D * D];
-        LIO::load(lp, W);
-        for (int a = 0; a < D; a++)
-            for (int b = 0; b < D; b++) U[a][b] = W[a * D + b];
+#pragma unroll
+        for (int a = 0; a < N; a++)
+#pragma unroll
+            for (int b = 0; b < N; b++) P[a][b] = {0, 0};
     }
-    // M = U A - B U^dag
-    cx<double> M[D][D];
-    for (int a = 0; a < D; a++)
-        for (int b = 0; b < D; b++) {
-            cx<double> m = {0, 0};
-            for (int k = 0; k < D; k++) {
-                cmac(m, U[a][k], A[k][b]);
-                cmac(m, (-1.0) * B[a][k], conj(U[b][k]));
-            }
-            M[a][b] = m;
+    // combine the two spin components of the link
+#pragma unroll
+    for (int a = 0; a < N; a++)
+#pragma unroll
+        for (int b = 0; b < N; b++) {
+            P[a][b].re += __shfl_xor_sync(0xffffffffu, P[a][b].re, 1);
+            P[a][b].im += __shfl_xor_sync(0xffffffffu, P[a][b].im, 1);
         }
-    const long lex = lex_of(g, s);
+    if (!active || r != 0) return;
+    const long lex = lex_of(g, site_of(g, i, fp.parity));
     double *Fo = fp.F + ((size_t)lex * 4 + mu) * NG;
-    for (int a = 0; a < NG; a++) {
-        const double2 *T = reinterpret_cast<const double2 *>(fp.TR) + (size_t)a * D * D;
-        double im = 0;
-        for (int p = 0; p < D; p++)
-            for (int q = 0; q < D; q++) {
-                const double2 tv = __ldg(&T[p * D + q]);
-                const cx<double> mv = M[q][p];
-                im += tv.x * mv.im + tv.y * mv.re;
-            }
-        Fo[a] += -fp.coeff * im;
-    }
+    // F^a += -coeff Im tr(T^a P) = -coeff Im sum_{(i,j,al) in T^a} al P_ji
+    static_for<0, NG>([&](auto AA) {
+        constexpr int a = decltype(AA)::value;
+        cx<double> tr = {0, 0};
+        static_for<0, gen_nent(N, a)>([&](auto EE) {
+            constexpr int e = decltype(EE)::value;
+            cmac(tr, gen_val<double>(N, a, e), P[gen_col(N, a, e)][gen_row(N, a, e)]);
+        });
+        Fo[a] += -fp.coeff * tr.im;
+    });
 }
 
 template <int N, int REP>
 hr_status force_launch(const ForceParams &fp, cudaStream_t stream)
 {
-    const long threads = fp.g.vh * 4;
+    const long threads = fp.g.vh * 8;   // two threads per link
     force_kernel<N, REP><<<(unsigned)((threads + 127) / 128), 128, 0, stream>>>(fp);
     HR_LAUNCH_CHECK("force_kernel");
     return HR_OK;
