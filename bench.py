@@ -197,7 +197,9 @@ def run_ours(args, rank, world, local_rank):
     t0.record(stream)
     deo_times = []
     for _ in range(args.steps):
+        torch.cuda.nvtx.range_push("hr_step")   # profiler captures select this range
         step(phi, U)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         deo_times += [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(n_deo)]
     t1.record(stream)

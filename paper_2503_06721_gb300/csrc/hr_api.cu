@@ -8,7 +8,6 @@
 #include <string>
 
 #include "hr_api.cuh"
-#include "hr_dslash_mrhs.cuh"
 
 namespace hr {
 
@@ -44,11 +43,7 @@ long long launch_counter() { return g_launches.load(); }
     extern template hr_status launch_hop<N_, R_, HR_F16>(const HopParams &, bool, int, cudaStream_t);     \
     extern template hr_status launch_hop<N_, R_, HR_BF16>(const HopParams &, bool, int, cudaStream_t);    \
     extern template hr_status represent_launch<N_, R_>(const hr_gauge &, const double2 *, cudaStream_t); \
-    extern template hr_status force_launch<N_, R_>(const ForceParams &, cudaStream_t);                   \
-    extern template hr_status launch_hop_mrhs<N_, R_, HR_F64>(const HopParams &, int, int *, cudaStream_t); \
-    extern template hr_status launch_hop_mrhs<N_, R_, HR_F32>(const HopParams &, int, int *, cudaStream_t); \
-    extern template hr_status launch_hop_mrhs<N_, R_, HR_F16>(const HopParams &, int, int *, cudaStream_t); \
-    extern template hr_status launch_hop_mrhs<N_, R_, HR_BF16>(const HopParams &, int, int *, cudaStream_t);
+    extern template hr_status force_launch<N_, R_>(const ForceParams &, cudaStream_t);
 HR_PAIRS(HR_DECL)
 
 bool pair_supported(int N, int rep)
@@ -72,23 +67,6 @@ hr_status hop_dispatch(int N, int rep, int P, const HopParams &prm, bool rebuild
     }
     HR_PAIRS(HR_HOP)
 #undef HR_HOP
-    set_error("SU(%d) representation %d not compiled", N, rep);
-    return HR_ERR_UNSUPPORTED;
-}
-
-hr_status hop_mrhs_dispatch(int N, int rep, int P, const HopParams &prm, int epi, int *err, cudaStream_t stream)
-{
-#define HR_HOPM(N_, R_)                                                                       \
-    if (N == N_ && rep == R_) {                                                               \
-        switch (P) {                                                                          \
-        case HR_F64: return launch_hop_mrhs<N_, R_, HR_F64>(prm, epi, err, stream);           \
-        case HR_F32: return launch_hop_mrhs<N_, R_, HR_F32>(prm, epi, err, stream);           \
-        case HR_F16: return launch_hop_mrhs<N_, R_, HR_F16>(prm, epi, err, stream);           \
-        case HR_BF16: return launch_hop_mrhs<N_, R_, HR_BF16>(prm, epi, err, stream);         \
-        }                                                                                     \
-    }
-    HR_PAIRS(HR_HOPM)
-#undef HR_HOPM
     set_error("SU(%d) representation %d not compiled", N, rep);
     return HR_ERR_UNSUPPORTED;
 }
@@ -287,33 +265,11 @@ hr_status hop(const hr_gauge *g, int P, int out_parity, int dagger, const FieldV
     if (r) prm.r = *r;
     if (x) prm.x = *x;
     if (p) prm.p = *p;
-    // a block of right-hand sides on stored links: the links are read once per
-    // chunk of up to mrhs_max(P) right-hand sides instead of once per rhs
-    if (nrhs >= 2 && !rebuild && g->err) {
-        const int chunk = mrhs_max(P);
-        const long mb = max_blocks_for(g);
-        for (int r0 = 0; r0 < nrhs; r0 += chunk) {
-            HopParams c = prm;
-            c.nrhs = std::min(chunk, nrhs - r0);
-            auto shift = [&](FieldView &f) {
-                if (f.data) f.data += (size_t)r0 * f.rhs_stride;
-                if (f.scale) f.scale += (size_t)r0 * f.rhs_stride;
-            };
-            shift(c.in);
-            shift(c.out);
-            shift(c.diag);
-            shift(c.r);
-            shift(c.x);
-            shift(c.p);
-            if (c.partials) c.partials += (size_t)r0 * mb;
-            if (c.counters) c.counters += r0;
-            if (c.state) c.state += r0;
-            if (c.red_out) c.red_out += r0;
-            if (c.carry) c.carry += r0;
-            hr_status st = hop_mrhs_dispatch(g->lat.N, g->lat.rep, P, c, epi, g->err, stream);
-            if (st != HR_OK) return st;
-        }
-        return HR_OK;
+    // a block of right-hand sides: right-hand-side-fastest block order, so the
+    // links are fetched from HBM once and served from L2 to the other rhs
+    if (nrhs >= 2) {
+        prm.rhs_inner = 1;
+        prm.nblk = (int)((g->geom.vh + 127) / 128);
     }
     return hop_dispatch(g->lat.N, g->lat.rep, P, prm, rebuild, epi, stream);
 }

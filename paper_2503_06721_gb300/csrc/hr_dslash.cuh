@@ -41,6 +41,11 @@ struct HopParams {
     const double *carry;      // [nrhs] added to the total before finalising, or nullptr
     int fin;                  // FIN_WRITE / FIN_CG_ALPHA / FIN_CG_BETA
     CgState *state;           // [nrhs]   (CG epilogues; skip converged rhs)
+    // right-hand-side-fastest block order: block b serves rhs b % nrhs and
+    // site block b / nrhs, so the blocks of one site range run back to back
+    // and every rhs after the first finds the links in L2
+    int rhs_inner;
+    int nblk;                 // site blocks per rhs
     // fused CG update (compute-type arrays, same layout as the fields)
     FieldView r, x, p;
 };
@@ -86,9 +91,11 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const HopParams prm)
     using LIO = LinkIO<P, REAL, NCOMP>;
 
     const Geom &g = prm.g;
-    const int rhs = blockIdx.y;
+    const int rhs = prm.rhs_inner ? (int)(blockIdx.x % prm.nrhs) : (int)blockIdx.y;
+    const int bx = prm.rhs_inner ? (int)(blockIdx.x / prm.nrhs) : (int)blockIdx.x;
+    const int nblk = prm.rhs_inner ? prm.nblk : (int)gridDim.x;
     if (prm.state && cg_idle(prm.state[rhs])) return;   // uniform per block
-    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long i = (long)bx * blockDim.x + threadIdx.x;
     const bool active = i < g.vh;
     const R sg = prm.dagger ? (R)-1 : (R)1;
 
@@ -120,9 +127,10 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const HopParams prm)
                     h[r][c] = psi[r][c] + sp * ipow(ephase(mu, r), psi[2 + eperm(mu, r)][c]);
             cx<R> chi[2][D];
             const uint4 *lp = LIO::slot_ptr(prm.links, tile, k, lane);
+            const bool keep = prm.rhs_inner;   // other rhs re-read these links from L2
             if constexpr (REBUILD) {
                 cx<R> Wf[N * N];
-                LIO::load(lp, Wf);
+                LIO::load(lp, Wf, keep);
                 cx<R> F[N][N];
 #pragma unroll
                 for (int a = 0; a < N; a++)
@@ -141,7 +149,7 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const HopParams prm)
                 }
             } else if constexpr (REAL) {
                 R W[D * D];
-                LIO::load(lp, W);
+                LIO::load(lp, W, keep);
 #pragma unroll
                 for (int row = 0; row < D; row++) {
                     cx<R> s0 = {0, 0}, s1 = {0, 0};
@@ -155,7 +163,7 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const HopParams prm)
                 }
             } else {
                 cx<R> W[D * D];
-                LIO::load(lp, W);
+                LIO::load(lp, W, keep);
 #pragma unroll
                 for (int row = 0; row < D; row++) {
                     cx<R> s0 = {0, 0}, s1 = {0, 0};
@@ -209,8 +217,7 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const HopParams prm)
             v[0] = (double)n2;
         }
         double tot[1];
-        if (grid_reduce<1>(v, prm.partials + (size_t)rhs * gridDim.x, prm.counters + rhs, gridDim.x,
-                           blockIdx.x, tot))
+        if (grid_reduce<1>(v, prm.partials + (size_t)rhs * nblk, prm.counters + rhs, nblk, bx, tot))
             hop_finalize(prm, rhs, tot[0]);
     } else {
         // fused CG update with out = A p:  x += alpha p;  r -= alpha A p;  |r|^2
@@ -239,8 +246,7 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const HopParams prm)
             v[0] = (double)n2;
         }
         double tot[1];
-        if (grid_reduce<1>(v, prm.partials + (size_t)rhs * gridDim.x, prm.counters + rhs, gridDim.x,
-                           blockIdx.x, tot))
+        if (grid_reduce<1>(v, prm.partials + (size_t)rhs * nblk, prm.counters + rhs, nblk, bx, tot))
             hop_finalize(prm, rhs, tot[0]);
     }
 }
@@ -248,7 +254,6 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const HopParams prm)
 // host-side launchers, instantiated per (N, REP, P) in hr_dslash_inst.cu
 template <int N, int REP, int P>
 hr_status launch_hop(const HopParams &prm, bool rebuild, int epi, cudaStream_t stream);
-template <int N, int REP, int P>
-hr_status launch_hop_mrhs(const HopParams &prm, int epi, int *err, cudaStream_t stream);
+
 
 }  // namespace hr

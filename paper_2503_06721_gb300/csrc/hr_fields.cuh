@@ -232,21 +232,23 @@ struct LinkIO {
     }
     // the whole slot, streamed with evict-first loads (each link is read once
     // per operator application)
-    __device__ __forceinline__ static void load(const uint4 *p, cx<R> (&W)[NCOMP])
+    // keep = true: normal caching (the links will be read again soon)
+    __device__ __forceinline__ static uint4 ld(const uint4 *p, bool keep) { return keep ? __ldcg(p) : __ldcs(p); }
+    __device__ __forceinline__ static void load(const uint4 *p, cx<R> (&W)[NCOMP], bool keep = false)
     {
 #pragma unroll
         for (int j = 0; j < NCHUNK; j++) {
-            const uint4 v = __ldcs(p + (size_t)j * HR_TILE);
+            const uint4 v = ld(p + (size_t)j * HR_TILE, keep);
 #pragma unroll
             for (int k = 0; k < VPC; k++)
                 if (j * VPC + k < NCOMP) W[j * VPC + k] = cunpack(v, k);
         }
     }
-    __device__ __forceinline__ static void load(const uint4 *p, R (&W)[NCOMP])
+    __device__ __forceinline__ static void load(const uint4 *p, R (&W)[NCOMP], bool keep = false)
     {
 #pragma unroll
         for (int j = 0; j < NCHUNK; j++) {
-            const uint4 v = __ldcs(p + (size_t)j * HR_TILE);
+            const uint4 v = ld(p + (size_t)j * HR_TILE, keep);
 #pragma unroll
             for (int k = 0; k < VPC; k++)
                 if (j * VPC + k < NCOMP) W[j * VPC + k] = runpack(v, k);

@@ -23,84 +23,86 @@ __device__ inline void store_entry(int P, bool real, char *dst, cx<double> v)
 }
 
 // ---------------------------------------------------------------------------
-// represent: one thread per (tile, slot, lane) so the record writes coalesce.
-// slot k < 4 : U_R(x, mu)        with -1 if bc_mu = -1 and x_mu = L_mu - 1
-// slot k >= 4: U_R(x - mu, mu)^dag = R(U_F(x - mu, mu)^dag), -1 if x_mu = 0
+// represent: one thread per link (x, mu), x of parity p with half index
+// tile*32 + lane, so every link is represented exactly once (in FP64) and
+// written twice, both writes coalesced:
+//   slot mu   of x's record (parity p):        U_R(x, mu)
+//   slot 4+mu of (x+mu)'s record (parity 1-p): U_R(x, mu)^dag = R(U(x, mu)^dag)
+// with -1 on both if bc_mu = -1 and x_mu = L_mu - 1 (Sec. 5.3.1).  The
+// fundamental records get U and U^dag (the in-kernel rebuild applies the
+// sign itself).
 // ---------------------------------------------------------------------------
 template <int N, int REP>
-__global__ void __launch_bounds__(128) represent_kernel(const double2 *__restrict__ UF, const Geom g, int parity,
-                                                        const RepOut o)
+__global__ void __launch_bounds__(128) represent_kernel(const double2 *__restrict__ UF, const Geom g, const RepOut o0,
+                                                        const RepOut o1)
 {
     constexpr int D = rep_dim(N, REP);
+    constexpr bool REAL = rep_real(REP);
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = (int)(t & 31);
-    const long rest = t >> 5;
-    const int slot = (int)(rest & 7);
-    const long tile = rest >> 3;
-    if (tile >= g.ntiles) return;
+    long rest = t >> 5;
+    const int mu = (int)(rest & 3);
+    rest >>= 2;
+    const long tile = rest % g.ntiles;
+    const int parity = (int)(rest / g.ntiles);
+    if (parity > 1) return;
     const long i = tile * HR_TILE + lane;
     if (i >= g.vh) return;
-    Site s = site_of(g, i, parity);
-    const int mu = slot & 3;
-    const bool fwd = slot < 4;
-    int c[4] = {s.c[0], s.c[1], s.c[2], s.c[3]};
+    const Site s = site_of(g, i, parity);
+    const long ib = neighbour(g, s, mu, +1);   // half index of x + mu in parity 1 - p
+    const long tb = ib / HR_TILE;
+    const int lb = (int)(ib % HR_TILE);
+    const RepOut &of = parity == 0 ? o0 : o1;   // records of x's parity
+    const RepOut &ob = parity == 0 ? o1 : o0;   // records of (x+mu)'s parity
     const int L[4] = {g.T, g.X, g.Y, g.Z};
-    if (!fwd) c[mu] = (c[mu] - 1 + L[mu]) % L[mu];
-    const long lex = (((long)c[0] * g.X + c[1]) * g.Y + c[2]) * g.Z + c[3];
+    const long lex = lex_of(g, s);
     const double2 *u = UF + ((size_t)lex * 4 + mu) * N * N;
     cx<double> U[N][N];
     for (int a = 0; a < N; a++)
         for (int b = 0; b < N; b++) {
-            double2 v = u[a * N + b];
-            if (fwd)
-                U[a][b] = {v.x, v.y};
-            else
-                U[b][a] = {v.x, -v.y};   // dagger
+            const double2 v = u[a * N + b];
+            U[a][b] = {v.x, v.y};
         }
-    const bool neg = g.bc[mu] == -1 && (fwd ? s.c[mu] == L[mu] - 1 : s.c[mu] == 0);
+    const bool neg = g.bc[mu] == -1 && s.c[mu] == L[mu] - 1;
     bool any_rep = false;
-    for (int p = 0; p < 4; p++) any_rep |= o.rep[p] != nullptr;
-    constexpr bool REAL = rep_real(REP);
+    for (int p = 0; p < 4; p++) any_rep |= of.rep[p] != nullptr;
     if (any_rep) {
         cx<double> Rm[D][D];
         represent<N, REP>(U, Rm);
         const double sg = neg ? -1.0 : 1.0;
         for (int r = 0; r < D; r++)
             for (int q = 0; q < D; q++) {
-                const int c = r * D + q;
                 const cx<double> v = sg * Rm[r][q];
                 for (int P = 0; P < 4; P++) {
-                    if (!o.rep[P]) continue;
-                    char *dst = reinterpret_cast<char *>(o.rep[P]) + link_offset(P, REAL, D * D, tile, slot, lane, c);
-                    store_entry(P, REAL, dst, v);
+                    if (!of.rep[P]) continue;
+                    store_entry(P, REAL, reinterpret_cast<char *>(of.rep[P]) + link_offset(P, REAL, D * D, tile, mu, lane, r * D + q), v);
+                    // the dagger: entry (q, r) of the backward slot
+                    store_entry(P, REAL, reinterpret_cast<char *>(ob.rep[P]) + link_offset(P, REAL, D * D, tb, 4 + mu, lb, q * D + r), conj(v));
                 }
             }
     }
     for (int r = 0; r < N; r++)
-        for (int q = 0; q < N; q++) {
-            const int c = r * N + q;
+        for (int q = 0; q < N; q++)
             for (int P = 0; P < 4; P++) {
-                if (!o.fund[P]) continue;
-                char *dst = reinterpret_cast<char *>(o.fund[P]) + link_offset(P, false, N * N, tile, slot, lane, c);
-                store_entry(P, false, dst, U[r][q]);
+                if (!of.fund[P]) continue;
+                store_entry(P, false, reinterpret_cast<char *>(of.fund[P]) + link_offset(P, false, N * N, tile, mu, lane, r * N + q), U[r][q]);
+                store_entry(P, false, reinterpret_cast<char *>(ob.fund[P]) + link_offset(P, false, N * N, tb, 4 + mu, lb, q * N + r), conj(U[r][q]));
             }
-        }
 }
 
 template <int N, int REP>
 hr_status represent_launch(const hr_gauge &gg, const double2 *UF, cudaStream_t stream)
 {
     const Geom &g = gg.geom;
-    for (int parity = 0; parity < 2; parity++) {
-        RepOut o;
+    RepOut o[2];
+    for (int parity = 0; parity < 2; parity++)
         for (int p = 0; p < 4; p++) {
-            o.rep[p] = gg.rep[p][parity];
-            o.fund[p] = gg.fund[p][parity];
+            o[parity].rep[p] = gg.rep[p][parity];
+            o[parity].fund[p] = gg.fund[p][parity];
         }
-        const long threads = g.ntiles * 8 * HR_TILE;
-        represent_kernel<N, REP><<<(unsigned)((threads + 127) / 128), 128, 0, stream>>>(UF, g, parity, o);
-        HR_LAUNCH_CHECK("represent_kernel");
-    }
+    const long threads = 2 * g.ntiles * 4 * HR_TILE;
+    represent_kernel<N, REP><<<(unsigned)((threads + 127) / 128), 128, 0, stream>>>(UF, g, o[0], o[1]);
+    HR_LAUNCH_CHECK("represent_kernel");
     return HR_OK;
 }
 
