@@ -136,3 +136,17 @@ def test_table1_reading_is_consistent():
         assert r["T"] * (r["N"] ** 2 - 1) == r["C2"] * r["D"]
         if r["rep"] == "ASYM":
             assert r["T_printed"] * (r["N"] ** 2 - 1) != r["C2"] * r["D"]
+
+
+def test_input_generator_philox_known_answers():
+    """The seeded generator is Philox4x32-10 (Salmon et al., SC'11): the
+    published known-answer vectors of the reference implementation."""
+    import torch
+    from paper_2503_06721_gb300 import synth
+    kat = [((0, 0, 0, 0), (0, 0), (0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8)),
+           ((0xffffffff,) * 4, (0xffffffff, 0xffffffff), (0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd)),
+           ((0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344), (0xa4093822, 0x299f31d0),
+            (0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1))]
+    for ctr, key, want in kat:
+        got = synth.philox4x32(tuple(torch.tensor([c], dtype=torch.int64) for c in ctr), key)
+        assert tuple(int(x) for x in got) == want
