@@ -8,7 +8,9 @@ input, as an HMC force evaluation of the fermion monomial does it:
   1. represent the fundamental gauge field (FP64 and FP32 stored links),
   2. D_eo applications in FP32 and FP64 (the metric's kernel, event-timed),
   3. mixed-precision CG (FP32 inner, FP64 defect correction) on
-     Dhat^dag Dhat x = phi to a true relative residual of 1e-10,
+     Dhat^dag Dhat x = phi to a true relative residual of 1e-10
+     (--residual df64 forms the intermediate true residuals in float-float
+     and confirms the one that meets the tolerance in FP64),
   4. Y = Dhat x and the fermion force of S = phi^dag (Dhat^dag Dhat)^-1 phi.
 
 value: algorithmic ("compulsory") bytes of every hopping-kernel launch of the
@@ -58,6 +60,27 @@ def hop_bytes(D: int, real_links: bool, prec: int, vh: int) -> int:
     lp = D * D * (cb // 2 if real_links else cb)
     sp = 4 * D * cb + (4 if prec >= 2 else 0)
     return vh * (8 * lp + 2 * sp)
+
+
+def job_throughput(step_bytes_local: float, ms_local: float, steps: int, dist=None, device=None):
+    """Whole-job throughput of N replicas: every rank processed step_bytes_local
+    per step; the job time is the slowest rank's.  Returns (GB/s, ms per step)."""
+    import torch
+    ms = float(ms_local)
+    world = 1
+    if dist is not None and dist.is_initialized():
+        world = dist.get_world_size()
+        t = torch.tensor([ms, step_bytes_local], dtype=torch.float64, device=device)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        ms = float(tmax[0].item())
+        total_bytes = float(tsum[1].item())
+    else:
+        total_bytes = step_bytes_local
+    ms_per_step = ms / steps
+    return total_bytes / (ms_per_step * 1e-3) / 1e9, ms_per_step
 
 
 class Clocks:
@@ -141,8 +164,14 @@ def run_ours(args, rank, world, local_rank):
     wl_r = dataclasses.replace(wl, seed=wl.seed + 1000 * rank)
     U = wl_r.links(device=dev)
     phi = synth.gaussian_spinor(vh, D, wl_r.seed + 7, device=dev)
-    g = hr.Gauge(lat, U, precs=("f64", "f32"), stored=True)
+    res_prec = hr.PRECS[args.residual]
+    g = hr.Gauge(lat, U, precs=("f64", "f32") + (("df64",) if res_prec == hr.DF64 else ()), stored=True)
     stream = torch.cuda.current_stream()
+    # pick the hopping-kernel variants of the bandwidth-bound precision (setup,
+    # outside the timed region; the solver would otherwise do it at its first call)
+    g.tune(hr.F32)
+    variants = {name: g.hop_variant(hr.F32, epi) for name, epi in
+                (("store", hr.EPI_STORE), ("store_norm", hr.EPI_STORE_NORM), ("cg_update", hr.EPI_CG_UPDATE))}
     x32 = phi.to(torch.complex64)
     y32 = torch.empty_like(x32)
     y64 = torch.empty_like(phi)
@@ -165,7 +194,7 @@ def run_ours(args, rank, world, local_rank):
         g.apply(hr.EVEN, hr.F64, phi_dev, out=y64)
         pev[2].record(stream)
         x, res, st = g.cg_solve(hr.EO_PRECOND, phi_dev, tol=TOL, max_iter=20000, inner=hr.F32,
-                                inner_tol=1e-5)
+                                inner_tol=1e-5, residual=res_prec)
         pev[3].record(stream)
         Y = g.apply(hr.EO_PRECOND, hr.F64, x)
         F = g.force(hr.EO_PRECOND, x, Y, coeff=-1.0)
@@ -176,7 +205,11 @@ def run_ours(args, rank, world, local_rank):
         r = res[0]
         # hop launches of this step by precision
         h32 = n_deo + 4 * r["iters"]
-        h64 = 1 + 4 * (r["outer_iters"] + 1) + 2 + 2
+        # FP64-class (FP64 or DF64, 16 bytes per complex either way) launches: the
+        # D_eo, 4 per true residual after each inner solve (the first one, of
+        # x = 0, is b itself) and 4 for the FP64 confirmation of a DF64 one, 2
+        # for Dhat x and 2 odd-half hops inside the force
+        h64 = 1 + 4 * (r["outer_iters"] + (res_prec == hr.DF64)) + 2 + 2
         work["bytes"] += h32 * hop_bytes(D, real, hr.F32, vh) + h64 * hop_bytes(D, real, hr.F64, vh)
         work["res"] = r
         return x, F
@@ -211,13 +244,8 @@ def run_ours(args, rank, world, local_rank):
     ms = t0.elapsed_time(t1)
     step_bytes = work["bytes"] / args.steps
     res = work["res"]
-    if dist:
-        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    ms_per_step = ms / args.steps
+    value, ms_per_step = job_throughput(step_bytes, ms, args.steps, dist, dev)
     phase_ms = {k: round(v / args.steps, 2) for k, v in phases.items()}
-    value = world * step_bytes / (ms_per_step * 1e-3) / 1e9
     deo_ms_avg = sum(deo_times) / len(deo_times)
     deo_bytes = hop_bytes(D, real, hr.F32, vh)
     peak, peak_kind = _peaks()
@@ -247,35 +275,40 @@ def run_ours(args, rank, world, local_rank):
         t1.record(stream)
         torch.cuda.synchronize()
         ems = t0.elapsed_time(t1)
-        if dist:
-            tt = torch.tensor([ems], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ems = float(tt.item())
-        e2e = {"value": world * (work["bytes"] / args.steps) / (ems / args.steps * 1e-3) / 1e9,
-               "unit": UNIT, "ms_per_step": ems / args.steps,
+        evalue, ems_step = job_throughput(work["bytes"] / args.steps, ems, args.steps, dist, dev)
+        e2e = {"value": round(evalue, 1), "unit": UNIT, "ms_per_step": round(ems_step, 3),
                "h2d_bytes_per_step": U_h.numel() * 16 + phi_h.numel() * 16,
                "d2h_bytes_per_step": X_h.numel() * 16 + F_h.numel() * 8}
 
     # time to 1e-10: plain FP64 CG vs defect correction with low-precision inner solves
     cg = None
     if rank == 0 and not args.no_cg_compare:
-        g2 = hr.Gauge(lat, U, precs=("f64", "f32", "f16", "bf16"), stored=True)
+        g2 = hr.Gauge(lat, U, precs=("f64", "f32", "f16", "bf16", "df64"), stored=True)
         cg = {}
-        for name, inner in (("fp64", hr.F64), ("mixed_fp32", hr.F32), ("mixed_fp16", hr.F16),
-                            ("mixed_bf16", hr.BF16)):
+        cg_variants = (("fp64", hr.F64, hr.F64), ("mixed_fp32", hr.F32, hr.F64), ("mixed_fp16", hr.F16, hr.F64),
+                    ("mixed_bf16", hr.BF16, hr.F64), ("mixed_fp32_df64res", hr.F32, hr.DF64),
+                    ("mixed_fp16_df64res", hr.F16, hr.DF64))
+        for name, inner, resid in cg_variants:
             g2.cg_solve(hr.EO_PRECOND, phi, tol=1e-3, inner=inner, max_iter=200, check=False)
             torch.cuda.synchronize()
             t0.record(stream)
             x, r, st = g2.cg_solve(hr.EO_PRECOND, phi, tol=TOL, max_iter=20000, inner=inner,
-                                   inner_tol=1e-5 if inner == hr.F32 else 2e-3, check=False)
+                                   inner_tol=1e-5 if inner == hr.F32 else 2e-3, residual=resid,
+                                   check=False)
             t1.record(stream)
             torch.cuda.synchronize()
             cg[name] = {"ms": round(t0.elapsed_time(t1), 2), "iters": r[0]["iters"],
                         "outer": r[0]["outer_iters"], "true_rel_residual": r[0]["true_rel_residual"],
                         "status": r[0]["status"]}
-        for name in ("mixed_fp32", "mixed_fp16", "mixed_bf16"):
+        for name, _, _ in cg_variants[1:]:
             cg[name]["speedup_vs_fp64"] = round(cg["fp64"]["ms"] / cg[name]["ms"], 2)
         g2.close()
+
+    batched = None
+    if rank == 0 and not args.no_batched:
+        g.close()
+        torch.cuda.empty_cache()
+        batched = batched_compare(hr, synth, dev, stream)
 
     out = None
     if rank == 0:
@@ -283,27 +316,31 @@ def run_ours(args, rank, world, local_rank):
         out = {
             "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" + ("+df64" if res_prec == hr.DF64 else ""),
             "data": "synthetic (seeded Philox4x32-10 links exp(i 0.4 H) + Haar gauge transform, "
                     "Gaussian pseudofermion)",
             "config": {"workload": f"SU(3) sextet (SYM, D_R=6) 32^3x64, m0=-0.3, even/odd, "
                                    f"mixed FP32/FP64 CG to 1e-10 + force",
+                       "true_residual_arith": args.residual,
                        "lattice": list(wl.dims), "N": wl.N, "rep": wl.rep, "m0": wl.m0,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (FP32 links 4.8 GB per parity)",
                        "deo_per_step": n_deo, "cg_iters_per_step": res["iters"],
                        "cg_outer_per_step": res["outer_iters"],
                        "true_rel_residual": res["true_rel_residual"]},
-            "roofline": {"bound": "hbm", "kernel": "hop_kernel<3,SYM,F32> (D_eo, stored links)",
+            "roofline": {"bound": "hbm", "kernel": f"hopping kernel <3,SYM,F32> variant {variants['store']} (D_eo, stored links)",
                          "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind,
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": args.traffic, "deo_ms": round(deo_ms_avg, 4),
                          "bytes_per_launch": deo_bytes},
+            "hop_variants_f32": variants,
             "gpu_launches": int(launches),
             "phases_ms": phase_ms,
             "clocks": ck,
             "e2e": e2e,
             "cg": cg,
+            "batched": batched,
             "cpu_baseline": cpu,
         }
         print(json.dumps(out), flush=True)
@@ -311,6 +348,66 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+    return out
+
+
+def batched_compare(hr, synth, dev, stream, rep="ASYM"):
+    """SU(4) 24^3 x 48 with 12 point sources (4 spins x 3 colour subsets) plus
+    8^4, 12^4, 16^3 x 32 instances (4 Gaussian rhs each, m0 = -0.1, -0.25, -0.4):
+    one batched FP32-inner / FP64-refined solve to 1e-10 against plain FP64 CG
+    solving every right-hand side one after the other."""
+    import torch
+    wl = synth.WORKLOADS[f"su4_{rep.lower()}_48x24x24x24"]
+    specs = [(wl.dims, wl.m0, 12)] + [(d, m, 4) for d, m in synth.UNEVEN_INSTANCES]
+    gauges, bs, nr = [], [], []
+    for i, (dims, m0, n) in enumerate(specs):
+        lat = hr.Lattice(wl.N, rep, dims, wl.bc, m0)
+        V = lat.volume
+        gauges.append(hr.Gauge(lat, synth.random_links(V, wl.N, wl.eps, wl.seed + i, device=dev),
+                               precs=("f64", "f32")))
+        if n == 12:
+            b = torch.zeros((12, V // 2, 4, lat.D), dtype=torch.complex128, device=dev)
+            for s in range(4):
+                for k in range(3):
+                    for c in range(lat.D):
+                        if c % 3 == k:
+                            b[3 * s + k, 0, s, c] = 1.0
+        else:
+            b = synth.gaussian_spinor(V // 2, lat.D, 700 + i, device=dev, nrhs=n)
+        bs.append(b.contiguous())
+        nr.append(n)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"workload": f"SU(4) {rep} 24^3x48 (12 point sources) + 8^4, 12^4, 16^3x32 (4 rhs each)",
+           "rhs_total": sum(nr)}
+    for name, inner in (("batched_mixed_fp32", hr.F32), ("batched_fp64", hr.F64)):
+        xs = [torch.zeros_like(b) for b in bs]
+        hr.cg_solve_batched(gauges, hr.EO_PRECOND, bs, xs, nr, tol=1e-3, inner=inner, check=False)
+        xs = [torch.zeros_like(b) for b in bs]
+        torch.cuda.synchronize()
+        e0.record(stream)
+        res, st = hr.cg_solve_batched(gauges, hr.EO_PRECOND, bs, xs, nr, tol=TOL, inner=inner, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"ms": round(e0.elapsed_time(e1), 2), "status": hr.STATUS.get(st, st),
+                     "max_true_rel_residual": max(r["true_rel_residual"] for r in res),
+                     "max_iters": max(r["iters"] for r in res)}
+    # plain FP64 CG, one right-hand side at a time
+    torch.cuda.synchronize()
+    e0.record(stream)
+    worst, its = 0.0, 0
+    for g, b, n in zip(gauges, bs, nr):
+        for k in range(n):
+            x, r, st = g.cg_solve(hr.EO_PRECOND, b[k].contiguous(), tol=TOL, inner=hr.F64, check=False)
+            worst = max(worst, r[0]["true_rel_residual"])
+            its += r[0]["iters"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["sequential_fp64"] = {"ms": round(e0.elapsed_time(e1), 2), "max_true_rel_residual": worst,
+                              "total_iters": its}
+    out["speedup_batched_mixed_vs_sequential_fp64"] = round(
+        out["sequential_fp64"]["ms"] / out["batched_mixed_fp32"]["ms"], 2)
+    for g in gauges:
+        g.close()
     return out
 
 
@@ -407,16 +504,18 @@ def run_deo(args, local_rank):
     build.build()
     wl = synth.WORKLOADS[args.workload]
     lat = hr.Lattice(wl.N, wl.rep, wl.dims, wl.bc, wl.m0)
-    prec = {"f64": hr.F64, "f32": hr.F32, "f16": hr.F16, "bf16": hr.BF16}[args.prec]
+    prec = hr.PRECS[args.prec]
     g = hr.Gauge(lat, wl.links(device=dev), precs=(args.prec,), stored=not args.rebuild,
                  rebuild=args.rebuild)
     vh = lat.volume // 2
     n = args.nrhs
+    g.tune(prec, nrhs=n)
+    variant = g.hop_variant(prec, hr.EPI_STORE, n)
     x = synth.gaussian_spinor(vh, lat.D, 3, device=dev, nrhs=n)
     x = x if prec == hr.F64 else (x.to(torch.complex64) if prec == hr.F32 else
                                   hr.field_convert(lat, hr.EVEN, x, hr.F64, prec, n))
     y = g.apply(hr.EVEN, prec, x, nrhs=n)
-    for _ in range(args.warmup):
+    for _ in range(max(args.warmup, 1)):
         g.apply(hr.EVEN, prec, x, out=y, nrhs=n)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -426,8 +525,8 @@ def run_deo(args, local_rank):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    cb = [16, 8, 4, 4][prec]
-    sp = 4 * lat.D * cb + (4 if prec >= 2 else 0)
+    cb = [16, 8, 4, 4, 16][prec]
+    sp = 4 * lat.D * cb + (4 if prec in (hr.F16, hr.BF16) else 0)
     if args.rebuild:
         lp = wl.N * wl.N * cb
     else:
@@ -435,7 +534,8 @@ def run_deo(args, local_rank):
     # compulsory bytes: every link once, every input and output spinor once
     byts = vh * (8 * lp + 2 * n * sp)
     print(json.dumps({"mode": "deo", "workload": args.workload, "prec": args.prec, "nrhs": n,
-                      "links": "rebuild" if args.rebuild else "stored", "ms": round(ms, 4),
+                      "links": "rebuild" if args.rebuild else "stored", "variant": variant,
+                      "ms": round(ms, 4),
                       "GBs": round(byts / (ms * 1e-3) / 1e9, 1), "bytes_per_launch": byts}))
 
 
@@ -450,10 +550,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cg-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-FP64 solve comparison")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--mode", choices=["step", "deo"], default="step",
                     help="deo: only D_eo applications (profiler captures)")
-    ap.add_argument("--prec", choices=["f64", "f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--prec", choices=["f64", "f32", "f16", "bf16", "df64"], default="f32")
+    ap.add_argument("--residual", choices=["df64", "f64"], default="f64",
+                    help="arithmetic of the defect-correction true residuals (df64: float-float, "
+                         "confirmed once in FP64 when it meets the tolerance)")
     ap.add_argument("--rebuild", action="store_true", help="deo mode: rebuild links in-kernel")
     ap.add_argument("--nrhs", type=int, default=1, help="deo mode: right-hand sides per application")
     ap.add_argument("--traffic", type=float, default=None,

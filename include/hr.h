@@ -15,6 +15,8 @@
  * Spinor fields (Sec. 3.1.2, Table "elementary data types"):
  *   HR_F64 / HR_F32: [nrhs][nsites][spin 0..3][colour 0..D_R-1] interleaved
  *     complex (re, im) in double / float.
+ *   HR_DF64: the same layout with every complex as four floats
+ *     (re.hi, re.lo, im.hi, im.lo), value = hi + lo.
  *   HR_F16 / HR_BF16 (reduced storage with one scale per site):
  *     each right-hand side is a block of hr_field_bytes(..., 1) bytes holding
  *     [nsites][4][D_R] pairs (re, im) of half / bfloat16 values v/s_x,
@@ -45,9 +47,11 @@ extern "C" {
 /* Supported representations, Table 1 (Sec. 2.3). HR_ASYM is "2AS". */
 typedef enum { HR_FUND = 0, HR_ADJ = 1, HR_SYM = 2, HR_ASYM = 3 } hr_rep;
 
-/* Storage precision of fields and links.  F64 computes in double, the others
- * in float.  F16/BF16 spinors carry one float scale per site. */
-typedef enum { HR_F64 = 0, HR_F32 = 1, HR_F16 = 2, HR_BF16 = 3 } hr_prec;
+/* Storage precision of fields and links.  F64 computes in double, F32/F16/BF16
+ * in float; F16/BF16 spinors carry one float scale per site.  DF64 holds every
+ * FP64 value as an exact pair of floats (hi, lo), 16 bytes per complex like
+ * F64, and computes in float-float arithmetic (about 48 significant bits). */
+typedef enum { HR_F64 = 0, HR_F32 = 1, HR_F16 = 2, HR_BF16 = 3, HR_DF64 = 4 } hr_prec;
 
 /* Output parity / operator selector (Sec. 4.3.3, Eq. dmeo and Eq. deo):
  *   HR_EVEN        out_e = D_eo in_o   (hopping block, includes the -1/2)
@@ -114,6 +118,44 @@ hr_status hr_gauge_set_link_mode(hr_gauge *g, hr_link_mode mode);
 
 /* Frees the link storage and solver workspace (synchronises the device). */
 hr_status hr_gauge_destroy(hr_gauge *g);
+
+/* ------------------------------------------------------------------ */
+/* Kernel-variant autotuning                                             */
+/* ------------------------------------------------------------------ */
+/* The hopping kernel (Eq. D_m^R) is compiled in several variants that
+ * produce bitwise identical results and differ in how a warp moves its
+ * site records and in register budget:
+ *   HR_HOP_DIRECT        each lane loads its own neighbour spinors;
+ *   HR_HOP_STAGED        the warp gathers its 32 records cooperatively
+ *                        through shared memory (cp.async, double-buffered);
+ *   HR_HOP_STAGED_TIGHT  the staged kernel at a smaller register budget
+ *                        (D_R > 4 only).
+ * FP64 and DF64 have the direct variant only.  Launches are identified by
+ * their epilogue: HR_EPI_STORE (out = a H in), HR_EPI_STORE_NORM (the same
+ * plus |out|^2), HR_EPI_CG_UPDATE (the fused r -= alpha A p, x += alpha p,
+ * |r|^2 of a CG iteration). */
+enum { HR_HOP_DIRECT = 0, HR_HOP_STAGED = 1, HR_HOP_STAGED_TIGHT = 2 };
+enum { HR_EPI_STORE = 0, HR_EPI_STORE_NORM = 1, HR_EPI_CG_UPDATE = 2 };
+
+/* Times every compiled variant of every epilogue in precision prec for g's
+ * lattice, current link mode and nrhs right-hand sides, on zero-filled
+ * scratch fields that it allocates and frees, and records the fastest in g;
+ * later launches with that (prec, link mode, epilogue, nrhs == 1 or > 1) use
+ * the record.  BLOCKS the calling thread.  hr_cg_solve and
+ * hr_cg_solve_batched call it for their inner precision when no record
+ * exists yet, unless autotuning is switched off with hr_gauge_set_tuning.
+ * Errors: HR_ERR_INVALID (precision not stored), HR_ERR_NOMEM, HR_ERR_CUDA. */
+hr_status hr_tune(hr_gauge *g, hr_prec prec, int nrhs, void *stream);
+
+/* autotune: 1 (default) lets the solvers tune before their first iteration
+ * in a precision, 0 never tunes implicitly.  variant: -1 (default) uses the
+ * tuned record, or a fixed default where none exists; HR_HOP_* forces that
+ * variant for every launch on g (clamped to the variants compiled for a
+ * precision), which is how the variants are compared. */
+hr_status hr_gauge_set_tuning(hr_gauge *g, int autotune, int variant);
+
+/* The variant a launch on g would use now; -1 for bad arguments. */
+int hr_gauge_hop_variant(const hr_gauge *g, hr_prec prec, int epilogue, int nrhs);
 
 /* ------------------------------------------------------------------ */
 /* Field helpers                                                         */
@@ -183,6 +225,12 @@ typedef struct {
                              correction around an inner CG in that precision */
     double inner_tol;     /* relative reduction asked of each inner solve */
     int use_initial_guess;/* 1: x holds the start vector; 0: start from 0 */
+    hr_prec residual;     /* arithmetic of the defect-correction true residuals
+                             (inner != HR_F64 only): HR_F64 (0, the default) or
+                             HR_DF64, float-float with the handle's DF64 links,
+                             which must be stored.  With HR_DF64 a residual that
+                             meets tol_rel is confirmed once in FP64, so the
+                             reported true_rel_residual is always the FP64 one. */
 } hr_cg_params;
 
 typedef struct {

@@ -24,19 +24,23 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
               f"-I{INCLUDE}", f"-I{CSRC}"]
 
+PRECS = ["HR_F64", "HR_F32", "HR_F16", "HR_BF16", "HR_DF64"]
 PAIRS = [(2, "HR_FUND"), (2, "HR_ADJ"), (2, "HR_SYM"), (3, "HR_FUND"), (3, "HR_ADJ"), (3, "HR_SYM"),
          (3, "HR_ASYM"), (4, "HR_FUND"), (4, "HR_ASYM")]
 
 
 def _units():
     units = []
-    for src in ("hr_api.cu", "hr_cg.cu", "hr_blas.cu", "hr_static.cu"):
+    for src in ("hr_api.cu", "hr_cg.cu", "hr_blas.cu", "hr_static.cu", "hr_tune.cu"):
         units.append((CSRC / src, OBJDIR / (Path(src).stem + ".o"), []))
     for n, rep in PAIRS:
         tag = f"{n}_{rep.lower()[3:]}"
-        for src in ("hr_dslash_inst.cu", "hr_gauge_inst.cu"):
-            units.append((CSRC / src, OBJDIR / f"{Path(src).stem}_{tag}.o",
-                          [f"-DHR_INST_N={n}", f"-DHR_INST_REP={rep}"]))
+        units.append((CSRC / "hr_gauge_inst.cu", OBJDIR / f"hr_gauge_inst_{tag}.o",
+                      [f"-DHR_INST_N={n}", f"-DHR_INST_REP={rep}"]))
+        for prec in PRECS:
+            units.append((CSRC / "hr_dslash_inst.cu",
+                          OBJDIR / f"hr_dslash_inst_{tag}_{prec.lower()[3:]}.o",
+                          [f"-DHR_INST_N={n}", f"-DHR_INST_REP={rep}", f"-DHR_INST_P={prec}"]))
     return units
 
 
@@ -69,7 +73,12 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
 
     jobs = jobs or max(1, os.cpu_count() or 1)
     # longest units first
-    todo.sort(key=lambda c: ("dslash" not in c[-3], c[-3]))
+    def weight(cmd):
+        obj = cmd[-1]
+        if "dslash" in obj:
+            return 0 if obj.endswith(("_f32.o", "_f16.o", "_bf16.o")) else 1
+        return 2
+    todo.sort(key=weight)
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         for f in cf.as_completed([ex.submit(run, c) for c in todo]):
             f.result()

@@ -38,10 +38,11 @@ long long launch_counter() { return g_launches.load(); }
     X(3, HR_ASYM) X(4, HR_FUND) X(4, HR_ASYM)
 
 #define HR_DECL(N_, R_)                                                                                    \
-    extern template hr_status launch_hop<N_, R_, HR_F64>(const HopParams &, bool, int, cudaStream_t);     \
-    extern template hr_status launch_hop<N_, R_, HR_F32>(const HopParams &, bool, int, cudaStream_t);     \
-    extern template hr_status launch_hop<N_, R_, HR_F16>(const HopParams &, bool, int, cudaStream_t);     \
-    extern template hr_status launch_hop<N_, R_, HR_BF16>(const HopParams &, bool, int, cudaStream_t);    \
+    extern template hr_status launch_hop<N_, R_, HR_F64>(const HopParams &, bool, int, int, cudaStream_t);     \
+    extern template hr_status launch_hop<N_, R_, HR_F32>(const HopParams &, bool, int, int, cudaStream_t);     \
+    extern template hr_status launch_hop<N_, R_, HR_F16>(const HopParams &, bool, int, int, cudaStream_t);     \
+    extern template hr_status launch_hop<N_, R_, HR_BF16>(const HopParams &, bool, int, int, cudaStream_t);    \
+    extern template hr_status launch_hop<N_, R_, HR_DF64>(const HopParams &, bool, int, int, cudaStream_t);    \
     extern template hr_status represent_launch<N_, R_>(const hr_gauge &, const double2 *, cudaStream_t); \
     extern template hr_status force_launch<N_, R_>(const ForceParams &, cudaStream_t);
 HR_PAIRS(HR_DECL)
@@ -54,16 +55,18 @@ bool pair_supported(int N, int rep)
     return false;
 }
 
-hr_status hop_dispatch(int N, int rep, int P, const HopParams &prm, bool rebuild, int epi, cudaStream_t stream)
+hr_status hop_dispatch(int N, int rep, int P, const HopParams &prm, bool rebuild, int epi, int variant,
+                       cudaStream_t stream)
 {
-#define HR_HOP(N_, R_)                                                                        \
-    if (N == N_ && rep == R_) {                                                               \
-        switch (P) {                                                                          \
-        case HR_F64: return launch_hop<N_, R_, HR_F64>(prm, rebuild, epi, stream);            \
-        case HR_F32: return launch_hop<N_, R_, HR_F32>(prm, rebuild, epi, stream);            \
-        case HR_F16: return launch_hop<N_, R_, HR_F16>(prm, rebuild, epi, stream);            \
-        case HR_BF16: return launch_hop<N_, R_, HR_BF16>(prm, rebuild, epi, stream);          \
-        }                                                                                     \
+#define HR_HOP(N_, R_)                                                                             \
+    if (N == N_ && rep == R_) {                                                                    \
+        switch (P) {                                                                               \
+        case HR_F64: return launch_hop<N_, R_, HR_F64>(prm, rebuild, epi, variant, stream);        \
+        case HR_F32: return launch_hop<N_, R_, HR_F32>(prm, rebuild, epi, variant, stream);        \
+        case HR_F16: return launch_hop<N_, R_, HR_F16>(prm, rebuild, epi, variant, stream);        \
+        case HR_BF16: return launch_hop<N_, R_, HR_BF16>(prm, rebuild, epi, variant, stream);      \
+        case HR_DF64: return launch_hop<N_, R_, HR_DF64>(prm, rebuild, epi, variant, stream);      \
+        }                                                                                          \
     }
     HR_PAIRS(HR_HOP)
 #undef HR_HOP
@@ -235,7 +238,7 @@ long max_blocks_for(const hr_gauge *g)
 hr_status hop(const hr_gauge *g, int P, int out_parity, int dagger, const FieldView &in, const FieldView &out,
               const FieldView *diag, double a, double b, int nrhs, cudaStream_t stream, int epi, const Scratch *sc,
               int fin, const double *carry, double *red_out, const FieldView *r, const FieldView *x,
-              const FieldView *p)
+              const FieldView *p, int variant)
 {
     HopParams prm;
     memset(&prm, 0, sizeof prm);
@@ -271,7 +274,31 @@ hr_status hop(const hr_gauge *g, int P, int out_parity, int dagger, const FieldV
         prm.rhs_inner = 1;
         prm.nblk = (int)((g->geom.vh + 127) / 128);
     }
-    return hop_dispatch(g->lat.N, g->lat.rep, P, prm, rebuild, epi, stream);
+    if (variant < 0) variant = hop_variant(g, P, rebuild, epi, nrhs);
+    return hop_dispatch(g->lat.N, g->lat.rep, P, prm, rebuild, epi, variant, stream);
+}
+
+int hop_variant_count(const hr_gauge *g, int P)
+{
+    if (P == HR_F64 || P == HR_DF64) return 1;
+    return g->D <= 4 ? 2 : 3;
+}
+
+int hop_variant(const hr_gauge *g, int P, bool rebuild, int epi, int nrhs)
+{
+    const int nv = hop_variant_count(g, P);
+    if (g->force_variant >= 0) return std::min(g->force_variant, nv - 1);
+    const int t = g->tuned[P][rebuild ? 1 : 0][epi][nrhs > 1 ? 1 : 0];
+    if (t >= 0 && t < nv) return t;
+    if (nv == 1) return HOP_DIRECT;
+    // untuned default, from measurements on GB300 (32^4 .. 64x32^3 lattices):
+    // the staged kernel wins every fused CG update (r, x, p are read and
+    // written at the warp's own sites) and the stores of the 8x8 real adjoint
+    // and the SU(4) fundamental, where per-lane gathers saturate the L1
+    // data pipe; the direct kernel wins the other stores
+    if (epi == EPI_CG_UPDATE) return HOP_STAGED;
+    if ((g->lat.rep == HR_ADJ && g->D >= 8) || (g->lat.rep == HR_FUND && g->lat.N >= 4)) return HOP_STAGED;
+    return HOP_DIRECT;
 }
 
 }  // namespace hr
@@ -328,7 +355,7 @@ hr_status hr_generators(int N, double *T)
 
 size_t hr_field_bytes(const hr_lattice_desc *lat, hr_parity par, hr_prec prec, int nrhs)
 {
-    if (check_lattice(lat) != HR_OK || prec < HR_F64 || prec > HR_BF16 || nrhs < 1) return 0;
+    if (check_lattice(lat) != HR_OK || prec < HR_F64 || prec > HR_DF64 || nrhs < 1) return 0;
     long V = lat_volume(*lat);
     long ns = par == HR_FULL ? V : V / 2;
     return field_rhs_bytes(ns, rep_dim(lat->N, lat->rep), prec) * (size_t)nrhs;
@@ -342,10 +369,13 @@ hr_status hr_represent_gauge(const hr_lattice_desc *lat, const void *U_fund, uns
     hr_status st = check_lattice(lat);
     if (st != HR_OK) return st;
     if (!U_fund) { set_error("hr_represent_gauge: U_fund is NULL"); return HR_ERR_INVALID; }
-    if (prec_mask == 0 || (prec_mask & ~0xFu)) { set_error("bad prec_mask 0x%x", prec_mask); return HR_ERR_INVALID; }
+    if (prec_mask == 0 || (prec_mask & ~0x1Fu)) { set_error("bad prec_mask 0x%x", prec_mask); return HR_ERR_INVALID; }
     if (link_modes == 0 || (link_modes & ~0x3u)) { set_error("bad link_modes 0x%x", link_modes); return HR_ERR_INVALID; }
     hr_gauge *g = new hr_gauge;
     memset(g, 0, sizeof *g);
+    memset(g->tuned, -1, sizeof g->tuned);
+    g->force_variant = -1;
+    g->autotune = 1;
     g->lat = *lat;
     g->geom = make_geom(*lat);
     g->D = rep_dim(lat->N, lat->rep);
@@ -356,7 +386,7 @@ hr_status hr_represent_gauge(const hr_lattice_desc *lat, const void *U_fund, uns
     cudaGetDevice(&g->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     auto fail = [&](hr_status e) { hr_gauge_destroy(g); return e; };
-    for (int P = 0; P < 4; P++) {
+    for (int P = 0; P < HR_NPREC; P++) {
         if (!(prec_mask & (1u << P))) continue;
         if (link_modes & (1u << HR_LINKS_STORED)) {
             size_t b = link_record_bytes(g->geom, P, g->real, g->D * g->D);
@@ -368,7 +398,8 @@ hr_status hr_represent_gauge(const hr_lattice_desc *lat, const void *U_fund, uns
                 if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemsetAsync"));
             }
         }
-        if (link_modes & (1u << HR_LINKS_REBUILD)) {
+        // float-float is compiled for stored links only
+        if ((link_modes & (1u << HR_LINKS_REBUILD)) && P != HR_DF64) {
             size_t b = link_record_bytes(g->geom, P, false, lat->N * lat->N);
             g->fund_bytes[P] = b;
             for (int par = 0; par < 2; par++) {
@@ -421,7 +452,7 @@ hr_status hr_gauge_destroy(hr_gauge *g)
 {
     if (!g) return HR_OK;
     cudaDeviceSynchronize();
-    for (int P = 0; P < 4; P++)
+    for (int P = 0; P < HR_NPREC; P++)
         for (int par = 0; par < 2; par++) {
             if (g->rep[P][par]) cudaFree(g->rep[P][par]);
             if (g->fund[P][par]) cudaFree(g->fund[P][par]);
@@ -438,7 +469,7 @@ hr_status hr_gauge_destroy(hr_gauge *g)
 static hr_status check_apply(const hr_gauge *g, hr_parity par, hr_prec prec, const void *in, void *out, int nrhs)
 {
     if (!g || !in || !out || nrhs < 1) { set_error("hr_dirac_apply: NULL argument or nrhs < 1"); return HR_ERR_INVALID; }
-    if (prec < HR_F64 || prec > HR_BF16 || !(g->prec_mask & (1u << prec))) {
+    if (prec < HR_F64 || prec > HR_DF64 || !(g->prec_mask & (1u << prec))) {
         set_error("precision %d not stored in this gauge handle (mask 0x%x)", (int)prec, g->prec_mask);
         return HR_ERR_INVALID;
     }
@@ -499,7 +530,7 @@ hr_status hr_field_convert(const hr_lattice_desc *lat, hr_parity par, hr_prec sr
     hr_status st = check_lattice(lat);
     if (st != HR_OK) return st;
     if (!src || !dst || nrhs < 1 || src == dst) { set_error("hr_field_convert: bad pointers or nrhs"); return HR_ERR_INVALID; }
-    if (src_prec < HR_F64 || src_prec > HR_BF16 || dst_prec < HR_F64 || dst_prec > HR_BF16) {
+    if (src_prec < HR_F64 || src_prec > HR_DF64 || dst_prec < HR_F64 || dst_prec > HR_DF64) {
         set_error("hr_field_convert: bad precision");
         return HR_ERR_INVALID;
     }
@@ -521,7 +552,7 @@ hr_status hr_field_dot(const hr_lattice_desc *lat, hr_parity par, hr_prec prec, 
 {
     hr_status st = check_lattice(lat);
     if (st != HR_OK) return st;
-    if (!a || !b || !out || nrhs < 1 || prec < HR_F64 || prec > HR_BF16) {
+    if (!a || !b || !out || nrhs < 1 || prec < HR_F64 || prec > HR_DF64) {
         set_error("hr_field_dot: bad arguments");
         return HR_ERR_INVALID;
     }

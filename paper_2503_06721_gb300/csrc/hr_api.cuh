@@ -32,11 +32,20 @@ long max_blocks_for(const hr_gauge *g);
 // the handle's reduction scratch for nrhs right-hand sides (grown and zeroed on demand)
 hr_status scratch_reserve(const hr_gauge *g, int nrhs, cudaStream_t stream, Scratch *out);
 
+// variant < 0: the handle's tuned (or default) choice for this launch
 hr_status hop(const hr_gauge *g, int P, int out_parity, int dagger, const FieldView &in, const FieldView &out,
               const FieldView *diag, double a, double b, int nrhs, cudaStream_t stream, int epi,
               const Scratch *sc = nullptr, int fin = FIN_WRITE, const double *carry = nullptr,
               double *red_out = nullptr, const FieldView *r = nullptr, const FieldView *x = nullptr,
-              const FieldView *p = nullptr);
+              const FieldView *p = nullptr, int variant = -1);
+
+// kernel variants compiled for the handle's pair in precision P
+int hop_variant_count(const hr_gauge *g, int P);
+// the variant a launch would use (forced, tuned, or the fixed default)
+int hop_variant(const hr_gauge *g, int P, bool rebuild, int epi, int nrhs);
+// time every variant of every epilogue in precision P for the handle's
+// lattice, link mode and nrhs, record the fastest (blocks the host)
+hr_status tune_hops(hr_gauge *g, int P, int nrhs, cudaStream_t stream);
 
 // number of kernel launches counted so far (graph contents counted when they run)
 long long launch_counter();

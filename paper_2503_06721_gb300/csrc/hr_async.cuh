@@ -1,0 +1,25 @@
+// hr_async.cuh -- per-thread asynchronous 16-byte copies global -> shared
+// (cp.async, L1-bypassing) and their group bookkeeping.
+#pragma once
+
+#include <stdint.h>
+
+namespace hr {
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// 16 bytes global -> shared; both addresses 16-byte aligned
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+// close the group of copies issued since the last commit (an empty group is allowed)
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most N of this thread's committed groups are still in flight
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+}  // namespace hr

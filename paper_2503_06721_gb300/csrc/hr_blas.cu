@@ -38,7 +38,14 @@ __global__ void __launch_bounds__(BLAS_THREADS) k_residual_init(const BlasParams
     if (i < bp.nsites) {
         cx<double> b[4][D], ax[4][D];
         SpinorIO<HR_F64, D>::load_rw(bp.b, rhs, i, b);
-        SpinorIO<HR_F64, D>::load_rw(bp.c, rhs, i, ax);
+        if (bp.c.data) {
+            SpinorIO<HR_F64, D>::load_rw(bp.c, rhs, i, ax);
+        } else {   // x = 0: r = b
+#pragma unroll
+            for (int s = 0; s < 4; s++)
+#pragma unroll
+                for (int c = 0; c < D; c++) ax[s][c] = {0.0, 0.0};
+        }
 #pragma unroll
         for (int s = 0; s < 4; s++)
 #pragma unroll
@@ -211,8 +218,10 @@ __global__ void __launch_bounds__(BLAS_THREADS) k_dot(const BlasParams bp)
         for (int s = 0; s < 4; s++)
 #pragma unroll
             for (int c = 0; c < D; c++) {
-                v[0] += (double)a[s][c].re * b[s][c].re + (double)a[s][c].im * b[s][c].im;
-                v[1] += (double)a[s][c].re * b[s][c].im - (double)a[s][c].im * b[s][c].re;
+                const double ar = (double)a[s][c].re, ai = (double)a[s][c].im;
+                const double br = (double)b[s][c].re, bi = (double)b[s][c].im;
+                v[0] += ar * br + ai * bi;
+                v[1] += ar * bi - ai * br;
             }
     }
     double tot[2];
@@ -249,9 +258,20 @@ static inline dim3 grid_of(const BlasParams &bp)
     default: set_error("bad precision %d", P_); return HR_ERR_INVALID; \
     }
 
+// the same with the float-float storage (conversions and dot products only)
+#define HR_FOR_PX(P_, PN, BODY)                              \
+    switch (P_) {                                           \
+    case HR_F64: { constexpr int PN = HR_F64; BODY; } break; \
+    case HR_F32: { constexpr int PN = HR_F32; BODY; } break; \
+    case HR_F16: { constexpr int PN = HR_F16; BODY; } break; \
+    case HR_BF16: { constexpr int PN = HR_BF16; BODY; } break; \
+    case HR_DF64: { constexpr int PN = HR_DF64; BODY; } break; \
+    default: set_error("bad precision %d", P_); return HR_ERR_INVALID; \
+    }
+
 hr_status blas_convert(int D, int Pdst, int Psrc, const BlasParams &bp, cudaStream_t st)
 {
-    HR_FOR_D(D, HR_FOR_P(Pdst, PD, HR_FOR_P(Psrc, PS, (k_convert<DD, PD, PS><<<grid_of(bp), BLAS_THREADS, 0, st>>>(bp)))));
+    HR_FOR_D(D, HR_FOR_PX(Pdst, PD, HR_FOR_PX(Psrc, PS, (k_convert<DD, PD, PS><<<grid_of(bp), BLAS_THREADS, 0, st>>>(bp)))));
     HR_LAUNCH_CHECK("k_convert");
     return HR_OK;
 }
@@ -293,7 +313,7 @@ hr_status blas_outer_update(int D, const BlasParams &bp, cudaStream_t st)
 
 hr_status blas_dot(int D, int P, const BlasParams &bp, cudaStream_t st)
 {
-    HR_FOR_D(D, HR_FOR_P(P, PN, (k_dot<DD, PN><<<grid_of(bp), BLAS_THREADS, 0, st>>>(bp))));
+    HR_FOR_D(D, HR_FOR_PX(P, PN, (k_dot<DD, PN><<<grid_of(bp), BLAS_THREADS, 0, st>>>(bp))));
     HR_LAUNCH_CHECK("k_dot");
     return HR_OK;
 }

@@ -55,6 +55,7 @@ struct Inst {
     hr_cg_result *res;
     std::vector<int> iters;
     bool done;
+    bool df;                   // true residuals in float-float (until one meets the tolerance)
 };
 
 hr_status apply_A(const Ctx &c, int P, const FieldView &v, const FieldView &out, const FieldView &q,
@@ -125,11 +126,33 @@ hr_status cg_iteration(const Ctx &c, const Vecs &v)
     return blas_xpay_beta(D, P, bp, c.s);
 }
 
-// r = b - A x (FP64) with |r|^2, |b|^2 into red[2 rhs], state initialised with tol
-hr_status true_residual(const Inst &in, double tol, int cap)
+// r = b - A x (FP64) with |r|^2, |b|^2 into red[2 rhs], state initialised with tol.
+// With in.df, A x is computed in float-float: x is split into (hi, lo) pairs in
+// r64 (a float-float complex takes 16 bytes, like an FP64 one, so the FP64
+// buffers serve), A is applied with the DF64 links, and the product is
+// rounded back to FP64 in place before the residual is formed in FP64.
+hr_status true_residual(const Inst &in, double tol, int cap, bool x_zero)
 {
     const Ctx &c = in.c;
-    hr_status st = apply_A(c, HR_F64, in.vx, in.q2, in.q64, in.t64);
+    hr_status st = HR_OK;
+    if (x_zero) {
+        // A 0 = 0: the residual is b itself
+    } else if (in.df) {
+        BlasParams cv;
+        memset(&cv, 0, sizeof cv);
+        cv.nsites = c.ns;
+        cv.nrhs = c.nrhs;
+        cv.s = 1.0;
+        cv.a = in.r64;
+        cv.b = in.vx;
+        st = blas_convert(c.D, HR_DF64, HR_F64, cv, c.s);
+        if (st == HR_OK) st = apply_A(c, HR_DF64, in.r64, in.q2, in.q64, in.t64);
+        cv.a = in.q2;
+        cv.b = in.q2;
+        if (st == HR_OK) st = blas_convert(c.D, HR_F64, HR_DF64, cv, c.s);
+    } else {
+        st = apply_A(c, HR_F64, in.vx, in.q2, in.q64, in.t64);
+    }
     if (st != HR_OK) return st;
     BlasParams bp;
     memset(&bp, 0, sizeof bp);
@@ -137,7 +160,7 @@ hr_status true_residual(const Inst &in, double tol, int cap)
     bp.nrhs = c.nrhs;
     bp.a = in.r64;
     bp.b = in.vb;
-    bp.c = in.q2;
+    if (!x_zero) bp.c = in.q2;
     bp.partials = c.sc.partials;
     bp.counters = c.sc.counters;
     bp.red_out = c.sc.red;
@@ -289,7 +312,7 @@ hr_status read_states(const Inst &in, std::vector<CgState> &out)
 
 // carve the instance's vectors out of its handle's workspace
 hr_status prepare(Inst &in, const hr_gauge *g, hr_parity sys, const void *b, void *x, int nrhs, int Pin,
-                  hr_cg_result *res, cudaStream_t s)
+                  int Pres, hr_cg_result *res, cudaStream_t s)
 {
     Ctx &c = in.c;
     c.g = g;
@@ -340,6 +363,7 @@ hr_status prepare(Inst &in, const hr_gauge *g, hr_parity sys, const void *b, voi
     in.res = res;
     in.iters.assign(nrhs, 0);
     in.done = false;
+    in.df = mixed && Pres == HR_DF64;
     for (int k = 0; k < nrhs; k++) {
         res[k].iters = 0;
         res[k].outer_iters = 0;
@@ -359,6 +383,18 @@ hr_status solve_all(std::vector<Inst> &ins, const hr_cg_params *prm, cudaStream_
     for (auto &in : ins)
         if (!prm->use_initial_guess)
             HR_CUDA_CHECK(cudaMemsetAsync(in.vx.data, 0, in.vx.rhs_stride * in.c.nrhs, s));
+    // pick the hopping-kernel variants of the inner precision before the
+    // iterations are captured into a graph
+    for (auto &in : ins) {
+        hr_gauge *g = const_cast<hr_gauge *>(in.c.g);
+        const int P = in.v.P;
+        const int rb = g->mode == HR_LINKS_REBUILD ? 1 : 0;
+        if (g->autotune && g->force_variant < 0 && hop_variant_count(g, P) > 1 &&
+            g->tuned[P][rb][EPI_CG_UPDATE][in.c.nrhs > 1 ? 1 : 0] < 0) {
+            hr_status ts = tune_hops(g, P, in.c.nrhs, s);
+            if (ts != HR_OK) return ts;
+        }
+    }
     InnerGraph ig;
     hr_status st = ig.build(ins);
     if (st != HR_OK) return st;
@@ -369,7 +405,7 @@ hr_status solve_all(std::vector<Inst> &ins, const hr_cg_params *prm, cudaStream_
         const int cap = std::max(1, prm->max_iter - total);
         for (auto &in : ins) {
             if (in.done) continue;
-            st = true_residual(in, tol, cap);
+            st = true_residual(in, tol, cap, outer == 0 && !prm->use_initial_guess);
             if (st != HR_OK) return st;
         }
         for (size_t i = 0; i < ins.size(); i++) {
@@ -379,6 +415,23 @@ hr_status solve_all(std::vector<Inst> &ins, const hr_cg_params *prm, cudaStream_
                                           cudaMemcpyDeviceToHost, s));
         }
         HR_CUDA_CHECK(cudaStreamSynchronize(s));
+        // a float-float residual that meets the tolerance is confirmed in FP64,
+        // which the instance then keeps using
+        bool rerun = false;
+        for (size_t i = 0; i < ins.size(); i++) {
+            Inst &in = ins[i];
+            if (in.done || !in.df) continue;
+            bool all_ok = true;
+            for (int k = 0; k < in.c.nrhs; k++) all_ok &= rel_residual(red[i][2 * k], red[i][2 * k + 1]) <= tol;
+            if (!all_ok) continue;
+            in.df = false;
+            st = true_residual(in, tol, cap, false);
+            if (st != HR_OK) return st;
+            HR_CUDA_CHECK(cudaMemcpyAsync(red[i].data(), in.c.sc.red, sizeof(double) * 2 * in.c.nrhs,
+                                          cudaMemcpyDeviceToHost, s));
+            rerun = true;
+        }
+        if (rerun) HR_CUDA_CHECK(cudaStreamSynchronize(s));
         bool any_active = false;
         double worst = 0;
         for (size_t i = 0; i < ins.size(); i++) {
@@ -506,6 +559,15 @@ static hr_status check_params(const hr_gauge *g, hr_parity sys, const hr_cg_para
         set_error("CG: inner_tol must be in (0, 1)");
         return HR_ERR_INVALID;
     }
+    if (params->residual != HR_F64 && params->residual != HR_DF64) {
+        set_error("CG: residual must be HR_F64 or HR_DF64");
+        return HR_ERR_INVALID;
+    }
+    if (params->residual == HR_DF64 && params->inner != HR_F64 &&
+        (!g->rep[HR_DF64][0] || g->mode != HR_LINKS_STORED)) {
+        set_error("CG: float-float residuals need stored DF64 links in the handle");
+        return HR_ERR_INVALID;
+    }
     return HR_OK;
 }
 
@@ -525,7 +587,7 @@ extern "C" hr_status hr_cg_solve(const hr_gauge *g, hr_parity sys, const void *b
     if (st != HR_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     std::vector<Inst> ins(1);
-    st = prepare(ins[0], g, sys, b, x, nrhs, params->inner, res, s);
+    st = prepare(ins[0], g, sys, b, x, nrhs, params->inner, params->residual, res, s);
     if (st != HR_OK) return st;
     return solve_all(ins, params, s);
 }
@@ -557,7 +619,7 @@ extern "C" hr_status hr_cg_solve_batched(int n_inst, const hr_gauge *const *g, h
         }
         hr_status st = check_params(g[i], sys, params);
         if (st != HR_OK) return st;
-        st = prepare(ins[i], g[i], sys, b[i], x[i], nrhs[i], params->inner, res + off, s);
+        st = prepare(ins[i], g[i], sys, b[i], x[i], nrhs[i], params->inner, params->residual, res + off, s);
         if (st != HR_OK) return st;
         off += nrhs[i];
     }

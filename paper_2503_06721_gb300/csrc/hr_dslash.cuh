@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const HopParams prm)
 #pragma unroll
             for (int s = 0; s < 4; s++)
 #pragma unroll
-                for (int c = 0; c < D; c++) acc[s][c] = a * acc[s][c] + b * d[s][c];
+                for (int c = 0; c < D; c++) acc[s][c] = axpby(a, acc[s][c], b, d[s][c]);
         } else {
 #pragma unroll
             for (int s = 0; s < 4; s++)
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const HopParams prm)
 #pragma unroll
             for (int s = 0; s < 4; s++)
 #pragma unroll
-                for (int c = 0; c < D; c++) n2 += acc[s][c].re * acc[s][c].re + acc[s][c].im * acc[s][c].im;
+                for (int c = 0; c < D; c++) norm_acc(n2, acc[s][c]);
             v[0] = (double)n2;
         }
         double tot[1];
@@ -236,9 +236,9 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const HopParams prm)
                 SIO::load_spin(prm.p, rhs, i, s, psc, pp);
 #pragma unroll
                 for (int c = 0; c < D; c++) {
-                    rr[c] = rr[c] - alpha * acc[s][c];
-                    xx[c] = xx[c] + alpha * pp[c];
-                    n2 += rr[c].re * rr[c].re + rr[c].im * rr[c].im;
+                    rmac(rr[c], -alpha, acc[s][c]);
+                    rmac(xx[c], alpha, pp[c]);
+                    norm_acc(n2, rr[c]);
                 }
                 CIO::store_spin(prm.r, rhs, i, s, rr);
                 CIO::store_spin(prm.x, rhs, i, s, xx);
@@ -251,9 +251,25 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const HopParams prm)
     }
 }
 
+// Kernel variants of one hopping launch.  Every variant computes the same
+// bits; which one is fastest depends on N, R, precision, link mode, epilogue,
+// lattice and right-hand-side count, and the autotuner picks among them.
+//   HOP_DIRECT        hop_kernel: each lane loads its own neighbour records
+//   HOP_STAGED        hop_staged_kernel: warp-cooperative gathers through
+//                     shared memory, register budget for 2 (D_R > 4) or 3
+//                     (D_R <= 4) blocks of 128 threads per SM
+//   HOP_STAGED_TIGHT  the same held to 3 blocks per SM (D_R > 4 only)
+// FP64 and DF64 have the direct kernel only: they are bound by FP64 (or
+// float-float) arithmetic, not by the memory system.
+enum { HOP_DIRECT = 0, HOP_STAGED = 1, HOP_STAGED_TIGHT = 2 };
+__host__ __device__ constexpr int hop_variants(int N, int REP, int P)
+{
+    return (P == HR_F64 || P == HR_DF64) ? 1 : rep_dim(N, REP) <= 4 ? 2 : 3;
+}
+
 // host-side launchers, instantiated per (N, REP, P) in hr_dslash_inst.cu
 template <int N, int REP, int P>
-hr_status launch_hop(const HopParams &prm, bool rebuild, int epi, cudaStream_t stream);
+hr_status launch_hop(const HopParams &prm, bool rebuild, int epi, int variant, cudaStream_t stream);
 
 
 }  // namespace hr

@@ -1,36 +1,89 @@
 // hr_dslash_inst.cu -- launcher and explicit instantiation of the hopping
-// kernel for one (N, representation) pair.  The build compiles this file once
-// per pair with -DHR_INST_N=<N> -DHR_INST_REP=<rep> so the instantiations
-// compile in parallel.
-#include "hr_dslash.cuh"
+// kernel for one (N, representation, precision).  The build compiles this
+// file once per combination with -DHR_INST_N=<N> -DHR_INST_REP=<rep>
+// -DHR_INST_P=<prec> so the instantiations compile in parallel.
+#include "hr_dslash_staged.cuh"
 
 namespace hr {
 
-template <int N, int REP, int P, bool RB>
-static hr_status launch_epi(const HopParams &prm, int epi, cudaStream_t stream)
+// register budget (resident blocks of 128 threads per SM) of a staged variant
+template <int N, int REP>
+constexpr int staged_minb(int variant)
 {
+    return rep_dim(N, REP) <= 4 ? 3 : (variant == HOP_STAGED ? 1 : 3);
+}
+
+template <int N, int REP, int P, bool RB, int EPI, int MINB>
+static hr_status launch_staged(const HopParams &prm, dim3 grid, cudaStream_t stream)
+{
+    constexpr size_t smem = StageShape<P, rep_dim(N, REP), EPI>::SMEM;
+    auto kern = hop_staged_kernel<N, REP, P, RB, EPI, MINB>;
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess) return cuda_fail(attr, "cudaFuncSetAttribute(hop_staged_kernel)");
+    kern<<<grid, 128, smem, stream>>>(prm);
+    HR_LAUNCH_CHECK("hop_staged_kernel");
+    return HR_OK;
+}
+
+template <int N, int REP, int P, bool RB, int MINB>
+static hr_status launch_staged_epi(const HopParams &prm, int epi, dim3 grid, cudaStream_t stream)
+{
+    switch (epi) {
+    case EPI_STORE: return launch_staged<N, REP, P, RB, EPI_STORE, MINB>(prm, grid, stream);
+    case EPI_STORE_NORM: return launch_staged<N, REP, P, RB, EPI_STORE_NORM, MINB>(prm, grid, stream);
+    case EPI_CG_UPDATE: return launch_staged<N, REP, P, RB, EPI_CG_UPDATE, MINB>(prm, grid, stream);
+    default: set_error("bad epilogue %d", epi); return HR_ERR_INVALID;
+    }
+}
+
+template <int N, int REP, int P, bool RB>
+static hr_status launch_epi(const HopParams &prm, int epi, int variant, cudaStream_t stream)
+{
+    if constexpr (P == HR_DF64) {
+        // float-float is compiled for stored links and plain stores only (the
+        // solver uses it for its FP64-class true residuals)
+        if (RB || epi != EPI_STORE) {
+            set_error("DF64 is available for stored links and plain applications only");
+            return HR_ERR_UNSUPPORTED;
+        }
+    }
+    if (variant < 0 || variant >= hop_variants(N, REP, P)) {
+        set_error("hop kernel variant %d not compiled for this precision", variant);
+        return HR_ERR_INVALID;
+    }
     dim3 block(128);
     const unsigned nb = (unsigned)((prm.g.vh + 127) / 128);
     dim3 grid = prm.rhs_inner ? dim3(nb * (unsigned)prm.nrhs) : dim3(nb, (unsigned)prm.nrhs);
-    switch (epi) {
-    case EPI_STORE: hop_kernel<N, REP, P, RB, EPI_STORE><<<grid, block, 0, stream>>>(prm); break;
-    case EPI_STORE_NORM: hop_kernel<N, REP, P, RB, EPI_STORE_NORM><<<grid, block, 0, stream>>>(prm); break;
-    case EPI_CG_UPDATE: hop_kernel<N, REP, P, RB, EPI_CG_UPDATE><<<grid, block, 0, stream>>>(prm); break;
-    default: set_error("bad epilogue %d", epi); return HR_ERR_INVALID;
+    if constexpr (hop_variants(N, REP, P) > 1) {
+        if (variant == HOP_STAGED)
+            return launch_staged_epi<N, REP, P, RB, staged_minb<N, REP>(HOP_STAGED)>(prm, epi, grid, stream);
+    }
+    if constexpr (hop_variants(N, REP, P) > 2) {
+        if (variant == HOP_STAGED_TIGHT)
+            return launch_staged_epi<N, REP, P, RB, staged_minb<N, REP>(HOP_STAGED_TIGHT)>(prm, epi, grid, stream);
+    }
+    if constexpr (P == HR_DF64) {
+        if constexpr (!RB) hop_kernel<N, REP, P, false, EPI_STORE><<<grid, block, 0, stream>>>(prm);
+    } else {
+        switch (epi) {
+        case EPI_STORE: hop_kernel<N, REP, P, RB, EPI_STORE><<<grid, block, 0, stream>>>(prm); break;
+        case EPI_STORE_NORM: hop_kernel<N, REP, P, RB, EPI_STORE_NORM><<<grid, block, 0, stream>>>(prm); break;
+        case EPI_CG_UPDATE: hop_kernel<N, REP, P, RB, EPI_CG_UPDATE><<<grid, block, 0, stream>>>(prm); break;
+        default: set_error("bad epilogue %d", epi); return HR_ERR_INVALID;
+        }
     }
     HR_LAUNCH_CHECK("hop_kernel");
     return HR_OK;
 }
 
 template <int N, int REP, int P>
-hr_status launch_hop(const HopParams &prm, bool rebuild, int epi, cudaStream_t stream)
+hr_status launch_hop(const HopParams &prm, bool rebuild, int epi, int variant, cudaStream_t stream)
 {
-    return rebuild ? launch_epi<N, REP, P, true>(prm, epi, stream) : launch_epi<N, REP, P, false>(prm, epi, stream);
+    return rebuild ? launch_epi<N, REP, P, true>(prm, epi, variant, stream)
+                   : launch_epi<N, REP, P, false>(prm, epi, variant, stream);
 }
 
-template hr_status launch_hop<HR_INST_N, HR_INST_REP, HR_F64>(const HopParams &, bool, int, cudaStream_t);
-template hr_status launch_hop<HR_INST_N, HR_INST_REP, HR_F32>(const HopParams &, bool, int, cudaStream_t);
-template hr_status launch_hop<HR_INST_N, HR_INST_REP, HR_F16>(const HopParams &, bool, int, cudaStream_t);
-template hr_status launch_hop<HR_INST_N, HR_INST_REP, HR_BF16>(const HopParams &, bool, int, cudaStream_t);
+template hr_status launch_hop<HR_INST_N, HR_INST_REP, HR_INST_P>(const HopParams &, bool, int, int, cudaStream_t);
 
 }  // namespace hr

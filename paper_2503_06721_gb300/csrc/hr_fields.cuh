@@ -41,6 +41,9 @@ struct SpinorIO {
         if constexpr (P == HR_F64) {
             const uint4 &v = raw[n];
             return {__hiloint2double((int)v.y, (int)v.x), __hiloint2double((int)v.w, (int)v.z)};
+        } else if constexpr (P == HR_DF64) {
+            const uint4 &v = raw[n];
+            return {df(__uint_as_float(v.x), __uint_as_float(v.y)), df(__uint_as_float(v.z), __uint_as_float(v.w))};
         } else if constexpr (P == HR_F32) {
             const uint4 &v = raw[n >> 1];
             return (n & 1) ? cx<R>{__uint_as_float(v.z), __uint_as_float(v.w)}
@@ -101,6 +104,8 @@ struct SpinorIO {
             if constexpr (P == HR_F64) {
                 const double2 d = *reinterpret_cast<const double2 *>(b + 16 * c);
                 v[c] = {d.x, d.y};
+            } else if constexpr (P == HR_DF64) {
+                v[c] = S::ld(*reinterpret_cast<const float4 *>(b + 16 * c));
             } else if constexpr (P == HR_F32) {
                 const float2 d = *reinterpret_cast<const float2 *>(b + 8 * c);
                 v[c] = {d.x, d.y};
@@ -118,6 +123,8 @@ struct SpinorIO {
         for (int c = 0; c < D; c++) {
             if constexpr (P == HR_F64)
                 *reinterpret_cast<double2 *>(b + 16 * c) = make_double2(v[c].re, v[c].im);
+            else if constexpr (P == HR_DF64)
+                *reinterpret_cast<float4 *>(b + 16 * c) = S::st(v[c]);
             else
                 *reinterpret_cast<float2 *>(b + 8 * c) = make_float2(v[c].re, v[c].im);
         }
@@ -144,6 +151,9 @@ struct SpinorIO {
                 raw[n].y = (unsigned)__double2hiint(v.re);
                 raw[n].z = (unsigned)__double2loint(v.im);
                 raw[n].w = (unsigned)__double2hiint(v.im);
+            } else if constexpr (P == HR_DF64) {
+                raw[n] = make_uint4(__float_as_uint(v.re.hi), __float_as_uint(v.re.lo), __float_as_uint(v.im.hi),
+                                    __float_as_uint(v.im.lo));
             } else if constexpr (P == HR_F32) {
                 if (n & 1) {
                     raw[n >> 1].z = __float_as_uint(v.re);
@@ -206,6 +216,8 @@ struct LinkIO {
     {
         if constexpr (P == HR_F64) {
             return {__hiloint2double((int)v.y, (int)v.x), __hiloint2double((int)v.w, (int)v.z)};
+        } else if constexpr (P == HR_DF64) {
+            return {df(__uint_as_float(v.x), __uint_as_float(v.y)), df(__uint_as_float(v.z), __uint_as_float(v.w))};
         } else if constexpr (P == HR_F32) {
             return {__uint_as_float(word(v, 2 * k)), __uint_as_float(word(v, 2 * k + 1))};
         } else {
@@ -220,6 +232,8 @@ struct LinkIO {
     {
         if constexpr (P == HR_F64) {
             return k == 0 ? __hiloint2double((int)v.y, (int)v.x) : __hiloint2double((int)v.w, (int)v.z);
+        } else if constexpr (P == HR_DF64) {
+            return k == 0 ? df(__uint_as_float(v.x), __uint_as_float(v.y)) : df(__uint_as_float(v.z), __uint_as_float(v.w));
         } else if constexpr (P == HR_F32) {
             return __uint_as_float(word(v, k));
         } else {

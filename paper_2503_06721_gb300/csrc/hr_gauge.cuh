@@ -15,9 +15,9 @@ struct hr_gauge {
     unsigned link_modes;
     hr_link_mode mode;
     // link records per [precision][output parity]
-    void *rep[4][2];
-    void *fund[4][2];
-    size_t rep_bytes[4], fund_bytes[4];
+    void *rep[HR_NPREC][2];
+    void *fund[HR_NPREC][2];
+    size_t rep_bytes[HR_NPREC], fund_bytes[HR_NPREC];
     // T_R^a tables for the force, [(N*N-1)][D][D] complex double
     double *TR;
     // field workspace (operator/force temporaries, solver vectors; grown on demand)
@@ -31,13 +31,18 @@ struct hr_gauge {
     void *pinned;         // host staging for solver state (pinned)
     size_t pinned_bytes;
     int device;
+    // hopping-kernel variant per [precision][rebuilt links][epilogue][nrhs > 1]
+    // chosen by the autotuner; -1 = not tuned (a fixed default applies)
+    signed char tuned[HR_NPREC][2][3][2];
+    int force_variant;    // >= 0: every launch uses this variant (testing)
+    int autotune;         // 1: the solver tunes its inner precision before iterating
 };
 
 namespace hr {
 
 struct RepOut {
-    void *rep[4];    // record base for this parity per precision (nullptr = skip)
-    void *fund[4];
+    void *rep[HR_NPREC];    // record base for this parity per precision (nullptr = skip)
+    void *fund[HR_NPREC];
 };
 
 // per-(N, REP) instantiated operations (hr_gauge_inst.cu)
@@ -58,7 +63,8 @@ template <int N, int REP>
 hr_status force_launch(const ForceParams &fp, cudaStream_t stream);
 
 // precision dispatch of the hop kernel for a runtime (N, rep)
-hr_status hop_dispatch(int N, int rep, int P, const HopParams &prm, bool rebuild, int epi, cudaStream_t stream);
+hr_status hop_dispatch(int N, int rep, int P, const HopParams &prm, bool rebuild, int epi, int variant,
+                       cudaStream_t stream);
 hr_status represent_dispatch(const hr_gauge &g, const double2 *UF, cudaStream_t stream);
 hr_status force_dispatch(const hr_gauge &g, const ForceParams &fp, cudaStream_t stream);
 

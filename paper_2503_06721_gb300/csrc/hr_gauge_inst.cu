@@ -8,6 +8,14 @@ namespace hr {
 // one link entry in precision P (real: the real part only)
 __device__ inline void store_entry(int P, bool real, char *dst, cx<double> v)
 {
+    if (P == HR_DF64) {
+        const df re(v.re), im(v.im);
+        if (real)
+            *reinterpret_cast<float2 *>(dst) = make_float2(re.hi, re.lo);
+        else
+            *reinterpret_cast<float4 *>(dst) = make_float4(re.hi, re.lo, im.hi, im.lo);
+        return;
+    }
     if (real) {
         if (P == HR_F64) *reinterpret_cast<double *>(dst) = v.re;
         if (P == HR_F32) *reinterpret_cast<float *>(dst) = (float)v.re;
@@ -65,7 +73,7 @@ __global__ void __launch_bounds__(128) represent_kernel(const double2 *__restric
         }
     const bool neg = g.bc[mu] == -1 && s.c[mu] == L[mu] - 1;
     bool any_rep = false;
-    for (int p = 0; p < 4; p++) any_rep |= of.rep[p] != nullptr;
+    for (int p = 0; p < HR_NPREC; p++) any_rep |= of.rep[p] != nullptr;
     if (any_rep) {
         cx<double> Rm[D][D];
         represent<N, REP>(U, Rm);
@@ -73,7 +81,7 @@ __global__ void __launch_bounds__(128) represent_kernel(const double2 *__restric
         for (int r = 0; r < D; r++)
             for (int q = 0; q < D; q++) {
                 const cx<double> v = sg * Rm[r][q];
-                for (int P = 0; P < 4; P++) {
+                for (int P = 0; P < HR_NPREC; P++) {
                     if (!of.rep[P]) continue;
                     store_entry(P, REAL, reinterpret_cast<char *>(of.rep[P]) + link_offset(P, REAL, D * D, tile, mu, lane, r * D + q), v);
                     // the dagger: entry (q, r) of the backward slot
@@ -83,7 +91,7 @@ __global__ void __launch_bounds__(128) represent_kernel(const double2 *__restric
     }
     for (int r = 0; r < N; r++)
         for (int q = 0; q < N; q++)
-            for (int P = 0; P < 4; P++) {
+            for (int P = 0; P < HR_NPREC; P++) {
                 if (!of.fund[P]) continue;
                 store_entry(P, false, reinterpret_cast<char *>(of.fund[P]) + link_offset(P, false, N * N, tile, mu, lane, r * N + q), U[r][q]);
                 store_entry(P, false, reinterpret_cast<char *>(ob.fund[P]) + link_offset(P, false, N * N, tb, 4 + mu, lb, q * N + r), conj(U[r][q]));
@@ -96,7 +104,7 @@ hr_status represent_launch(const hr_gauge &gg, const double2 *UF, cudaStream_t s
     const Geom &g = gg.geom;
     RepOut o[2];
     for (int parity = 0; parity < 2; parity++)
-        for (int p = 0; p < 4; p++) {
+        for (int p = 0; p < HR_NPREC; p++) {
             o[parity].rep[p] = gg.rep[p][parity];
             o[parity].fund[p] = gg.fund[p][parity];
         }

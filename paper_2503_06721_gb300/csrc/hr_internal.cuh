@@ -24,6 +24,7 @@
 
 #define HR_MAX_N 4
 #define HR_TILE 32
+#define HR_NPREC 5   // F64, F32, F16, BF16, DF64
 
 namespace hr {
 
@@ -75,6 +76,22 @@ __host__ __device__ __forceinline__ void rmac(cx<R> &a, R s, cx<R> c)
     a.re = fma(s, c.re, a.re);
     a.im = fma(s, c.im, a.im);
 }
+// the epilogue forms, each with one fixed rounding sequence so that every
+// kernel variant produces the same bits:
+//   s*x + t*y  = fma(s, x, t*y) per part;   n2 += |v|^2 as two fmas
+template <class R>
+__host__ __device__ __forceinline__ cx<R> axpby(R s, cx<R> x, R t, cx<R> y)
+{
+    cx<R> r = {t * y.re, t * y.im};
+    rmac(r, s, x);
+    return r;
+}
+template <class R>
+__host__ __device__ __forceinline__ void norm_acc(R &n2, cx<R> v)
+{
+    n2 = fma(v.re, v.re, n2);
+    n2 = fma(v.im, v.im, n2);
+}
 // multiply by i^k, k known at compile time after unrolling
 template <class R>
 __host__ __device__ __forceinline__ cx<R> ipow(int k, cx<R> a)
@@ -86,6 +103,67 @@ __host__ __device__ __forceinline__ cx<R> ipow(int k, cx<R> a)
     default: return {a.im, -a.re};
     }
 }
+
+// ---------------------------------------------------------------------------
+// float-float ("df64") numbers: value = hi + lo with |lo| <= ulp(hi)/2, about
+// 48 significant bits.  Sums use Knuth's TwoSum, products the FMA-based exact
+// product (Dekker's TwoProduct with a fused multiply-add), then a fast
+// renormalisation.  GB300 executes FP32 FMAs at many times its FP64 rate, so
+// FP64-class accuracy for the operator costs far less in float-float.
+// ---------------------------------------------------------------------------
+// the float-float overloads below join the standard ones instead of hiding them
+using ::fma;
+using ::isfinite;
+
+struct df {
+    float hi, lo;
+    __host__ __device__ df() : hi(0.f), lo(0.f) {}
+    __host__ __device__ df(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ df(int v) : hi((float)v), lo(0.f) {}
+    // exact split of a double into two floats (uses one FP64 subtraction)
+    __host__ __device__ df(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+    __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+__host__ __device__ __forceinline__ df df_qts(float a, float b)   // |a| >= |b|
+{
+    const float s = a + b;
+    return df(s, b - (s - a));
+}
+__host__ __device__ __forceinline__ df df_ts(float a, float b, float &err)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    err = (a - (s - bb)) + (b - bb);
+    return df(s, 0.f);
+}
+__host__ __device__ __forceinline__ df operator+(df a, df b)
+{
+    float e;
+    const df s = df_ts(a.hi, b.hi, e);
+    return df_qts(s.hi, e + a.lo + b.lo);
+}
+__host__ __device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
+__host__ __device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__host__ __device__ __forceinline__ df operator*(df a, df b)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return df_qts(p, e);
+}
+// a * b + c with one renormalisation
+__host__ __device__ __forceinline__ df fma(df a, df b, df c)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    float t;
+    const df s = df_ts(p, c.hi, t);
+    return df_qts(s.hi, t + c.lo + e);
+}
+__host__ __device__ __forceinline__ bool isfinite(df a) { return isfinite(a.hi); }
 
 // ---------------------------------------------------------------------------
 // representations (Table 1) -- compile-time structure
@@ -205,8 +283,24 @@ struct St<HR_BF16> {
     __device__ __forceinline__ static Rs str(double v) { return __double2bfloat16(v); }
 };
 
-__host__ __device__ constexpr size_t prec_cbytes(int P) { return P == HR_F64 ? 16 : P == HR_F32 ? 8 : 4; }
-__host__ __device__ constexpr size_t prec_rbytes(int P) { return P == HR_F64 ? 8 : P == HR_F32 ? 4 : 2; }
+template <>
+struct St<HR_DF64> {
+    using R = df;
+    using C = float4;   // (re.hi, re.lo, im.hi, im.lo)
+    using Rs = float2;  // (hi, lo)
+    static constexpr bool scaled = false;
+    __device__ __forceinline__ static cx<R> ld(C v) { return {df(v.x, v.y), df(v.z, v.w)}; }
+    __device__ __forceinline__ static C st(cx<R> v) { return make_float4(v.re.hi, v.re.lo, v.im.hi, v.im.lo); }
+    __device__ __forceinline__ static R ldr(Rs v) { return df(v.x, v.y); }
+    __host__ __device__ __forceinline__ static Rs str(double v)
+    {
+        const df d(v);
+        return make_float2(d.hi, d.lo);
+    }
+};
+
+__host__ __device__ constexpr size_t prec_cbytes(int P) { return (P == HR_F64 || P == HR_DF64) ? 16 : P == HR_F32 ? 8 : 4; }
+__host__ __device__ constexpr size_t prec_rbytes(int P) { return (P == HR_F64 || P == HR_DF64) ? 8 : P == HR_F32 ? 4 : 2; }
 
 static inline size_t align_up(size_t n, size_t a) { return (n + a - 1) / a * a; }
 

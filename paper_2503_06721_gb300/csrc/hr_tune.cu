@@ -1,0 +1,170 @@
+// hr_tune.cu -- the hopping-kernel variant autotuner and its C ABI.
+//
+// The hopping kernel exists as a direct variant (each lane loads its own
+// neighbour records) and as shared-memory-staged variants (the warp moves
+// its 32 records cooperatively) at one or two register budgets.  All compute
+// the same bits.  Which is fastest depends on the representation (record
+// sizes, registers), the precision, the link mode, the epilogue and the
+// lattice, so the choice is measured: every variant of every epilogue is
+// launched on zero-filled scratch fields of the handle's lattice, timed with
+// CUDA events on the caller's stream, and the fastest is recorded in the
+// handle per (precision, link mode, epilogue, nrhs == 1 / > 1).
+#include <climits>
+#include <cstring>
+
+#include "hr_api.cuh"
+
+namespace hr {
+
+namespace {
+
+struct DeviceBuffer {
+    void *p = nullptr;
+    ~DeviceBuffer()
+    {
+        if (p) cudaFree(p);
+    }
+};
+
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~EventPair()
+    {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
+constexpr int TUNE_REPS = 3;
+
+}  // namespace
+
+hr_status tune_hops(hr_gauge *g, int P, int nrhs, cudaStream_t s)
+{
+    const int nv = hop_variant_count(g, P);
+    if (nv <= 1) return HR_OK;
+    const bool rb = g->mode == HR_LINKS_REBUILD;
+    const int D = g->D;
+    const long vh = g->geom.vh;
+    const int PC = P == HR_F64 ? HR_F64 : HR_F32;   // r and x of a fused CG update
+    const size_t fP = align_up(field_rhs_bytes(vh, D, P) * nrhs, 256);
+    const size_t fC = align_up(field_rhs_bytes(vh, D, PC) * nrhs, 256);
+    const long nblk = (vh + 127) / 128;
+    const size_t bpart = align_up(sizeof(double) * (size_t)nrhs * (nblk + 1), 256);
+    const size_t bcnt = align_up(sizeof(unsigned) * nrhs, 256);
+    const size_t bstate = align_up(sizeof(CgState) * nrhs, 256);
+    const size_t bred = align_up(sizeof(double) * nrhs, 256);
+    const size_t total = 3 * fP + 2 * fC + bpart + bcnt + bstate + bred;
+
+    DeviceBuffer mem;
+    cudaError_t e = cudaMalloc(&mem.p, total);
+    if (e != cudaSuccess) {
+        mem.p = nullptr;
+        cudaGetLastError();
+        set_error("hr_tune: cannot allocate %zu bytes of scratch", total);
+        return HR_ERR_NOMEM;
+    }
+    HR_CUDA_CHECK(cudaMemsetAsync(mem.p, 0, total, s));
+    char *q = static_cast<char *>(mem.p);
+    auto take = [&](size_t b) { char *r = q; q += b; return r; };
+    FieldView vin = make_view(take(fP), vh, D, P);
+    FieldView vout = make_view(take(fP), vh, D, P);
+    FieldView vaux = make_view(take(fP), vh, D, P);
+    FieldView vr = make_view(take(fC), vh, D, PC);
+    FieldView vx = make_view(take(fC), vh, D, PC);
+    Scratch sc;
+    memset(&sc, 0, sizeof sc);
+    sc.partials = reinterpret_cast<double *>(take(bpart));
+    sc.counters = reinterpret_cast<unsigned *>(take(bcnt));
+    sc.state = reinterpret_cast<CgState *>(take(bstate));
+    double *red = reinterpret_cast<double *>(take(bred));
+    Scratch sc_ns = sc;
+    sc_ns.state = nullptr;
+    // a solver state that never converges and never reaches its cap, so that
+    // every timed CG-update launch does its full work
+    std::vector<CgState> st0(nrhs);
+    for (auto &c : st0) {
+        memset(&c, 0, sizeof c);
+        c.rr = 1.0;
+        c.stop2 = -1.0;
+        c.cap = INT_MAX;
+    }
+    HR_CUDA_CHECK(cudaMemcpyAsync(sc.state, st0.data(), sizeof(CgState) * nrhs, cudaMemcpyHostToDevice, s));
+
+    // the launch shapes of a CG iteration on the even/odd system
+    auto launch = [&](int epi, int v) -> hr_status {
+        switch (epi) {
+        case EPI_STORE:
+            return hop(g, P, 0, 0, vin, vout, nullptr, -0.5, 0.0, nrhs, s, EPI_STORE, nullptr, FIN_WRITE, nullptr,
+                       nullptr, nullptr, nullptr, nullptr, v);
+        case EPI_STORE_NORM:
+            return hop(g, P, 0, 0, vin, vout, &vaux, 0.5, 1.0, nrhs, s, EPI_STORE_NORM, &sc_ns, FIN_WRITE, nullptr,
+                       red, nullptr, nullptr, nullptr, v);
+        default:
+            return hop(g, P, 0, 1, vin, vin, &vaux, 0.5, 1.0, nrhs, s, EPI_CG_UPDATE, &sc, FIN_CG_BETA, nullptr,
+                       nullptr, &vr, &vx, &vaux, v);
+        }
+    };
+    EventPair ev;
+    HR_CUDA_CHECK(cudaEventCreate(&ev.a));
+    HR_CUDA_CHECK(cudaEventCreate(&ev.b));
+    for (int epi = EPI_STORE; epi <= EPI_CG_UPDATE; epi++) {
+        float best = 0;
+        int best_v = HOP_DIRECT;
+        for (int v = 0; v < nv; v++) {
+            hr_status st = launch(epi, v);   // warm-up (and first-use setup)
+            if (st != HR_OK) return st;
+            HR_CUDA_CHECK(cudaEventRecord(ev.a, s));
+            for (int k = 0; k < TUNE_REPS; k++) {
+                st = launch(epi, v);
+                if (st != HR_OK) return st;
+            }
+            HR_CUDA_CHECK(cudaEventRecord(ev.b, s));
+            HR_CUDA_CHECK(cudaEventSynchronize(ev.b));
+            float ms = 0;
+            HR_CUDA_CHECK(cudaEventElapsedTime(&ms, ev.a, ev.b));
+            if (v == 0 || ms < best) {
+                best = ms;
+                best_v = v;
+            }
+        }
+        g->tuned[P][rb ? 1 : 0][epi][nrhs > 1 ? 1 : 0] = (signed char)best_v;
+    }
+    HR_CUDA_CHECK(cudaStreamSynchronize(s));
+    return HR_OK;
+}
+
+}  // namespace hr
+
+using namespace hr;
+
+extern "C" {
+
+hr_status hr_tune(hr_gauge *g, hr_prec prec, int nrhs, void *stream)
+{
+    if (!g || nrhs < 1 || prec < HR_F64 || prec > HR_DF64 || !(g->prec_mask & (1u << prec))) {
+        set_error("hr_tune: NULL handle, nrhs < 1 or precision not stored in the handle");
+        return HR_ERR_INVALID;
+    }
+    return tune_hops(g, prec, nrhs, reinterpret_cast<cudaStream_t>(stream));
+}
+
+hr_status hr_gauge_set_tuning(hr_gauge *g, int autotune, int variant)
+{
+    if (!g || (autotune != 0 && autotune != 1) || variant < -1 || variant > HR_HOP_STAGED_TIGHT) {
+        set_error("hr_gauge_set_tuning: bad arguments");
+        return HR_ERR_INVALID;
+    }
+    g->autotune = autotune;
+    g->force_variant = variant;
+    return HR_OK;
+}
+
+int hr_gauge_hop_variant(const hr_gauge *g, hr_prec prec, int epilogue, int nrhs)
+{
+    if (!g || prec < HR_F64 || prec > HR_DF64 || epilogue < HR_EPI_STORE || epilogue > HR_EPI_CG_UPDATE || nrhs < 1)
+        return -1;
+    return hop_variant(g, prec, g->mode == HR_LINKS_REBUILD, epilogue, nrhs);
+}
+
+}  // extern "C"

@@ -6,6 +6,7 @@ Tensors are torch CUDA tensors (PyTorch supplies device memory and streams):
   FP64 fields  complex128 [nrhs, nsites, 4, D] (or [nsites, 4, D])
   FP32 fields  complex64  of the same shape
   F16/BF16     uint8 buffers of field_bytes(...) bytes (data + per-site scales)
+  DF64 fields  float32 [nrhs, nsites, 4, D, 4] = (re.hi, re.lo, im.hi, im.lo)
   gauge input  complex128 [V, 4, N, N]
 """
 from __future__ import annotations
@@ -20,9 +21,11 @@ _LIB_PATH = Path(__file__).resolve().parent / "_lib" / "libhr.so"
 
 FUND, ADJ, SYM, ASYM = 0, 1, 2, 3
 REPS = {"FUND": FUND, "ADJ": ADJ, "SYM": SYM, "ASYM": ASYM, "2AS": ASYM}
-F64, F32, F16, BF16 = 0, 1, 2, 3
-PRECS = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
+F64, F32, F16, BF16, DF64 = 0, 1, 2, 3, 4
+PRECS = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16, "df64": DF64}
 EVEN, ODD, FULL, EO_PRECOND = 0, 1, 2, 3
+HOP_DIRECT, HOP_STAGED, HOP_STAGED_TIGHT = 0, 1, 2
+EPI_STORE, EPI_STORE_NORM, EPI_CG_UPDATE = 0, 1, 2
 LINKS_STORED, LINKS_REBUILD = 0, 1
 
 STATUS = {0: "HR_OK", -1: "HR_ERR_INVALID", -2: "HR_ERR_CUDA", -3: "HR_ERR_NOMEM",
@@ -31,6 +34,7 @@ STATUS = {0: "HR_OK", -1: "HR_ERR_INVALID", -2: "HR_ERR_CUDA", -3: "HR_ERR_NOMEM
 
 # every symbol include/hr.h declares
 EXPORTS = ["hr_represent_gauge", "hr_gauge_update", "hr_gauge_set_link_mode", "hr_gauge_destroy",
+           "hr_tune", "hr_gauge_set_tuning", "hr_gauge_hop_variant",
            "hr_field_bytes", "hr_field_convert", "hr_field_dot", "hr_field_dot_static",
            "hr_dirac_apply", "hr_dirac_dagger",
            "hr_cg_solve", "hr_cg_solve_batched", "hr_dirac_force", "hr_rep_dim", "hr_generators",
@@ -50,7 +54,8 @@ class LatticeDesc(ctypes.Structure):
 
 class CgParams(ctypes.Structure):
     _fields_ = [("tol_rel", ctypes.c_double), ("max_iter", ctypes.c_int), ("inner", ctypes.c_int),
-                ("inner_tol", ctypes.c_double), ("use_initial_guess", ctypes.c_int)]
+                ("inner_tol", ctypes.c_double), ("use_initial_guess", ctypes.c_int),
+                ("residual", ctypes.c_int)]
 
 
 class CgResult(ctypes.Structure):
@@ -80,6 +85,9 @@ def load():
         "hr_gauge_update": (I, [P, P, P]),
         "hr_gauge_set_link_mode": (I, [P, I]),
         "hr_gauge_destroy": (I, [P]),
+        "hr_tune": (I, [P, I, I, P]),
+        "hr_gauge_set_tuning": (I, [P, I, I]),
+        "hr_gauge_hop_variant": (I, [P, I, I, I]),
         "hr_field_bytes": (S, [LP, I, I, I]),
         "hr_field_convert": (I, [LP, I, I, P, I, P, I, P]),
         "hr_field_dot": (I, [LP, I, I, P, P, I, ctypes.POINTER(D), P]),
@@ -178,6 +186,8 @@ def empty_field(lat: Lattice, parity: int, prec: int, nrhs: int = 1, device="cud
         return torch.empty(shape, dtype=torch.complex128, device=device)
     if prec == F32:
         return torch.empty(shape, dtype=torch.complex64, device=device)
+    if prec == DF64:
+        return torch.empty(shape + (4,), dtype=torch.float32, device=device)
     return torch.empty(field_bytes(lat, parity, prec, nrhs), dtype=torch.uint8, device=device)
 
 
@@ -227,6 +237,17 @@ class Gauge:
     def set_link_mode(self, mode: int):
         _check(load().hr_gauge_set_link_mode(self.handle, mode))
 
+    def tune(self, prec: int, nrhs: int = 1, stream=None):
+        """Times the hopping-kernel variants of every epilogue in precision
+        prec and records the fastest (hr_tune)."""
+        _check(load().hr_tune(self.handle, prec, nrhs, _stream(stream)))
+
+    def set_tuning(self, autotune: bool = True, variant: int = -1):
+        _check(load().hr_gauge_set_tuning(self.handle, int(autotune), variant))
+
+    def hop_variant(self, prec: int, epilogue: int, nrhs: int = 1) -> int:
+        return load().hr_gauge_hop_variant(self.handle, prec, epilogue, nrhs)
+
     def close(self):
         if self.handle and self.handle.value:
             load().hr_gauge_destroy(self.handle)
@@ -243,7 +264,7 @@ class Gauge:
         out_par = EVEN if parity == EO_PRECOND else parity
         if out is None:
             ns = self.lat.nsites(FULL if parity == FULL else EVEN)
-            if prec in (F64, F32):
+            if prec in (F64, F32, DF64):
                 out = torch.empty_like(x)
             else:
                 out = torch.empty(field_bytes(self.lat, out_par if parity != FULL else FULL, prec, nrhs),
@@ -254,10 +275,11 @@ class Gauge:
 
     def cg_solve(self, sys: int, b, x=None, nrhs: int = 1, tol: float = 1e-10,
                  max_iter: int = 10000, inner: int = F64, inner_tol: float = 1e-5,
-                 use_initial_guess: bool = False, stream=None, check: bool = True):
+                 use_initial_guess: bool = False, residual: int = F64, stream=None,
+                 check: bool = True):
         if x is None:
             x = torch.zeros_like(b)
-        p = CgParams(tol, max_iter, inner, inner_tol, int(use_initial_guess))
+        p = CgParams(tol, max_iter, inner, inner_tol, int(use_initial_guess), residual)
         res = (CgResult * nrhs)()
         st = load().hr_cg_solve(self.handle, sys, _ptr(b), _ptr(x), nrhs, ctypes.byref(p), res,
                                 _stream(stream))
@@ -277,14 +299,14 @@ class Gauge:
 
 
 def cg_solve_batched(gauges, sys: int, bs, xs, nrhs, tol=1e-10, max_iter=10000, inner=F32,
-                     inner_tol=1e-5, stream=None, check=True):
+                     inner_tol=1e-5, residual=F64, stream=None, check=True):
     n = len(gauges)
     P = ctypes.c_void_p
     g_arr = (P * n)(*[g.handle.value for g in gauges])
     b_arr = (P * n)(*[b.data_ptr() for b in bs])
     x_arr = (P * n)(*[x.data_ptr() for x in xs])
     n_arr = (ctypes.c_int * n)(*nrhs)
-    p = CgParams(tol, max_iter, inner, inner_tol, 0)
+    p = CgParams(tol, max_iter, inner, inner_tol, 0, residual)
     res = (CgResult * sum(nrhs))()
     st = load().hr_cg_solve_batched(n, g_arr, sys, b_arr, x_arr, n_arr, ctypes.byref(p), res,
                                     _stream(stream))
