@@ -125,66 +125,92 @@ hr_status represent_launch(const hr_gauge &gg, const double2 *UF, cudaStream_t s
 //   hY = upper[(1 + g_mu) Y(x+mu)],  w = upper[(1 + g_mu) X(x)],
 // and U A - B U^dag = K = sum_r (U hX_r) z_r^dag - w_r (U hY_r)^dag needs four
 // matrix-vector products.  tr(T_R^a K) is pulled back to the fundamental,
-// tr(T_R^a K) = tr(T^a P), by differentiating the sparse representation
-// formulas (the same ones the represent kernel evaluates), so only the
-// N x N matrix P meets the generators.
+// tr(T_R^a K) = tr(T^a P) (below), so only the N x N matrix P meets the
+// generators.
 // One thread per (site of `parity`, mu); FP64 throughout.
 // ---------------------------------------------------------------------------
-// Kf(m, n) returns the entry K_mn (computed on demand, so K is never stored)
-template <int N, int REP, class KF>
-__device__ __forceinline__ void pullback(KF &&Kf, cx<double> (&P)[N][N])
+// The pullback tr(T_R^a K) = tr(T^a P) for K = x y^dag (x, y in the space of
+// R), written with the N x N matrices of the representation-space vectors:
+//   SYM/2AS: X = sum_n x_n e_n (e_n the orthonormal basis of symmetric /
+//     antisymmetric matrices, R(U) X = U X U^T, T_R^a X = T X + X T^T), so
+//     y^dag T_R^a x = tr(Y^dag (T X + X T^T)) = tr(T^a (X Y^dag + (Y^dag X)^T))
+//     and with X^T = s X, Y^T = s Y (s = +1 SYM, -1 2AS) this is
+//     P = 2 s X conj(Y);
+//   ADJ: X = sum_a x_a T^a (R(U) X = U X U^dag, T_R^a X = [T^a, X], and
+//     x_a = 2 tr(T^a X)), so y^dag T_R^a x = 2 tr(Y^dag [T^a, X]) and
+//     P = 2 [X, Y^dag] with Y^dag = sum_a conj(y_a) T^a;
+//   FUND: P = K.
+// Each costs N^3 (SYM/2AS) or 2 N^3 (ADJ) complex products instead of the
+// D_R^2 products of K itself.
+
+// M = sum_n x_n e_n (SYM/2AS) or sum_a x_a T^a (ADJ); conj_x: use conj(x_n)
+template <int N, int REP, bool CONJ_X>
+__device__ __forceinline__ void rep_matrix(const cx<double> (&x)[rep_dim(N, REP)], cx<double> (&M)[N][N])
 {
-    constexpr int D = rep_dim(N, REP);
 #pragma unroll
     for (int i = 0; i < N; i++)
 #pragma unroll
-        for (int j = 0; j < N; j++) P[i][j] = {0, 0};
-    if constexpr (REP == HR_FUND) {
-        // tr(T K) = sum T_ik K_ki  ->  P = K
-#pragma unroll
-        for (int i = 0; i < N; i++)
-#pragma unroll
-            for (int j = 0; j < N; j++) P[i][j] = Kf(i, j);
-    } else if constexpr (REP == HR_ADJ) {
-        // (T_R)_nm = 2 sum be ga [T_jk d_il - d_jk T_li]  (T Hermitian)
-        static_for<0, D>([&](auto NN) {
-            constexpr int n = decltype(NN)::value;
-            static_for<0, D>([&](auto MM) {
-                constexpr int m = decltype(MM)::value;
-                const cx<double> kmn = Kf(m, n);
-                static_for<0, gen_nent(N, n)>([&](auto E1) {
-                    constexpr int e1 = decltype(E1)::value;
-                    constexpr int i = gen_row(N, n, e1), j = gen_col(N, n, e1);
-                    static_for<0, gen_nent(N, m)>([&](auto E2) {
-                        constexpr int e2 = decltype(E2)::value;
-                        constexpr int k = gen_row(N, m, e2), l = gen_col(N, m, e2);
-                        const cx<double> c = 2.0 * (gen_val<double>(N, n, e1) * gen_val<double>(N, m, e2)) * kmn;
-                        if constexpr (i == l) P[k][j] = P[k][j] + c;   // T_jk P_kj
-                        if constexpr (j == k) P[i][l] = P[i][l] - c;   // T_li P_il
-                    });
-                });
+        for (int j = 0; j < N; j++) M[i][j] = {0, 0};
+    if constexpr (REP == HR_ADJ) {
+        static_for<0, N * N - 1>([&](auto AA) {
+            constexpr int a = decltype(AA)::value;
+            const cx<double> xa = CONJ_X ? conj(x[a]) : x[a];
+            static_for<0, gen_nent(N, a)>([&](auto EE) {
+                constexpr int e = decltype(EE)::value;
+                cx<double> &m = M[gen_row(N, a, e)][gen_col(N, a, e)];
+                cmac(m, gen_val<double>(N, a, e), xa);
             });
         });
     } else {
-        // (T_R)_nm = sum w v [T_ik d_jl + d_ik T_jl]
-        static_for<0, D>([&](auto NN) {
+        static_for<0, rep_dim(N, REP)>([&](auto NN) {
             constexpr int n = decltype(NN)::value;
-            static_for<0, D>([&](auto MM) {
-                constexpr int m = decltype(MM)::value;
-                const cx<double> kmn = Kf(m, n);
-                static_for<0, sb_nent(N, REP, n)>([&](auto E1) {
-                    constexpr int e1 = decltype(E1)::value;
-                    constexpr int i = sb_row(N, REP, n, e1), j = sb_col(N, REP, n, e1);
-                    static_for<0, sb_nent(N, REP, m)>([&](auto E2) {
-                        constexpr int e2 = decltype(E2)::value;
-                        constexpr int k = sb_row(N, REP, m, e2), l = sb_col(N, REP, m, e2);
-                        const cx<double> c = (sb_val(N, REP, n, e1) * sb_val(N, REP, m, e2)) * kmn;
-                        if constexpr (j == l) P[k][i] = P[k][i] + c;   // T_ik P_ki
-                        if constexpr (i == k) P[l][j] = P[l][j] + c;   // T_jl P_lj
-                    });
-                });
+            const cx<double> xn = CONJ_X ? conj(x[n]) : x[n];
+            static_for<0, sb_nent(N, REP, n)>([&](auto EE) {
+                constexpr int e = decltype(EE)::value;
+                cx<double> &m = M[sb_row(N, REP, n, e)][sb_col(N, REP, n, e)];
+                rmac(m, sb_val(N, REP, n, e), xn);
             });
         });
+    }
+}
+
+// P += f (A B)
+template <int N>
+__device__ __forceinline__ void mat_mac(cx<double> (&P)[N][N], double f, const cx<double> (&A)[N][N],
+                                        const cx<double> (&B)[N][N])
+{
+#pragma unroll
+    for (int i = 0; i < N; i++)
+#pragma unroll
+        for (int j = 0; j < N; j++) {
+            cx<double> s = {0, 0};
+#pragma unroll
+            for (int k = 0; k < N; k++) cmac(s, A[i][k], B[k][j]);
+            rmac(P[i][j], f, s);
+        }
+}
+
+// P += sgn * (pullback of x y^dag)
+template <int N, int REP>
+__device__ __forceinline__ void pullback_add(cx<double> (&P)[N][N], double sgn, const cx<double> (&x)[rep_dim(N, REP)],
+                                             const cx<double> (&y)[rep_dim(N, REP)])
+{
+    if constexpr (REP == HR_FUND) {
+#pragma unroll
+        for (int i = 0; i < N; i++)
+#pragma unroll
+            for (int j = 0; j < N; j++) rmac(P[i][j], sgn, x[i] * conj(y[j]));
+    } else if constexpr (REP == HR_ADJ) {
+        cx<double> X[N][N], Yd[N][N];
+        rep_matrix<N, REP, false>(x, X);
+        rep_matrix<N, REP, true>(y, Yd);   // Y^dag (T^a Hermitian)
+        mat_mac<N>(P, 2.0 * sgn, X, Yd);
+        mat_mac<N>(P, -2.0 * sgn, Yd, X);
+    } else {
+        cx<double> X[N][N], Yc[N][N];
+        rep_matrix<N, REP, false>(x, X);
+        rep_matrix<N, REP, true>(y, Yc);   // conj(Y)
+        mat_mac<N>(P, (REP == HR_SYM ? 2.0 : -2.0) * sgn, X, Yc);
     }
 }
 
@@ -242,15 +268,13 @@ __global__ void __launch_bounds__(128) force_kernel(const ForceParams fp)
             u[a] = su;
             v[a] = sv;
         }
-        // K_r = u z^dag - w v^dag, pulled back entry by entry
-        pullback<N, REP>(
-            [&](int a, int b) {
-                cx<double> k = {0, 0};
-                cmac(k, u[a], conj(z[b]));
-                cmac(k, (-1.0) * w[a], conj(v[b]));
-                return k;
-            },
-            P);
+        // K_r = u z^dag - w v^dag, pulled back to the fundamental
+#pragma unroll
+        for (int a = 0; a < N; a++)
+#pragma unroll
+            for (int b = 0; b < N; b++) P[a][b] = {0, 0};
+        pullback_add<N, REP>(P, 1.0, u, z);
+        pullback_add<N, REP>(P, -1.0, w, v);
     } else {
 #pragma unroll
         for (int a = 0; a < N; a++)
