@@ -11,11 +11,13 @@ input, as an HMC force evaluation of the fermion monomial does it:
      Dhat^dag Dhat x = phi to a true relative residual of 1e-10
      (--residual df64 forms the intermediate true residuals in float-float
      and confirms the one that meets the tolerance in FP64),
-  4. Y = Dhat x and the fermion force of S = phi^dag (Dhat^dag Dhat)^-1 phi.
+  4. the fermion force of S = phi^dag (Dhat^dag Dhat)^-1 phi (fused with the
+     solve: the force reuses the operator applications of its final residual).
 
 value: algorithmic ("compulsory") bytes of every hopping-kernel launch of the
-step, V/2 (8 L_p + 2 S_p) each, divided by the step's device time -- the
-whole step's D_eo-equivalent bandwidth.  roofline: the FP32 D_eo kernel,
+step, V/2 (8 L_p + 2 S_p) each with stored-link L_p whatever link mode the
+launch used, divided by the step's device time -- the whole step's
+D_eo-equivalent bandwidth.  roofline: the FP32 D_eo kernel,
 bytes per launch over its CUDA-event duration, against the measured HBM copy
 bandwidth.  cg: time to 1e-10 of plain FP64 CG vs FP32 / F16 / BF16-inner
 defect correction on the same GPU (measured once, after the timed steps).
@@ -59,12 +61,14 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def hop_bytes(D: int, real_links: bool, prec: int, vh: int) -> int:
-    """compulsory bytes of one hopping launch: V/2 (8 L_p + 2 S_p)."""
+def hop_bytes(D: int, real_links: bool, prec: int, vh: int, spinor_reads: int = 1) -> int:
+    """compulsory bytes of one hopping launch: V/2 (8 L_p + 2 S_p); with
+    spinor_reads = 8 the conventional "effective" count V/2 (8 L_p + 9 S_p)
+    that charges every neighbour gather."""
     cb = [16, 8, 4, 4][prec]
     lp = D * D * (cb // 2 if real_links else cb)
     sp = 4 * D * cb + (4 if prec >= 2 else 0)
-    return vh * (8 * lp + 2 * sp)
+    return vh * (8 * lp + (1 + spinor_reads) * sp)
 
 
 def job_throughput(step_bytes_local: float, ms_local: float, steps: int, dist=None, device=None):
@@ -170,13 +174,26 @@ def run_ours(args, rank, world, local_rank):
     U = wl_r.links(device=dev)
     phi = synth.gaussian_spinor(vh, D, wl_r.seed + 7, device=dev)
     res_prec = hr.PRECS[args.residual]
-    g = hr.Gauge(lat, U, precs=("f64", "f32") + (("df64",) if res_prec == hr.DF64 else ()), stored=True)
+    # stored and fundamental links: the solver's precisions each use the way of
+    # obtaining U_R the tuner measures faster (LINKS_AUTO); the D_eo launches of
+    # the metric read the stored links
+    g = hr.Gauge(lat, U, precs=("f64", "f32") + (("df64",) if res_prec == hr.DF64 else ()), stored=True,
+                 rebuild=True)
     stream = torch.cuda.current_stream()
-    # pick the hopping-kernel variants of the bandwidth-bound precision (setup,
-    # outside the timed region; the solver would otherwise do it at its first call)
+    # pick link modes and hopping-kernel variants (setup, outside the timed
+    # region; the solver would otherwise do it at its first call)
+    g.set_link_mode(hr.LINKS_STORED)
     g.tune(hr.F32)
     variants = {name: g.hop_variant(hr.F32, epi) for name, epi in
                 (("store", hr.EPI_STORE), ("store_norm", hr.EPI_STORE_NORM), ("cg_update", hr.EPI_CG_UPDATE))}
+    g.set_link_mode(hr.LINKS_AUTO)
+    g.tune(hr.F32)
+    g.tune(hr.F64)
+    solver_links = {"f32": ["stored", "rebuild"][g.link_mode(hr.F32)],
+                    "f64": ["stored", "rebuild"][g.link_mode(hr.F64)]}
+    solver_variants = {name: g.hop_variant(hr.F32, epi) for name, epi in
+                       (("store", hr.EPI_STORE), ("store_norm", hr.EPI_STORE_NORM),
+                        ("cg_update", hr.EPI_CG_UPDATE))}
     x32 = phi.to(torch.complex64)
     y32 = torch.empty_like(x32)
     y64 = torch.empty_like(phi)
@@ -185,36 +202,41 @@ def run_ours(args, rank, world, local_rank):
     deo_ms = []
     work = {"bytes": 0}
 
-    pev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-    phases = {"represent": 0.0, "deo": 0.0, "cg": 0.0, "force": 0.0}
+    pev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    phases = {"represent": 0.0, "deo": 0.0, "cg_force": 0.0}
+    Fbuf = torch.zeros((lat.volume, 4, wl.N ** 2 - 1), dtype=torch.float64, device=dev)
+    xbuf = torch.zeros_like(phi)
 
     def step(phi_dev, U_dev):
         pev[0].record(stream)
         g.update(U_dev)
         pev[1].record(stream)
+        g.set_link_mode(hr.LINKS_STORED)
         for k in range(n_deo):
             ev[2 * k].record(stream)
             g.apply(hr.EVEN, hr.F32, x32, out=y32)
             ev[2 * k + 1].record(stream)
         g.apply(hr.EVEN, hr.F64, phi_dev, out=y64)
+        g.set_link_mode(hr.LINKS_AUTO)
         pev[2].record(stream)
-        x, res, st = g.cg_solve(hr.EO_PRECOND, phi_dev, tol=TOL, max_iter=20000, inner=hr.F32,
-                                inner_tol=1e-5, residual=res_prec)
+        # x = (Dhat^dag Dhat)^-1 phi and the force of S = phi^dag x in one call;
+        # the force's Dhat x, D_oe x and (D^dag)_oe Dhat x come from the
+        # solve's final FP64 true residual
+        Fbuf.zero_()
+        x, F, _, res, st = g.cg_solve_force(hr.EO_PRECOND, phi_dev, x=xbuf, tol=TOL, max_iter=20000,
+                                            inner=hr.F32, inner_tol=1e-5, residual=res_prec, coeff=-1.0,
+                                            F=Fbuf)
         pev[3].record(stream)
-        Y = g.apply(hr.EO_PRECOND, hr.F64, x)
-        F = g.force(hr.EO_PRECOND, x, Y, coeff=-1.0)
-        pev[4].record(stream)
         torch.cuda.synchronize()
-        for name, a, b in (("represent", 0, 1), ("deo", 1, 2), ("cg", 2, 3), ("force", 3, 4)):
+        for name, a, b in (("represent", 0, 1), ("deo", 1, 2), ("cg_force", 2, 3)):
             phases[name] += pev[a].elapsed_time(pev[b])
         r = res[0]
         # hop launches of this step by precision
         h32 = n_deo + 4 * r["iters"]
         # FP64-class (FP64 or DF64, 16 bytes per complex either way) launches: the
-        # D_eo, 4 per true residual after each inner solve (the first one, of
-        # x = 0, is b itself) and 4 for the FP64 confirmation of a DF64 one, 2
-        # for Dhat x and 2 odd-half hops inside the force
-        h64 = 1 + 4 * (r["outer_iters"] + (res_prec == hr.DF64)) + 2 + 2
+        # D_eo and 4 per true residual after each inner solve (the first one, of
+        # x = 0, is b itself), plus 4 for the FP64 confirmation of a DF64 one
+        h64 = 1 + 4 * (r["outer_iters"] + (res_prec == hr.DF64))
         work["bytes"] += h32 * hop_bytes(D, real, hr.F32, vh) + h64 * hop_bytes(D, real, hr.F64, vh)
         work["res"] = r
         return x, F
@@ -291,7 +313,8 @@ def run_ours(args, rank, world, local_rank):
     # time to 1e-10: plain FP64 CG vs defect correction with low-precision inner solves
     cg = None
     if rank == 0 and not args.no_cg_compare:
-        g2 = hr.Gauge(lat, U, precs=("f64", "f32", "f16", "bf16", "df64"), stored=True)
+        g2 = hr.Gauge(lat, U, precs=("f64", "f32", "f16", "bf16", "df64"), stored=True, rebuild=True)
+        g2.set_link_mode(hr.LINKS_AUTO)
         cg = {}
         cg_variants = (("fp64", hr.F64, hr.F64), ("mixed_fp32", hr.F32, hr.F64), ("mixed_fp16", hr.F16, hr.F64),
                     ("mixed_bf16", hr.BF16, hr.F64), ("mixed_fp32_df64res", hr.F32, hr.DF64),
@@ -341,8 +364,12 @@ def run_ours(args, rank, world, local_rank):
                          "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind,
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": traffic, "deo_ms": round(deo_ms_avg, 4),
-                         "bytes_per_launch": deo_bytes},
+                         "bytes_per_launch": deo_bytes,
+                         "effective_GBs": round(hop_bytes(D, real, hr.F32, vh, 8) / (deo_ms_avg * 1e-3) / 1e9, 1),
+                         "frac_of_nominal_7900": round(achieved / 7900.0, 4)},
             "hop_variants_f32": variants,
+            "solver_links": solver_links,
+            "solver_hop_variants_f32": solver_variants,
             "gpu_launches": int(launches),
             "phases_ms": phase_ms,
             "clocks": ck,
@@ -552,6 +579,36 @@ def run_deo(args, local_rank):
                       "GBs": round(byts / (ms * 1e-3) / 1e9, 1), "bytes_per_launch": byts}))
 
 
+def run_force(args, local_rank):
+    """Fermion force only (for profiler captures): Y = Dhat X, then W untimed
+    and K timed calls of the even/odd force in FP64."""
+    import torch
+    from paper_2503_06721_gb300 import build, hr, synth
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    build.build()
+    wl = synth.WORKLOADS[args.workload]
+    lat = hr.Lattice(wl.N, wl.rep, wl.dims, wl.bc, wl.m0)
+    g = hr.Gauge(lat, wl.links(device=dev), precs=("f64",))
+    X = synth.gaussian_spinor(lat.volume // 2, lat.D, 5, device=dev)
+    Y = g.apply(hr.EO_PRECOND, hr.F64, X)
+    F = torch.zeros((lat.volume, 4, wl.N ** 2 - 1), dtype=torch.float64, device=dev)
+    for _ in range(max(args.warmup, 1)):
+        g.force(hr.EO_PRECOND, X, Y, F=F)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("hr_force")
+    e0.record()
+    for _ in range(args.steps):
+        g.force(hr.EO_PRECOND, X, Y, F=F)
+    e1.record()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "force", "workload": args.workload,
+                      "ms_per_call": round(e0.elapsed_time(e1) / args.steps, 4),
+                      "note": "two force_kernel launches (one per parity) and two FP64 odd-half hops per call"}))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -565,15 +622,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-FP64 solve comparison")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--mode", choices=["step", "deo"], default="step",
-                    help="deo: only D_eo applications (profiler captures)")
+    ap.add_argument("--mode", choices=["step", "deo", "force"], default="step",
+                    help="deo: only D_eo applications; force: only the fermion force (profiler captures)")
     ap.add_argument("--prec", choices=["f64", "f32", "f16", "bf16", "df64"], default="f32")
     ap.add_argument("--residual", choices=["df64", "f64"], default="f64",
                     help="arithmetic of the defect-correction true residuals (df64: float-float, "
                          "confirmed once in FP64 when it meets the tolerance)")
     ap.add_argument("--rebuild", action="store_true", help="deo mode: rebuild links in-kernel")
     ap.add_argument("--nrhs", type=int, default=1, help="deo mode: right-hand sides per application")
-    ap.add_argument("--variant", type=int, default=None, choices=[0, 1, 2],
+    ap.add_argument("--variant", type=int, default=None, choices=[0, 1, 2, 3],
                     help="deo mode: force a hopping-kernel variant instead of autotuning")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per D_eo launch, when known for the current kernel")
@@ -587,6 +644,8 @@ def main():
         run_reference(args, rank, world)
     elif args.mode == "deo":
         run_deo(args, local_rank)
+    elif args.mode == "force":
+        run_force(args, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -74,8 +74,11 @@ typedef enum {
 /* How the operator kernels obtain U_R (Sec. 3.1.3, represented field):
  *   HR_LINKS_STORED   read the D_R x D_R represented links kept in HBM
  *   HR_LINKS_REBUILD  read the N x N fundamental links and rebuild the action
- *                     of U_R inside the kernel (fewer bytes, more flops) */
-typedef enum { HR_LINKS_STORED = 0, HR_LINKS_REBUILD = 1 } hr_link_mode;
+ *                     of U_R inside the kernel (fewer bytes, more flops)
+ *   HR_LINKS_AUTO     per precision, whichever of the two hr_tune measured
+ *                     faster on the handle's lattice (STORED until tuned);
+ *                     needs both storages (hr_gauge_set_link_mode only) */
+typedef enum { HR_LINKS_STORED = 0, HR_LINKS_REBUILD = 1, HR_LINKS_AUTO = 2 } hr_link_mode;
 
 typedef struct {
     int N;          /* SU(N), 2 <= N <= 4 */
@@ -112,9 +115,14 @@ hr_status hr_represent_gauge(const hr_lattice_desc *lat, const void *U_fund,
  * update, Sec. 5.3.1: "only necessary after every gauge update"). */
 hr_status hr_gauge_update(hr_gauge *g, const void *U_fund, void *stream);
 
-/* Chooses STORED or REBUILD links for later operator calls on g.
- * HR_ERR_INVALID if that storage was not requested at creation. */
+/* Chooses STORED, REBUILD or AUTO links for later operator calls on g.
+ * HR_ERR_INVALID if that storage (both, for AUTO) was not requested at
+ * creation.  The force always reads the stored FP64 links. */
 hr_status hr_gauge_set_link_mode(hr_gauge *g, hr_link_mode mode);
+
+/* The link mode operator calls in precision prec use now (STORED or
+ * REBUILD); -1 for bad arguments. */
+int hr_gauge_link_mode(const hr_gauge *g, hr_prec prec);
 
 /* Frees the link storage and solver workspace (synchronises the device). */
 hr_status hr_gauge_destroy(hr_gauge *g);
@@ -129,19 +137,23 @@ hr_status hr_gauge_destroy(hr_gauge *g);
  *   HR_HOP_STAGED        the warp gathers its 32 records cooperatively
  *                        through shared memory (cp.async, double-buffered);
  *   HR_HOP_STAGED_TIGHT  the staged kernel at a smaller register budget
- *                        (D_R > 4 only).
+ *                        (D_R > 4 only);
+ *   HR_HOP_STAGED_LINKS  the staged kernel with the link records staged
+ *                        through shared memory as well.
  * FP64 and DF64 have the direct variant only.  Launches are identified by
  * their epilogue: HR_EPI_STORE (out = a H in), HR_EPI_STORE_NORM (the same
  * plus |out|^2), HR_EPI_CG_UPDATE (the fused r -= alpha A p, x += alpha p,
  * |r|^2 of a CG iteration). */
-enum { HR_HOP_DIRECT = 0, HR_HOP_STAGED = 1, HR_HOP_STAGED_TIGHT = 2 };
+enum { HR_HOP_DIRECT = 0, HR_HOP_STAGED = 1, HR_HOP_STAGED_TIGHT = 2, HR_HOP_STAGED_LINKS = 3 };
 enum { HR_EPI_STORE = 0, HR_EPI_STORE_NORM = 1, HR_EPI_CG_UPDATE = 2 };
 
 /* Times every compiled variant of every epilogue in precision prec for g's
  * lattice, current link mode and nrhs right-hand sides, on zero-filled
  * scratch fields that it allocates and frees, and records the fastest in g;
  * later launches with that (prec, link mode, epilogue, nrhs == 1 or > 1) use
- * the record.  BLOCKS the calling thread.  hr_cg_solve and
+ * the record.  In HR_LINKS_AUTO mode it does so for both link modes and
+ * keeps, for prec, the mode whose best kernels make one CG iteration (two
+ * stores, a store with |out|^2 and a fused update) faster.  BLOCKS the calling thread.  hr_cg_solve and
  * hr_cg_solve_batched call it for their inner precision when no record
  * exists yet, unless autotuning is switched off with hr_gauge_set_tuning.
  * Errors: HR_ERR_INVALID (precision not stored), HR_ERR_NOMEM, HR_ERR_CUDA. */
@@ -263,6 +275,21 @@ hr_status hr_cg_solve_batched(int n_inst, const hr_gauge *const *g,
                               void *const *x, const int *nrhs,
                               const hr_cg_params *params, hr_cg_result *res,
                               void *stream);
+
+/* The fermion force of S_f = b^dag A^{-1} b in one call (the HMC force step,
+ * Sec. 2.5 with the solve of Sec. 4.1.2): solves A x = b as hr_cg_solve with
+ * one right-hand side, then F += coeff * dS/dU with Y = D x (sys = HR_FULL)
+ * or Y = Dhat x (HR_EO_PRECOND), exactly as hr_dirac_force(g, sys, x, Y,
+ * coeff, F).  The operator applications the force needs (D x, and for the
+ * even/odd system D_oe x and (D^dag)_oe Dhat x) are those of the solve's
+ * final FP64 true residual, kept instead of recomputed.
+ *   Y  optional DEVICE output of D x / Dhat x (NULL: not returned).
+ * The handle needs stored FP64 links.  F is left unchanged if the solve
+ * fails (its status is returned).  BLOCKS like hr_cg_solve. */
+hr_status hr_cg_solve_force(const hr_gauge *g, hr_parity sys, const void *b,
+                            void *x, const hr_cg_params *params,
+                            hr_cg_result *res, void *Y, double coeff,
+                            void *F, void *stream);
 
 /* ------------------------------------------------------------------ */
 /* Fermion force (Sec. 2.5)                                              */

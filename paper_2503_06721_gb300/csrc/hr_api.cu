@@ -172,9 +172,15 @@ hr_status ws_reserve(const hr_gauge *cg, size_t bytes, cudaStream_t stream)
     return HR_OK;
 }
 
+bool rebuild_for(const hr_gauge *g, int P)
+{
+    if (g->mode == HR_LINKS_AUTO) return g->auto_mode[P] == HR_LINKS_REBUILD && g->fund[P][0] != nullptr;
+    return g->mode == HR_LINKS_REBUILD;
+}
+
 const void *links_for(const hr_gauge *g, int P, int parity, bool *rebuild)
 {
-    if (g->mode == HR_LINKS_REBUILD) {
+    if (rebuild_for(g, P)) {
         *rebuild = true;
         return g->fund[P][parity];
     }
@@ -278,19 +284,20 @@ hr_status hop(const hr_gauge *g, int P, int out_parity, int dagger, const FieldV
     return hop_dispatch(g->lat.N, g->lat.rep, P, prm, rebuild, epi, variant, stream);
 }
 
-int hop_variant_count(const hr_gauge *g, int P)
+unsigned hop_variants_of(const hr_gauge *g, int P)
 {
-    if (P == HR_F64 || P == HR_DF64) return 1;
-    return g->D <= 4 ? 2 : 3;
+    if (P == HR_F64 || P == HR_DF64) return 0x1u;
+    return g->D <= 4 ? 0xBu : 0xFu;   // as hop_variant_mask for the handle's pair
 }
 
 int hop_variant(const hr_gauge *g, int P, bool rebuild, int epi, int nrhs)
 {
-    const int nv = hop_variant_count(g, P);
-    if (g->force_variant >= 0) return std::min(g->force_variant, nv - 1);
+    const unsigned mask = hop_variants_of(g, P);
+    auto compiled = [&](int v) { return v >= 0 && v < HOP_NVARIANTS && ((mask >> v) & 1u); };
+    if (g->force_variant >= 0) return compiled(g->force_variant) ? g->force_variant : HOP_DIRECT;
     const int t = g->tuned[P][rebuild ? 1 : 0][epi][nrhs > 1 ? 1 : 0];
-    if (t >= 0 && t < nv) return t;
-    if (nv == 1) return HOP_DIRECT;
+    if (compiled(t)) return t;
+    if (mask == 0x1u) return HOP_DIRECT;
     // untuned default, from measurements on GB300 (32^4 .. 64x32^3 lattices):
     // the staged kernel wins every fused CG update (r, x, p are read and
     // written at the warp's own sites) and the stores of the 8x8 real adjoint
@@ -374,6 +381,7 @@ hr_status hr_represent_gauge(const hr_lattice_desc *lat, const void *U_fund, uns
     hr_gauge *g = new hr_gauge;
     memset(g, 0, sizeof *g);
     memset(g->tuned, -1, sizeof g->tuned);
+    memset(g->auto_mode, -1, sizeof g->auto_mode);
     g->force_variant = -1;
     g->autotune = 1;
     g->lat = *lat;
@@ -440,12 +448,20 @@ hr_status hr_gauge_update(hr_gauge *g, const void *U_fund, void *stream)
 
 hr_status hr_gauge_set_link_mode(hr_gauge *g, hr_link_mode mode)
 {
-    if (!g || (mode != HR_LINKS_STORED && mode != HR_LINKS_REBUILD) || !(g->link_modes & (1u << mode))) {
+    const unsigned need = mode == HR_LINKS_AUTO ? 0x3u : (mode == HR_LINKS_STORED || mode == HR_LINKS_REBUILD)
+                                                              ? (1u << mode) : 0x4u;
+    if (!g || (g->link_modes & need) != need) {
         set_error("hr_gauge_set_link_mode: mode %d not available", (int)mode);
         return HR_ERR_INVALID;
     }
     g->mode = mode;
     return HR_OK;
+}
+
+int hr_gauge_link_mode(const hr_gauge *g, hr_prec prec)
+{
+    if (!g || prec < HR_F64 || prec > HR_DF64) return -1;
+    return rebuild_for(g, prec) ? HR_LINKS_REBUILD : HR_LINKS_STORED;
 }
 
 hr_status hr_gauge_destroy(hr_gauge *g)
@@ -624,6 +640,18 @@ hr_status hr_dirac_force(const hr_gauge *g, hr_parity sys, const void *X, const 
         if (st != HR_OK) return st;
         c = -coeff;
     }
+    return force_full(g, fx, fy, c, reinterpret_cast<double *>(F), s);
+}
+
+}  // extern "C"
+
+namespace hr {
+
+hr_status force_full(const hr_gauge *g, const FieldView &fx, const FieldView &fy, double c, double *F,
+                     cudaStream_t s)
+{
+    const long vh = g->geom.vh;
+    const int D = g->D;
     for (int p = 0; p < 2; p++) {
         ForceParams fp;
         fp.g = g->geom;
@@ -635,14 +663,14 @@ hr_status hr_dirac_force(const hr_gauge *g, hr_parity sys, const void *X, const 
         fp.Y_nb = half_view(fy, 1 - p, vh, D, HR_F64);
         fp.TR = g->TR;
         fp.coeff = c;
-        fp.F = reinterpret_cast<double *>(F);
-        st = force_dispatch(*g, fp, s);
+        fp.F = F;
+        hr_status st = force_dispatch(*g, fp, s);
         if (st != HR_OK) return st;
     }
     return HR_OK;
 }
 
-}  // extern "C"
+}  // namespace hr
 
 namespace hr {
 

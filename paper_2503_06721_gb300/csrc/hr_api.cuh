@@ -39,13 +39,21 @@ hr_status hop(const hr_gauge *g, int P, int out_parity, int dagger, const FieldV
               double *red_out = nullptr, const FieldView *r = nullptr, const FieldView *x = nullptr,
               const FieldView *p = nullptr, int variant = -1);
 
-// kernel variants compiled for the handle's pair in precision P
-int hop_variant_count(const hr_gauge *g, int P);
+// whether operator launches in precision P read fundamental links (rebuild)
+bool rebuild_for(const hr_gauge *g, int P);
+
+// kernel variants compiled for the handle's pair in precision P (bit v = variant v)
+unsigned hop_variants_of(const hr_gauge *g, int P);
 // the variant a launch would use (forced, tuned, or the fixed default)
 int hop_variant(const hr_gauge *g, int P, bool rebuild, int epi, int nrhs);
 // time every variant of every epilogue in precision P for the handle's
 // lattice, link mode and nrhs, record the fastest (blocks the host)
 hr_status tune_hops(hr_gauge *g, int P, int nrhs, cudaStream_t stream);
+
+// F += c * (force of the full-operator action -2 Re <Y, D X>) for full FP64
+// fields X = fx, Y = fy, reading the stored FP64 links
+hr_status force_full(const hr_gauge *g, const FieldView &fx, const FieldView &fy, double c, double *F,
+                     cudaStream_t s);
 
 // number of kernel launches counted so far (graph contents counted when they run)
 long long launch_counter();

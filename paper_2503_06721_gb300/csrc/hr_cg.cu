@@ -39,6 +39,8 @@ struct Ctx {
     double m4;
     Scratch sc;    // with solver state
     Scratch sc_ns; // same buffers, no state (launches that must not skip)
+    bool keep_t1;  // even/odd A: write D_oe v to t1 and keep it (fused force)
+    FieldView t1;
 };
 
 struct Vecs {
@@ -56,6 +58,10 @@ struct Inst {
     std::vector<int> iters;
     bool done;
     bool df;                   // true residuals in float-float (until one meets the tolerance)
+    // fused force: the last FP64 true residual of the final x leaves D x (q64)
+    // and, for the even/odd system, D_oe x (c.t1) and (D^dag)_oe D x (t64)
+    bool fused_ok;
+    FieldView fx, fy;          // full fields (x, D_oe x) and (D x, (D^dag)_oe D x)
 };
 
 hr_status apply_A(const Ctx &c, int P, const FieldView &v, const FieldView &out, const FieldView &q,
@@ -64,8 +70,9 @@ hr_status apply_A(const Ctx &c, int P, const FieldView &v, const FieldView &out,
     hr_status st;
     const int D = c.D;
     if (c.sys == HR_EO_PRECOND) {
-        st = hop(c.g, P, 1, 0, v, t, nullptr, -0.5, 0.0, c.nrhs, c.s, EPI_STORE, &c.sc_ns);
-        if (st == HR_OK) st = hop(c.g, P, 0, 0, t, q, &v, 0.5, c.m4 * c.m4, c.nrhs, c.s, EPI_STORE, &c.sc_ns);
+        const FieldView &t1 = c.keep_t1 && P == HR_F64 ? c.t1 : t;
+        st = hop(c.g, P, 1, 0, v, t1, nullptr, -0.5, 0.0, c.nrhs, c.s, EPI_STORE, &c.sc_ns);
+        if (st == HR_OK) st = hop(c.g, P, 0, 0, t1, q, &v, 0.5, c.m4 * c.m4, c.nrhs, c.s, EPI_STORE, &c.sc_ns);
         if (st == HR_OK) st = hop(c.g, P, 1, 1, q, t, nullptr, -0.5, 0.0, c.nrhs, c.s, EPI_STORE, &c.sc_ns);
         if (st == HR_OK) st = hop(c.g, P, 0, 1, t, out, &q, 0.5, c.m4 * c.m4, c.nrhs, c.s, EPI_STORE, &c.sc_ns);
         return st;
@@ -312,7 +319,7 @@ hr_status read_states(const Inst &in, std::vector<CgState> &out)
 
 // carve the instance's vectors out of its handle's workspace
 hr_status prepare(Inst &in, const hr_gauge *g, hr_parity sys, const void *b, void *x, int nrhs, int Pin,
-                  int Pres, hr_cg_result *res, cudaStream_t s)
+                  int Pres, hr_cg_result *res, cudaStream_t s, bool force_out = false)
 {
     Ctx &c = in.c;
     c.g = g;
@@ -327,7 +334,9 @@ hr_status prepare(Inst &in, const hr_gauge *g, hr_parity sys, const void *b, voi
     const bool mixed = Pin != HR_F64;
     const size_t f64 = field_rhs_bytes(c.ns, D, HR_F64) * nrhs;
     const size_t t64 = field_rhs_bytes(c.vh, D, HR_F64) * nrhs;
+    const size_t full64 = field_rhs_bytes(2 * c.vh, D, HR_F64) * nrhs;
     size_t need = 4 * f64 + t64 + 8192;
+    if (force_out && sys == HR_EO_PRECOND) need += 2 * full64 + 512;
     size_t f32 = 0, fP = 0, tP = 0;
     if (mixed) {
         f32 = field_rhs_bytes(c.ns, D, HR_F32) * nrhs;
@@ -345,10 +354,23 @@ hr_status prepare(Inst &in, const hr_gauge *g, hr_parity sys, const void *b, voi
     auto take = [&](size_t bytes) { char *q = p; p += align_up(bytes, 256); return q; };
     in.vb = make_view(const_cast<void *>(b), c.ns, D, HR_F64);
     in.vx = make_view(x, c.ns, D, HR_F64);
+    c.keep_t1 = false;
+    in.fused_ok = false;
     in.r64 = make_view(take(f64), c.ns, D, HR_F64);
-    in.q64 = make_view(take(f64), c.ns, D, HR_F64);
+    if (force_out && sys == HR_EO_PRECOND) {
+        // q64 | t64 form the full field (D x, (D^dag)_oe D x); D_oe x goes
+        // to the odd half of a full field whose even half receives x
+        in.fx = make_view(take(full64), 2 * c.vh, D, HR_F64);
+        in.fy = make_view(take(full64), 2 * c.vh, D, HR_F64);
+        in.q64 = half_view(in.fy, 0, c.vh, D, HR_F64);
+        in.t64 = half_view(in.fy, 1, c.vh, D, HR_F64);
+        c.keep_t1 = true;
+        c.t1 = half_view(in.fx, 1, c.vh, D, HR_F64);
+    } else {
+        in.q64 = make_view(take(f64), c.ns, D, HR_F64);
+        in.t64 = make_view(take(t64), c.vh, D, HR_F64);
+    }
     in.q2 = make_view(take(f64), c.ns, D, HR_F64);
-    in.t64 = make_view(take(t64), c.vh, D, HR_F64);
     FieldView p64 = make_view(take(f64), c.ns, D, HR_F64);
     if (mixed) {
         in.r32 = make_view(take(f32), c.ns, D, HR_F32);
@@ -388,9 +410,10 @@ hr_status solve_all(std::vector<Inst> &ins, const hr_cg_params *prm, cudaStream_
     for (auto &in : ins) {
         hr_gauge *g = const_cast<hr_gauge *>(in.c.g);
         const int P = in.v.P;
-        const int rb = g->mode == HR_LINKS_REBUILD ? 1 : 0;
-        if (g->autotune && g->force_variant < 0 && hop_variant_count(g, P) > 1 &&
-            g->tuned[P][rb][EPI_CG_UPDATE][in.c.nrhs > 1 ? 1 : 0] < 0) {
+        const int rb = rebuild_for(g, P) ? 1 : 0;
+        const bool untuned = (g->mode == HR_LINKS_AUTO && g->auto_mode[P] < 0) ||
+                             (hop_variants_of(g, P) != 0x1u && g->tuned[P][rb][EPI_CG_UPDATE][in.c.nrhs > 1 ? 1 : 0] < 0);
+        if (g->autotune && g->force_variant < 0 && untuned) {
             hr_status ts = tune_hops(g, P, in.c.nrhs, s);
             if (ts != HR_OK) return ts;
         }
@@ -405,8 +428,10 @@ hr_status solve_all(std::vector<Inst> &ins, const hr_cg_params *prm, cudaStream_
         const int cap = std::max(1, prm->max_iter - total);
         for (auto &in : ins) {
             if (in.done) continue;
-            st = true_residual(in, tol, cap, outer == 0 && !prm->use_initial_guess);
+            const bool x_zero = outer == 0 && !prm->use_initial_guess;
+            st = true_residual(in, tol, cap, x_zero);
             if (st != HR_OK) return st;
+            in.fused_ok = !x_zero && !in.df;
         }
         for (size_t i = 0; i < ins.size(); i++) {
             if (ins[i].done) continue;
@@ -426,6 +451,7 @@ hr_status solve_all(std::vector<Inst> &ins, const hr_cg_params *prm, cudaStream_
             if (!all_ok) continue;
             in.df = false;
             st = true_residual(in, tol, cap, false);
+            in.fused_ok = true;
             if (st != HR_OK) return st;
             HR_CUDA_CHECK(cudaMemcpyAsync(red[i].data(), in.c.sc.red, sizeof(double) * 2 * in.c.nrhs,
                                           cudaMemcpyDeviceToHost, s));
@@ -564,7 +590,7 @@ static hr_status check_params(const hr_gauge *g, hr_parity sys, const hr_cg_para
         return HR_ERR_INVALID;
     }
     if (params->residual == HR_DF64 && params->inner != HR_F64 &&
-        (!g->rep[HR_DF64][0] || g->mode != HR_LINKS_STORED)) {
+        (!g->rep[HR_DF64][0] || rebuild_for(g, HR_DF64))) {
         set_error("CG: float-float residuals need stored DF64 links in the handle");
         return HR_ERR_INVALID;
     }
@@ -590,6 +616,42 @@ extern "C" hr_status hr_cg_solve(const hr_gauge *g, hr_parity sys, const void *b
     st = prepare(ins[0], g, sys, b, x, nrhs, params->inner, params->residual, res, s);
     if (st != HR_OK) return st;
     return solve_all(ins, params, s);
+}
+
+extern "C" hr_status hr_cg_solve_force(const hr_gauge *g, hr_parity sys, const void *b, void *x,
+                                       const hr_cg_params *params, hr_cg_result *res, void *Y, double coeff,
+                                       void *F, void *stream)
+{
+    if (!g || !b || !x || !params || !res || !F) {
+        set_error("hr_cg_solve_force: NULL argument");
+        return HR_ERR_INVALID;
+    }
+    if (b == x) { set_error("hr_cg_solve_force: b and x must not overlap"); return HR_ERR_INVALID; }
+    hr_status st = check_params(g, sys, params);
+    if (st != HR_OK) return st;
+    if (!g->rep[HR_F64][0]) {
+        set_error("hr_cg_solve_force needs FP64 stored represented links in the handle");
+        return HR_ERR_INVALID;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<Inst> ins(1);
+    st = prepare(ins[0], g, sys, b, x, 1, params->inner, params->residual, res, s, true);
+    if (st != HR_OK) return st;
+    st = solve_all(ins, params, s);
+    if (st != HR_OK) return st;
+    Inst &in = ins[0];
+    const Ctx &c = in.c;
+    if (!in.fused_ok) {
+        // the last true residual was not an FP64 application to the final x
+        st = apply_A(c, HR_F64, in.vx, in.q2, in.q64, in.t64);
+        if (st != HR_OK) return st;
+    }
+    const size_t fb = field_rhs_bytes(c.ns, c.D, HR_F64);
+    if (Y) HR_CUDA_CHECK(cudaMemcpyAsync(Y, in.q64.data, fb, cudaMemcpyDeviceToDevice, s));
+    if (sys == HR_FULL) return force_full(g, in.vx, in.q64, coeff, reinterpret_cast<double *>(F), s);
+    // even/odd: minus the full-operator force on X' = (x, D_oe x), Y' = (Dhat x, (D^dag)_oe Dhat x)
+    HR_CUDA_CHECK(cudaMemcpyAsync(in.fx.data, x, fb, cudaMemcpyDeviceToDevice, s));
+    return force_full(g, in.fx, in.fy, -coeff, reinterpret_cast<double *>(F), s);
 }
 
 extern "C" hr_status hr_cg_solve_batched(int n_inst, const hr_gauge *const *g, hr_parity sys, const void *const *b,

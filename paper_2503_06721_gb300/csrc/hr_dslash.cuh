@@ -255,16 +255,18 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const HopParams prm)
 // bits; which one is fastest depends on N, R, precision, link mode, epilogue,
 // lattice and right-hand-side count, and the autotuner picks among them.
 //   HOP_DIRECT        hop_kernel: each lane loads its own neighbour records
-//   HOP_STAGED        hop_staged_kernel: warp-cooperative gathers through
-//                     shared memory, register budget for 2 (D_R > 4) or 3
-//                     (D_R <= 4) blocks of 128 threads per SM
+//   HOP_STAGED        hop_staged_kernel: warp-cooperative spinor gathers
+//                     through shared memory, register budget for 2 (D_R > 4)
+//                     or 3 (D_R <= 4) blocks of 128 threads per SM
 //   HOP_STAGED_TIGHT  the same held to 3 blocks per SM (D_R > 4 only)
+//   HOP_STAGED_LINKS  the staged kernel with the link records staged too
 // FP64 and DF64 have the direct kernel only: they are bound by FP64 (or
 // float-float) arithmetic, not by the memory system.
-enum { HOP_DIRECT = 0, HOP_STAGED = 1, HOP_STAGED_TIGHT = 2 };
-__host__ __device__ constexpr int hop_variants(int N, int REP, int P)
+enum { HOP_DIRECT = 0, HOP_STAGED = 1, HOP_STAGED_TIGHT = 2, HOP_STAGED_LINKS = 3, HOP_NVARIANTS = 4 };
+// bit v set: variant v is compiled for (N, REP, P)
+__host__ __device__ constexpr unsigned hop_variant_mask(int N, int REP, int P)
 {
-    return (P == HR_F64 || P == HR_DF64) ? 1 : rep_dim(N, REP) <= 4 ? 2 : 3;
+    return (P == HR_F64 || P == HR_DF64) ? 0x1u : rep_dim(N, REP) <= 4 ? 0xBu : 0xFu;
 }
 
 // host-side launchers, instantiated per (N, REP, P) in hr_dslash_inst.cu

@@ -13,11 +13,23 @@ constexpr int staged_minb(int variant)
     return rep_dim(N, REP) <= 4 ? 3 : (variant == HOP_STAGED ? 1 : 3);
 }
 
-template <int N, int REP, int P, bool RB, int EPI, int MINB>
+// the staged kernel with staged links: as many blocks per SM as its shared
+// memory allows (at most 4)
+template <int N, int REP, int P, bool RB, int EPI>
+constexpr int links_minb()
+{
+    constexpr int NCH = link_nchunk(P, rep_real(REP) && !RB, RB ? N * N : rep_dim(N, REP) * rep_dim(N, REP));
+    constexpr size_t smem = StageShape<P, rep_dim(N, REP), EPI, 2, NCH>::SMEM + 8192;
+    constexpr int b = (int)((size_t)227 * 1024 / smem);
+    return b < 1 ? 1 : b > 4 ? 4 : b;
+}
+
+template <int N, int REP, int P, bool RB, int EPI, int MINB, bool LST = false>
 static hr_status launch_staged(const HopParams &prm, dim3 grid, cudaStream_t stream)
 {
-    constexpr size_t smem = StageShape<P, rep_dim(N, REP), EPI>::SMEM;
-    auto kern = hop_staged_kernel<N, REP, P, RB, EPI, MINB>;
+    constexpr int NCH = link_nchunk(P, rep_real(REP) && !RB, RB ? N * N : rep_dim(N, REP) * rep_dim(N, REP));
+    constexpr size_t smem = StageShape<P, rep_dim(N, REP), EPI, 2, LST ? NCH : 0>::SMEM;
+    auto kern = hop_staged_kernel<N, REP, P, RB, EPI, MINB, 2, LST>;
     static const cudaError_t attr =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (attr != cudaSuccess) return cuda_fail(attr, "cudaFuncSetAttribute(hop_staged_kernel)");
@@ -38,6 +50,22 @@ static hr_status launch_staged_epi(const HopParams &prm, int epi, dim3 grid, cud
 }
 
 template <int N, int REP, int P, bool RB>
+static hr_status launch_links_epi(const HopParams &prm, int epi, dim3 grid, cudaStream_t stream)
+{
+    switch (epi) {
+    case EPI_STORE:
+        return launch_staged<N, REP, P, RB, EPI_STORE, links_minb<N, REP, P, RB, EPI_STORE>(), true>(prm, grid, stream);
+    case EPI_STORE_NORM:
+        return launch_staged<N, REP, P, RB, EPI_STORE_NORM, links_minb<N, REP, P, RB, EPI_STORE_NORM>(), true>(
+            prm, grid, stream);
+    case EPI_CG_UPDATE:
+        return launch_staged<N, REP, P, RB, EPI_CG_UPDATE, links_minb<N, REP, P, RB, EPI_CG_UPDATE>(), true>(
+            prm, grid, stream);
+    default: set_error("bad epilogue %d", epi); return HR_ERR_INVALID;
+    }
+}
+
+template <int N, int REP, int P, bool RB>
 static hr_status launch_epi(const HopParams &prm, int epi, int variant, cudaStream_t stream)
 {
     if constexpr (P == HR_DF64) {
@@ -48,20 +76,24 @@ static hr_status launch_epi(const HopParams &prm, int epi, int variant, cudaStre
             return HR_ERR_UNSUPPORTED;
         }
     }
-    if (variant < 0 || variant >= hop_variants(N, REP, P)) {
+    constexpr unsigned mask = hop_variant_mask(N, REP, P);
+    if (variant < 0 || variant >= HOP_NVARIANTS || !(mask & (1u << variant))) {
         set_error("hop kernel variant %d not compiled for this precision", variant);
         return HR_ERR_INVALID;
     }
     dim3 block(128);
     const unsigned nb = (unsigned)((prm.g.vh + 127) / 128);
     dim3 grid = prm.rhs_inner ? dim3(nb * (unsigned)prm.nrhs) : dim3(nb, (unsigned)prm.nrhs);
-    if constexpr (hop_variants(N, REP, P) > 1) {
+    if constexpr ((mask >> HOP_STAGED) & 1u) {
         if (variant == HOP_STAGED)
             return launch_staged_epi<N, REP, P, RB, staged_minb<N, REP>(HOP_STAGED)>(prm, epi, grid, stream);
     }
-    if constexpr (hop_variants(N, REP, P) > 2) {
+    if constexpr ((mask >> HOP_STAGED_TIGHT) & 1u) {
         if (variant == HOP_STAGED_TIGHT)
             return launch_staged_epi<N, REP, P, RB, staged_minb<N, REP>(HOP_STAGED_TIGHT)>(prm, epi, grid, stream);
+    }
+    if constexpr ((mask >> HOP_STAGED_LINKS) & 1u) {
+        if (variant == HOP_STAGED_LINKS) return launch_links_epi<N, REP, P, RB>(prm, epi, grid, stream);
     }
     if constexpr (P == HR_DF64) {
         if constexpr (!RB) hop_kernel<N, REP, P, false, EPI_STORE><<<grid, block, 0, stream>>>(prm);

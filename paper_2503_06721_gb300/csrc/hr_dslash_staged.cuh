@@ -29,8 +29,9 @@
 
 namespace hr {
 
-// shared-memory geometry of the staged kernel for (P, D, epilogue, pipeline depth)
-template <int P, int D, int EPI, int NST = 2>
+// shared-memory geometry of the staged kernel for (P, D, epilogue, pipeline
+// depth, 16-byte chunks per link record when the links are staged too, else 0)
+template <int P, int D, int EPI, int NST = 2, int LCH = 0>
 struct StageShape {
     static constexpr int PC = (P == HR_F64 || P == HR_DF64) ? P : HR_F32;  // r, x precision (CG update)
     static constexpr int NC = SpinorIO<P, D>::NV;                          // 16-byte chunks per record
@@ -38,8 +39,9 @@ struct StageShape {
     static constexpr int NMAX = (EPI == EPI_CG_UPDATE && NCC > NC) ? NCC : NC;
     static constexpr int SU = (NMAX % 2) ? NMAX : NMAX + 1;   // record stride in chunks (odd)
     static constexpr int BUF = 32 * SU;                       // chunks per warp buffer
+    static constexpr int LBUF = LCH * 32;                     // chunks per warp link buffer
     static constexpr int WARPS = 4;
-    static constexpr size_t SMEM = (size_t)WARPS * NST * BUF * 16;
+    static constexpr size_t SMEM = (size_t)WARPS * NST * (BUF + LBUF) * 16;
 };
 
 // the records of the sites held by the 32 lanes (lane s holds site `site`)
@@ -132,7 +134,11 @@ __device__ __forceinline__ void rec_store(uint4 *rec, const cx<typename St<P>::R
     for (int j = 0; j < NV; j++) rec[j] = raw[j];
 }
 
-template <int N, int REP, int P, bool REBUILD, int EPI, int MINB = 1, int NST = 2>
+// LST: the warp's link records of hop k+1 are copied to shared memory with
+// the spinors (one contiguous 512-byte-per-chunk block per slot in the AoSoA
+// layout), so both are in flight while hop k is computed and the links do not
+// occupy registers until they are used.
+template <int N, int REP, int P, bool REBUILD, int EPI, int MINB = 1, int NST = 2, bool LST = false>
 __global__ void __launch_bounds__(128, MINB) hop_staged_kernel(const HopParams prm)
 {
     using S = St<P>;
@@ -142,7 +148,7 @@ __global__ void __launch_bounds__(128, MINB) hop_staged_kernel(const HopParams p
     constexpr int NCOMP = REBUILD ? N * N : D * D;
     using SIO = SpinorIO<P, D>;
     using LIO = LinkIO<P, REAL, NCOMP>;
-    using Sh = StageShape<P, D, EPI, NST>;
+    using Sh = StageShape<P, D, EPI, NST, LST ? LIO::NCHUNK : 0>;
     static_assert(NST >= 2 && NST <= 4, "pipeline depth");
     constexpr int NC = Sh::NC, SU = Sh::SU;
 
@@ -150,9 +156,11 @@ __global__ void __launch_bounds__(128, MINB) hop_staged_kernel(const HopParams p
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // NST record buffers per warp; gather g (hops 0..7, then the diagonal
     // term's records as gather 8) lands in buffer g % NST
-    uint4 *const wbuf = stage_smem + (size_t)warp * NST * Sh::BUF;
+    uint4 *const wbuf = stage_smem + (size_t)warp * NST * (Sh::BUF + Sh::LBUF);
     auto buf = [&](int g) { return wbuf + (g % NST) * Sh::BUF; };
     auto own = [&](int g) { return wbuf + (g % NST) * Sh::BUF + lane * SU; };
+    // link buffers after the spinor buffers; chunk j of lane l at [j * 32 + l]
+    auto lbuf = [&](int g) { return wbuf + NST * Sh::BUF + (g % NST) * Sh::LBUF; };
 
     const Geom &g = prm.g;
     const int rhs = prm.rhs_inner ? (int)(blockIdx.x % prm.nrhs) : (int)blockIdx.y;
@@ -170,6 +178,25 @@ __global__ void __launch_bounds__(128, MINB) hop_staged_kernel(const HopParams p
     const Site st = site_of(g, ie, prm.out_parity);
     const long tile = ie / HR_TILE;
     const int llane = (int)(ie % HR_TILE);
+    // the warp's own tile (a block of 128 threads covers 4 whole tiles); a warp
+    // entirely past the end copies the last tile's records and stores nothing
+    const long wtile = min(wfirst / HR_TILE, g.ntiles - 1);
+    const bool keep = prm.rhs_inner;   // other rhs re-read these links from L2
+    uint64_t lpol = 0;
+    if constexpr (LST) lpol = policy_evict_first();
+    auto copy_links = [&](int kk) {
+        if constexpr (LST) {
+            const uint4 *src = LIO::slot_ptr(prm.links, wtile, kk, 0);
+            uint4 *dst = lbuf(kk);
+#pragma unroll
+            for (int j = 0; j < LIO::NCHUNK; j++) {
+                if (keep)
+                    cp_async16(dst + j * 32 + lane, src + (size_t)j * HR_TILE + lane);
+                else
+                    cp_async16_hint(dst + j * 32 + lane, src + (size_t)j * HR_TILE + lane, lpol);
+            }
+        }
+    };
 
     cx<R> acc[4][D];
 #pragma unroll
@@ -189,6 +216,7 @@ __global__ void __launch_bounds__(128, MINB) hop_staged_kernel(const HopParams p
         const int site = gather_site(q);
         scale_q[q] = (R)SIO::ld_scale(prm.in, rhs, site);
         warp_gather<NC, SU>(buf(q), in_base, site, lane);
+        copy_links(q);
         cp_async_commit();
     }
 
@@ -205,6 +233,7 @@ __global__ void __launch_bounds__(128, MINB) hop_staged_kernel(const HopParams p
                 const int site = gather_site(q);
                 scale_q[q % NST] = (R)SIO::ld_scale(prm.in, rhs, site);
                 warp_gather<NC, SU>(buf(q), in_base, site, lane);
+                copy_links(q);
             } else if (q == 8 && diag_base) {
                 warp_gather<NC, SU>(buf(8), diag_base, (int)ie, lane);
             }
@@ -230,13 +259,17 @@ __global__ void __launch_bounds__(128, MINB) hop_staged_kernel(const HopParams p
                     h[r][c] = up + sp * ipow(ephase(mu, r), dn);
                 }
         }
-        __syncwarp();   // the buffer is refilled by gather k+NST
         cx<R> chi[2][D];
-        const uint4 *lp = LIO::slot_ptr(prm.links, tile, k, llane);
-        const bool keep = prm.rhs_inner;
+        const uint4 *lp = LST ? lbuf(k) + lane : LIO::slot_ptr(prm.links, tile, k, llane);
+        auto load_links = [&](auto &W) {
+            if constexpr (LST)
+                LIO::load_shared(lp, W);
+            else
+                LIO::load(lp, W, keep);
+        };
         if constexpr (REBUILD) {
             cx<R> Wf[N * N];
-            LIO::load(lp, Wf, keep);
+            load_links(Wf);
             cx<R> F[N][N];
 #pragma unroll
             for (int a = 0; a < N; a++)
@@ -252,9 +285,33 @@ __global__ void __launch_bounds__(128, MINB) hop_staged_kernel(const HopParams p
 #pragma unroll
                     for (int c = 0; c < D; c++) chi[r][c] = (R)-1 * chi[r][c];
             }
+        } else if constexpr (LST) {
+            // links from shared memory one row at a time (the compiler barrier
+            // keeps the rows from being hoisted into one register-hungry block)
+#pragma unroll
+            for (int row = 0; row < D; row++) {
+                cx<R> s0 = {0, 0}, s1 = {0, 0};
+#pragma unroll
+                for (int col = 0; col < D; col++) {
+                    const int cc = row * D + col;
+                    const uint4 v = lp[(cc / LIO::VPC) * HR_TILE];
+                    if constexpr (REAL) {
+                        const R w = LIO::runpack(v, cc % LIO::VPC);
+                        rmac(s0, w, h[0][col]);
+                        rmac(s1, w, h[1][col]);
+                    } else {
+                        const cx<R> w = LIO::cunpack(v, cc % LIO::VPC);
+                        cmac(s0, w, h[0][col]);
+                        cmac(s1, w, h[1][col]);
+                    }
+                }
+                chi[0][row] = s0;
+                chi[1][row] = s1;
+                asm volatile("" ::: "memory");
+            }
         } else if constexpr (REAL) {
             R W[D * D];
-            LIO::load(lp, W, keep);
+            load_links(W);
 #pragma unroll
             for (int row = 0; row < D; row++) {
                 cx<R> s0 = {0, 0}, s1 = {0, 0};
@@ -268,7 +325,7 @@ __global__ void __launch_bounds__(128, MINB) hop_staged_kernel(const HopParams p
             }
         } else {
             cx<R> W[D * D];
-            LIO::load(lp, W, keep);
+            load_links(W);
 #pragma unroll
             for (int row = 0; row < D; row++) {
                 cx<R> s0 = {0, 0}, s1 = {0, 0};
@@ -281,6 +338,7 @@ __global__ void __launch_bounds__(128, MINB) hop_staged_kernel(const HopParams p
                 chi[1][row] = s1;
             }
         }
+        __syncwarp();   // this hop's buffers are refilled by gather k+NST
 #pragma unroll
         for (int r = 0; r < 2; r++)
 #pragma unroll

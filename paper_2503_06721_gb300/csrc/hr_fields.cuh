@@ -268,6 +268,28 @@ struct LinkIO {
                 if (j * VPC + k < NCOMP) W[j * VPC + k] = runpack(v, k);
         }
     }
+    // the same from a copy of the warp's slot records in shared memory
+    // (chunk j of lane l at p[j * 32], p = base + l)
+    __device__ __forceinline__ static void load_shared(const uint4 *p, cx<R> (&W)[NCOMP])
+    {
+#pragma unroll
+        for (int j = 0; j < NCHUNK; j++) {
+            const uint4 v = p[j * HR_TILE];
+#pragma unroll
+            for (int k = 0; k < VPC; k++)
+                if (j * VPC + k < NCOMP) W[j * VPC + k] = cunpack(v, k);
+        }
+    }
+    __device__ __forceinline__ static void load_shared(const uint4 *p, R (&W)[NCOMP])
+    {
+#pragma unroll
+        for (int j = 0; j < NCHUNK; j++) {
+            const uint4 v = p[j * HR_TILE];
+#pragma unroll
+            for (int k = 0; k < VPC; k++)
+                if (j * VPC + k < NCOMP) W[j * VPC + k] = runpack(v, k);
+        }
+    }
 };
 
 }  // namespace hr

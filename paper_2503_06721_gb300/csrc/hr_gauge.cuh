@@ -35,6 +35,7 @@ struct hr_gauge {
     // chosen by the autotuner; -1 = not tuned (a fixed default applies)
     signed char tuned[HR_NPREC][2][3][2];
     int force_variant;    // >= 0: every launch uses this variant (testing)
+    signed char auto_mode[HR_NPREC];   // HR_LINKS_AUTO: the tuned mode per precision, -1 = not tuned
     int autotune;         // 1: the solver tunes its inner precision before iterating
 };
 

@@ -2,10 +2,10 @@
 //
 // The hopping kernel exists as a direct variant (each lane loads its own
 // neighbour records) and as shared-memory-staged variants (the warp moves
-// its 32 records cooperatively) at one or two register budgets.  All compute
-// the same bits.  Which is fastest depends on the representation (record
-// sizes, registers), the precision, the link mode, the epilogue and the
-// lattice, so the choice is measured: every variant of every epilogue is
+// its 32 records cooperatively) at two register budgets and with the link
+// records staged as well.  All compute the same bits.  Which is fastest
+// depends on the representation (record sizes, registers), the precision,
+// the link mode, the epilogue and the lattice, so the choice is measured: every variant of every epilogue is
 // launched on zero-filled scratch fields of the handle's lattice, timed with
 // CUDA events on the caller's stream, and the fastest is recorded in the
 // handle per (precision, link mode, epilogue, nrhs == 1 / > 1).
@@ -39,11 +39,37 @@ constexpr int TUNE_REPS = 3;
 
 }  // namespace
 
+// time the variants of every epilogue in the current link mode of P; record
+// the fastest and return one CG iteration's worth of their times
+static hr_status tune_mode(hr_gauge *g, int P, int nrhs, cudaStream_t s, float *iteration_ms);
+
 hr_status tune_hops(hr_gauge *g, int P, int nrhs, cudaStream_t s)
 {
-    const int nv = hop_variant_count(g, P);
-    if (nv <= 1) return HR_OK;
-    const bool rb = g->mode == HR_LINKS_REBUILD;
+    const bool both = g->mode == HR_LINKS_AUTO && g->rep[P][0] && g->fund[P][0];
+    if (!both) {
+        if (g->mode == HR_LINKS_AUTO) g->auto_mode[P] = g->rep[P][0] ? HR_LINKS_STORED : HR_LINKS_REBUILD;
+        if (hop_variants_of(g, P) == 0x1u) return HR_OK;
+        float t;
+        return tune_mode(g, P, nrhs, s, &t);
+    }
+    // AUTO: measure both ways of obtaining U_R and keep the faster for P
+    float t_mode[2];
+    for (int m = HR_LINKS_STORED; m <= HR_LINKS_REBUILD; m++) {
+        g->auto_mode[P] = (signed char)m;
+        hr_status st = tune_mode(g, P, nrhs, s, &t_mode[m]);
+        if (st != HR_OK) {
+            g->auto_mode[P] = -1;
+            return st;
+        }
+    }
+    g->auto_mode[P] = (signed char)(t_mode[HR_LINKS_REBUILD] < t_mode[HR_LINKS_STORED] ? HR_LINKS_REBUILD : HR_LINKS_STORED);
+    return HR_OK;
+}
+
+static hr_status tune_mode(hr_gauge *g, int P, int nrhs, cudaStream_t s, float *iteration_ms)
+{
+    const unsigned mask = hop_variants_of(g, P);
+    const bool rb = rebuild_for(g, P);
     const int D = g->D;
     const long vh = g->geom.vh;
     const int PC = P == HR_F64 ? HR_F64 : HR_F32;   // r and x of a fused CG update
@@ -108,10 +134,12 @@ hr_status tune_hops(hr_gauge *g, int P, int nrhs, cudaStream_t s)
     EventPair ev;
     HR_CUDA_CHECK(cudaEventCreate(&ev.a));
     HR_CUDA_CHECK(cudaEventCreate(&ev.b));
+    *iteration_ms = 0;
     for (int epi = EPI_STORE; epi <= EPI_CG_UPDATE; epi++) {
         float best = 0;
-        int best_v = HOP_DIRECT;
-        for (int v = 0; v < nv; v++) {
+        int best_v = -1;
+        for (int v = 0; v < HOP_NVARIANTS; v++) {
+            if (!((mask >> v) & 1u)) continue;
             hr_status st = launch(epi, v);   // warm-up (and first-use setup)
             if (st != HR_OK) return st;
             HR_CUDA_CHECK(cudaEventRecord(ev.a, s));
@@ -123,12 +151,13 @@ hr_status tune_hops(hr_gauge *g, int P, int nrhs, cudaStream_t s)
             HR_CUDA_CHECK(cudaEventSynchronize(ev.b));
             float ms = 0;
             HR_CUDA_CHECK(cudaEventElapsedTime(&ms, ev.a, ev.b));
-            if (v == 0 || ms < best) {
+            if (best_v < 0 || ms < best) {
                 best = ms;
                 best_v = v;
             }
         }
         g->tuned[P][rb ? 1 : 0][epi][nrhs > 1 ? 1 : 0] = (signed char)best_v;
+        *iteration_ms += (epi == EPI_STORE ? 2.0f : 1.0f) * best / TUNE_REPS;
     }
     HR_CUDA_CHECK(cudaStreamSynchronize(s));
     return HR_OK;
@@ -151,7 +180,7 @@ hr_status hr_tune(hr_gauge *g, hr_prec prec, int nrhs, void *stream)
 
 hr_status hr_gauge_set_tuning(hr_gauge *g, int autotune, int variant)
 {
-    if (!g || (autotune != 0 && autotune != 1) || variant < -1 || variant > HR_HOP_STAGED_TIGHT) {
+    if (!g || (autotune != 0 && autotune != 1) || variant < -1 || variant > HR_HOP_STAGED_LINKS) {
         set_error("hr_gauge_set_tuning: bad arguments");
         return HR_ERR_INVALID;
     }
@@ -164,7 +193,7 @@ int hr_gauge_hop_variant(const hr_gauge *g, hr_prec prec, int epilogue, int nrhs
 {
     if (!g || prec < HR_F64 || prec > HR_DF64 || epilogue < HR_EPI_STORE || epilogue > HR_EPI_CG_UPDATE || nrhs < 1)
         return -1;
-    return hop_variant(g, prec, g->mode == HR_LINKS_REBUILD, epilogue, nrhs);
+    return hop_variant(g, prec, rebuild_for(g, prec), epilogue, nrhs);
 }
 
 }  // extern "C"

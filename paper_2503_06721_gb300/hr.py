@@ -24,9 +24,9 @@ REPS = {"FUND": FUND, "ADJ": ADJ, "SYM": SYM, "ASYM": ASYM, "2AS": ASYM}
 F64, F32, F16, BF16, DF64 = 0, 1, 2, 3, 4
 PRECS = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16, "df64": DF64}
 EVEN, ODD, FULL, EO_PRECOND = 0, 1, 2, 3
-HOP_DIRECT, HOP_STAGED, HOP_STAGED_TIGHT = 0, 1, 2
+HOP_DIRECT, HOP_STAGED, HOP_STAGED_TIGHT, HOP_STAGED_LINKS = 0, 1, 2, 3
 EPI_STORE, EPI_STORE_NORM, EPI_CG_UPDATE = 0, 1, 2
-LINKS_STORED, LINKS_REBUILD = 0, 1
+LINKS_STORED, LINKS_REBUILD, LINKS_AUTO = 0, 1, 2
 
 STATUS = {0: "HR_OK", -1: "HR_ERR_INVALID", -2: "HR_ERR_CUDA", -3: "HR_ERR_NOMEM",
           -4: "HR_ERR_NOT_CONVERGED", -5: "HR_ERR_NONFINITE", -6: "HR_ERR_TIMEOUT",
@@ -34,10 +34,10 @@ STATUS = {0: "HR_OK", -1: "HR_ERR_INVALID", -2: "HR_ERR_CUDA", -3: "HR_ERR_NOMEM
 
 # every symbol include/hr.h declares
 EXPORTS = ["hr_represent_gauge", "hr_gauge_update", "hr_gauge_set_link_mode", "hr_gauge_destroy",
-           "hr_tune", "hr_gauge_set_tuning", "hr_gauge_hop_variant",
+           "hr_tune", "hr_gauge_set_tuning", "hr_gauge_hop_variant", "hr_gauge_link_mode",
            "hr_field_bytes", "hr_field_convert", "hr_field_dot", "hr_field_dot_static",
            "hr_dirac_apply", "hr_dirac_dagger",
-           "hr_cg_solve", "hr_cg_solve_batched", "hr_dirac_force", "hr_rep_dim", "hr_generators",
+           "hr_cg_solve", "hr_cg_solve_batched", "hr_cg_solve_force", "hr_dirac_force", "hr_rep_dim", "hr_generators",
            "hr_status_string", "hr_last_error", "hr_launch_count"]
 
 
@@ -88,6 +88,7 @@ def load():
         "hr_tune": (I, [P, I, I, P]),
         "hr_gauge_set_tuning": (I, [P, I, I]),
         "hr_gauge_hop_variant": (I, [P, I, I, I]),
+        "hr_gauge_link_mode": (I, [P, I]),
         "hr_field_bytes": (S, [LP, I, I, I]),
         "hr_field_convert": (I, [LP, I, I, P, I, P, I, P]),
         "hr_field_dot": (I, [LP, I, I, P, P, I, ctypes.POINTER(D), P]),
@@ -99,6 +100,7 @@ def load():
                                     ctypes.POINTER(I), ctypes.POINTER(CgParams),
                                     ctypes.POINTER(CgResult), P]),
         "hr_dirac_force": (I, [P, I, P, P, D, P, P]),
+        "hr_cg_solve_force": (I, [P, I, P, P, ctypes.POINTER(CgParams), ctypes.POINTER(CgResult), P, D, P, P]),
         "hr_rep_dim": (I, [I, I]),
         "hr_generators": (I, [I, ctypes.POINTER(D)]),
         "hr_status_string": (ctypes.c_char_p, [I]),
@@ -248,6 +250,10 @@ class Gauge:
     def hop_variant(self, prec: int, epilogue: int, nrhs: int = 1) -> int:
         return load().hr_gauge_hop_variant(self.handle, prec, epilogue, nrhs)
 
+    def link_mode(self, prec: int) -> int:
+        """the link mode (LINKS_STORED or LINKS_REBUILD) launches in prec use now"""
+        return load().hr_gauge_link_mode(self.handle, prec)
+
     def close(self):
         if self.handle and self.handle.value:
             load().hr_gauge_destroy(self.handle)
@@ -288,6 +294,26 @@ class Gauge:
         out = [dict(iters=r.iters, outer_iters=r.outer_iters, true_rel_residual=r.true_rel_residual,
                     status=STATUS.get(r.status, r.status)) for r in res]
         return x, out, st
+
+    def cg_solve_force(self, sys: int, b, x=None, tol: float = 1e-10, max_iter: int = 10000,
+                       inner: int = F64, inner_tol: float = 1e-5, residual: int = F64, coeff: float = 1.0,
+                       F=None, want_y: bool = False, stream=None, check: bool = True):
+        """x = A^-1 b and F += coeff * force(x, D x) in one call (hr_cg_solve_force)."""
+        if x is None:
+            x = torch.zeros_like(b)
+        if F is None:
+            F = torch.zeros((self.lat.volume, 4, self.lat.N ** 2 - 1), dtype=torch.float64,
+                            device=b.device)
+        Y = torch.empty_like(b) if want_y else None
+        p = CgParams(tol, max_iter, inner, inner_tol, 0, residual)
+        res = (CgResult * 1)()
+        st = load().hr_cg_solve_force(self.handle, sys, _ptr(b), _ptr(x), ctypes.byref(p), res,
+                                      _ptr(Y), coeff, _ptr(F), _stream(stream))
+        if check:
+            _check(st)
+        out = [dict(iters=r.iters, outer_iters=r.outer_iters, true_rel_residual=r.true_rel_residual,
+                    status=STATUS.get(r.status, r.status)) for r in res]
+        return x, F, Y, out, st
 
     def force(self, sys: int, X, Y, coeff: float = 1.0, F=None, stream=None):
         if F is None:

@@ -143,3 +143,30 @@ def test_force_parity(hr, oracle_mod, N, rep):
     Fo = -oracle_mod.force(L, UR, Xp, Yp)
     F = g.force(hr.EO_PRECOND, G.to_gpu(Xe), G.to_gpu(Ye), coeff=2.0)
     np.testing.assert_allclose(F.cpu().numpy(), 2.0 * Fo, atol=1e-12 * np.abs(Fo).max())
+
+
+@pytest.mark.parametrize("N,rep", [(3, "SYM"), (3, "ADJ"), (4, "FUND")])
+@pytest.mark.parametrize("sys", [3, 2], ids=["eo", "full"])
+@pytest.mark.parametrize("inner", [0, 1], ids=["f64", "f32"])
+def test_cg_solve_force_fused(hr, oracle_mod, N, rep, sys, inner):
+    """hr_cg_solve_force equals hr_cg_solve + Y = D x + hr_dirac_force bit for
+    bit: it applies the same FP64 kernels to the same x, it only keeps the
+    operator applications of the final true residual instead of redoing them."""
+    dims = (8, 4, 4, 6)
+    lat = hr.Lattice(N, rep, dims, (-1, 1, 1, 1), -0.2)
+    UF = H.links(dims, N, 0.5, seed=31)
+    g = hr.Gauge(lat, G.to_gpu(UF), precs=("f64", "f32"))
+    ns = lat.nsites(sys if sys == hr.FULL else hr.EVEN)
+    b = G.to_gpu(H.spinor(ns, lat.D, 23))
+    x1, F1, Y1, res, st = g.cg_solve_force(sys, b, tol=1e-10, inner=inner, inner_tol=1e-4, coeff=0.7,
+                                           want_y=True)
+    assert st == 0 and res[0]["true_rel_residual"] <= 1e-10
+    x2, res2, st2 = g.cg_solve(sys, b, tol=1e-10, inner=inner, inner_tol=1e-4)
+    assert st2 == 0
+    Y2 = g.apply(sys, hr.F64, x2)
+    F2 = g.force(sys, x2, Y2, coeff=0.7)
+    torch.cuda.synchronize()
+    assert torch.equal(x1, x2)
+    assert torch.equal(Y1, Y2)
+    assert torch.equal(F1, F2)
+    g.close()

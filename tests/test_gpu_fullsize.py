@@ -88,6 +88,7 @@ def test_sym_32x32x32x64_deo(hr, oracle_mod):
     lat = hr.Lattice(wl.N, wl.rep, wl.dims, wl.bc, wl.m0)
     U = wl.links(device="cuda")
     g = hr.Gauge(lat, U, precs=("f64", "f32"), stored=True)
+    g.tune(hr.F32)   # the benchmark's kernel variants
     x = synth.gaussian_spinor(lat.volume // 2, lat.D, 5, device="cuda")
     for prec, dt in ((hr.F64, torch.complex128), (hr.F32, torch.complex64)):
         xin = x.to(dt)
@@ -112,6 +113,7 @@ def test_adj_64x64x64x128_stored_and_rebuilt(hr, oracle_mod):
     x = synth.gaussian_spinor(lat.volume // 2, lat.D, 7, device="cuda").to(torch.complex64)
     for mode in (hr.LINKS_STORED, hr.LINKS_REBUILD):
         g.set_link_mode(mode)
+        g.tune(hr.F32)
         y = g.apply(hr.EVEN, hr.F32, x)
         _sampled_check(hr, oracle_mod, wl, U, x, y, 0, False, G.TOL[hr.F32], seed=mode)
         del y
@@ -127,6 +129,8 @@ def test_su4_24x24x24x48_deo(hr, oracle_mod, name):
     lat = hr.Lattice(wl.N, wl.rep, wl.dims, wl.bc, wl.m0)
     U = wl.links(device="cuda")
     g = hr.Gauge(lat, U, precs=("f32", "f16"), stored=True)
+    g.tune(hr.F32)
+    g.tune(hr.F16)
     x = synth.gaussian_spinor(lat.volume // 2, lat.D, 9, device="cuda")
     y = g.apply(hr.EVEN, hr.F32, x.to(torch.complex64))
     _sampled_check(hr, oracle_mod, wl, U, x.to(torch.complex64), y, 0, False, G.TOL[hr.F32])
@@ -141,17 +145,34 @@ def test_su4_24x24x24x48_deo(hr, oracle_mod, name):
 
 
 def test_sym_32x32x32x64_mixed_cg(hr, oracle_mod):
-    """Mixed-precision (FP32 inner) CG on Dhat^dag Dhat reaches 1e-10; the true
-    residual is recomputed in FP64 by the library and cross-checked at sampled
-    sites of Dhat x by the oracle's hopping term."""
+    """The benchmark's solve, in its launch configuration (stored and
+    fundamental links, link mode and kernel variants chosen by the tuner,
+    fused solve + force): mixed-precision (FP32 inner) CG on Dhat^dag Dhat
+    reaches 1e-10; the true residual is recomputed in FP64 by the library and
+    cross-checked at sampled sites of Dhat x by the oracle's hopping term; the
+    FP32 operator in the solver's link mode matches the oracle at sampled
+    sites; the fused force equals solve + apply + force."""
     from paper_2503_06721_gb300 import synth
     wl = synth.WORKLOADS["su3_sym_64x32x32x32"]
     lat = hr.Lattice(wl.N, wl.rep, wl.dims, wl.bc, wl.m0)
     U = wl.links(device="cuda")
-    g = hr.Gauge(lat, U, precs=("f64", "f32"), stored=True)
+    g = hr.Gauge(lat, U, precs=("f64", "f32"), stored=True, rebuild=True)
+    g.set_link_mode(hr.LINKS_AUTO)
+    g.tune(hr.F32)
+    g.tune(hr.F64)
     b = synth.gaussian_spinor(lat.volume // 2, lat.D, 13, device="cuda")
-    x, res, st = g.cg_solve(hr.EO_PRECOND, b, tol=1e-10, inner=hr.F32, inner_tol=1e-5)
+    x, F, Y, res, st = g.cg_solve_force(hr.EO_PRECOND, b, tol=1e-10, inner=hr.F32, inner_tol=1e-5,
+                                        coeff=-1.0, want_y=True)
     assert st == 0 and res[0]["true_rel_residual"] <= 1e-10
+    if g.link_mode(hr.F64) == hr.LINKS_STORED:
+        F2 = g.force(hr.EO_PRECOND, x, g.apply(hr.EO_PRECOND, hr.F64, x), coeff=-1.0)
+        assert torch.equal(F, F2)
+        del F2
+    del F, Y
+    x32 = x.to(torch.complex64)
+    y32 = g.apply(hr.EVEN, hr.F32, x32)
+    _sampled_check(hr, oracle_mod, wl, U, x32, y32, 0, False, G.TOL[hr.F32], seed=4)
+    del x32, y32
     # independent residual: A x - b with A applied hop by hop and |.| by field_dot
     t = g.apply(hr.EO_PRECOND, hr.F64, x)
     Ax = g.apply(hr.EO_PRECOND, hr.F64, t, dagger=True)

@@ -1,5 +1,6 @@
 """The hopping-kernel variants (direct, shared-memory staged, staged at a
-tighter register budget) and the autotuner that picks among them.
+tighter register budget, staged with staged links) and the autotuner that
+picks among them.
 
 Every variant must produce the same bits as the direct kernel in every
 epilogue: the plain store (D_eo, D_oe, D_m, Dhat and their adjoints), the
@@ -37,7 +38,7 @@ def _gauge(hr, N, rep, dims=DIMS, m0=-0.23, rebuild=False):
 
 
 def _variants(lat):
-    return [0, 1] if lat.D <= 4 else [0, 1, 2]
+    return [0, 1, 3] if lat.D <= 4 else [0, 1, 2, 3]
 
 
 def _written_bytes(hr, lat, par, prec, y):
@@ -117,7 +118,7 @@ def test_tune_records_a_compiled_variant(hr):
 
 def test_tuning_arguments_checked(hr):
     lat, g = _gauge(hr, 3, "SYM")
-    for bad in ((2, -1), (1, 3), (1, -2)):
+    for bad in ((2, -1), (1, 4), (1, -2)):
         with pytest.raises(hr.HrError) as e:
             g.set_tuning(*bad)
         assert e.value.status == -1
@@ -126,4 +127,27 @@ def test_tuning_arguments_checked(hr):
         g2.tune(hr.F32)
     assert g2.hop_variant(hr.F64, 7, 1) == -1
     g.close()
+    g2.close()
+
+
+def test_auto_link_mode(hr, oracle_mod):
+    """LINKS_AUTO: the tuner keeps, per precision, the faster of stored and
+    rebuilt links; solves in that mode still meet their tolerance, and the
+    mode needs both storages."""
+    lat, g = _gauge(hr, 3, "SYM", dims=(8, 8, 8, 8), rebuild=True)
+    g.set_link_mode(hr.LINKS_AUTO)
+    assert g.link_mode(hr.F32) == hr.LINKS_STORED   # until tuned
+    g.tune(hr.F32)
+    assert g.link_mode(hr.F32) in (hr.LINKS_STORED, hr.LINKS_REBUILD)
+    b = H.spinor(lat.volume // 2, lat.D, 12)
+    x, res, st = g.cg_solve(hr.EO_PRECOND, G.to_gpu(b), tol=1e-10, inner=hr.F32, inner_tol=1e-4)
+    assert st == 0 and res[0]["true_rel_residual"] <= 1e-10
+    L = oracle_mod.lat(3, "SYM", (8, 8, 8, 8), (-1, 1, 1, 1), -0.23)
+    UR = oracle_mod.represent_field(L, H.links((8, 8, 8, 8), 3, 0.6, seed=21))
+    r = b - oracle_mod.dhat(L, UR, oracle_mod.dhat(L, UR, x.cpu().numpy()), dagger=True)
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.001e-10
+    g.close()
+    lat2, g2 = _gauge(hr, 3, "SYM")
+    with pytest.raises(hr.HrError):
+        g2.set_link_mode(hr.LINKS_AUTO)
     g2.close()
