@@ -207,7 +207,7 @@ def run_ours(args, rank, world, local_rank):
     Fbuf = torch.zeros((lat.volume, 4, wl.N ** 2 - 1), dtype=torch.float64, device=dev)
     xbuf = torch.zeros_like(phi)
 
-    def step(phi_dev, U_dev):
+    def step(phi_dev, U_dev, xb=xbuf, Fb=Fbuf, phase_times=True):
         pev[0].record(stream)
         g.update(U_dev)
         pev[1].record(stream)
@@ -222,14 +222,15 @@ def run_ours(args, rank, world, local_rank):
         # x = (Dhat^dag Dhat)^-1 phi and the force of S = phi^dag x in one call;
         # the force's Dhat x, D_oe x and (D^dag)_oe Dhat x come from the
         # solve's final FP64 true residual
-        Fbuf.zero_()
-        x, F, _, res, st = g.cg_solve_force(hr.EO_PRECOND, phi_dev, x=xbuf, tol=TOL, max_iter=20000,
+        Fb.zero_()
+        x, F, _, res, st = g.cg_solve_force(hr.EO_PRECOND, phi_dev, x=xb, tol=TOL, max_iter=20000,
                                             inner=hr.F32, inner_tol=1e-5, residual=res_prec, coeff=-1.0,
-                                            F=Fbuf)
+                                            F=Fb)
         pev[3].record(stream)
-        torch.cuda.synchronize()
-        for name, a, b in (("represent", 0, 1), ("deo", 1, 2), ("cg_force", 2, 3)):
-            phases[name] += pev[a].elapsed_time(pev[b])
+        if phase_times:
+            torch.cuda.synchronize()
+            for name, a, b in (("represent", 0, 1), ("deo", 1, 2), ("cg_force", 2, 3)):
+                phases[name] += pev[a].elapsed_time(pev[b])
         r = res[0]
         # hop launches of this step by precision
         h32 = n_deo + 4 * r["iters"]
@@ -283,28 +284,59 @@ def run_ours(args, rank, world, local_rank):
 
     # end to end through the C ABI with host buffers: inputs copied in and the
     # solution and force copied out inside the timed region
+    # end to end with host buffers: every step copies its inputs (gauge field,
+    # pseudofermion) from pinned host memory and its results (solution, force)
+    # back.  The copies run on their own stream, double-buffered: step k+1's
+    # inputs arrive while step k computes, and step k's results leave while
+    # step k+1 computes; all of them lie inside the timed region.
     e2e = None
     if not args.no_e2e:
         U_h = U.cpu().pin_memory()
         phi_h = phi.cpu().pin_memory()
-        U_d = torch.empty_like(U)
-        phi_d = torch.empty_like(phi)
-        X_h = torch.empty(phi.shape, dtype=phi.dtype).pin_memory()
-        F_h = torch.empty((lat.volume, 4, wl.N ** 2 - 1), dtype=torch.float64).pin_memory()
+        X_h = [torch.empty(phi.shape, dtype=phi.dtype).pin_memory() for _ in range(2)]
+        F_h = [torch.empty((lat.volume, 4, wl.N ** 2 - 1), dtype=torch.float64).pin_memory() for _ in range(2)]
+        U_d = [torch.empty_like(U) for _ in range(2)]
+        phi_d = [torch.empty_like(phi) for _ in range(2)]
+        x_d = [xbuf, torch.empty_like(phi)]
+        F_d = [Fbuf, torch.empty_like(Fbuf)]
+        cs = torch.cuda.Stream(device=dev)
+        ready = [torch.cuda.Event() for _ in range(2)]
+        done = [torch.cuda.Event() for _ in range(2)]
+        sent = [torch.cuda.Event() for _ in range(2)]
         work["bytes"] = 0
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
         t0.record(stream)
-        for _ in range(args.steps):
-            U_d.copy_(U_h, non_blocking=True)
-            phi_d.copy_(phi_h, non_blocking=True)
-            x, F = step(phi_d, U_d)
-            X_h.copy_(x, non_blocking=True)
-            F_h.copy_(F, non_blocking=True)
+        cs.wait_stream(stream)
+        with torch.cuda.stream(cs):
+            U_d[0].copy_(U_h, non_blocking=True)
+            phi_d[0].copy_(phi_h, non_blocking=True)
+            ready[0].record(cs)
+        for k in range(args.steps):
+            b, nb = k % 2, (k + 1) % 2
+            if k + 1 < args.steps:
+                with torch.cuda.stream(cs):
+                    if k >= 1:
+                        cs.wait_event(done[nb])      # step k-1 is finished with these buffers
+                    U_d[nb].copy_(U_h, non_blocking=True)
+                    phi_d[nb].copy_(phi_h, non_blocking=True)
+                    ready[nb].record(cs)
+            stream.wait_event(ready[b])
+            if k >= 2:
+                stream.wait_event(sent[b])           # step k-2's results have left
+            x, F = step(phi_d[b], U_d[b], x_d[b], F_d[b], phase_times=False)
+            done[b].record(stream)
+            with torch.cuda.stream(cs):
+                cs.wait_event(done[b])
+                X_h[b].copy_(x, non_blocking=True)
+                F_h[b].copy_(F, non_blocking=True)
+                sent[b].record(cs)
+        stream.wait_stream(cs)
         t1.record(stream)
         torch.cuda.synchronize()
         ems = t0.elapsed_time(t1)
+        X_h, F_h = X_h[0], F_h[0]
         evalue, ems_step = job_throughput(work["bytes"] / args.steps, ems, args.steps, dist, dev)
         e2e = {"value": round(evalue, 1), "unit": UNIT, "ms_per_step": round(ems_step, 3),
                "h2d_bytes_per_step": U_h.numel() * 16 + phi_h.numel() * 16,
@@ -630,7 +662,7 @@ def main():
                          "confirmed once in FP64 when it meets the tolerance)")
     ap.add_argument("--rebuild", action="store_true", help="deo mode: rebuild links in-kernel")
     ap.add_argument("--nrhs", type=int, default=1, help="deo mode: right-hand sides per application")
-    ap.add_argument("--variant", type=int, default=None, choices=[0, 1, 2, 3],
+    ap.add_argument("--variant", type=int, default=None, choices=[0, 1, 2, 3, 4],
                     help="deo mode: force a hopping-kernel variant instead of autotuning")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per D_eo launch, when known for the current kernel")

@@ -139,12 +139,15 @@ hr_status hr_gauge_destroy(hr_gauge *g);
  *   HR_HOP_STAGED_TIGHT  the staged kernel at a smaller register budget
  *                        (D_R > 4 only);
  *   HR_HOP_STAGED_LINKS  the staged kernel with the link records staged
- *                        through shared memory as well.
+ *                        through shared memory as well;
+ *   HR_HOP_MRHS          for nrhs >= 2: a block of 4 right-hand sides shares
+ *                        each loaded link record (a9).
  * FP64 and DF64 have the direct variant only.  Launches are identified by
  * their epilogue: HR_EPI_STORE (out = a H in), HR_EPI_STORE_NORM (the same
  * plus |out|^2), HR_EPI_CG_UPDATE (the fused r -= alpha A p, x += alpha p,
  * |r|^2 of a CG iteration). */
-enum { HR_HOP_DIRECT = 0, HR_HOP_STAGED = 1, HR_HOP_STAGED_TIGHT = 2, HR_HOP_STAGED_LINKS = 3 };
+enum { HR_HOP_DIRECT = 0, HR_HOP_STAGED = 1, HR_HOP_STAGED_TIGHT = 2, HR_HOP_STAGED_LINKS = 3,
+       HR_HOP_MRHS = 4 };
 enum { HR_EPI_STORE = 0, HR_EPI_STORE_NORM = 1, HR_EPI_CG_UPDATE = 2 };
 
 /* Times every compiled variant of every epilogue in precision prec for g's

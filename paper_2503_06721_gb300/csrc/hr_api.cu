@@ -287,13 +287,15 @@ hr_status hop(const hr_gauge *g, int P, int out_parity, int dagger, const FieldV
 unsigned hop_variants_of(const hr_gauge *g, int P)
 {
     if (P == HR_F64 || P == HR_DF64) return 0x1u;
-    return g->D <= 4 ? 0xBu : 0xFu;   // as hop_variant_mask for the handle's pair
+    return g->D <= 4 ? 0x1Bu : 0x1Fu;   // as hop_variant_mask for the handle's pair
 }
 
 int hop_variant(const hr_gauge *g, int P, bool rebuild, int epi, int nrhs)
 {
     const unsigned mask = hop_variants_of(g, P);
-    auto compiled = [&](int v) { return v >= 0 && v < HOP_NVARIANTS && ((mask >> v) & 1u); };
+    auto compiled = [&](int v) {
+        return v >= 0 && v < HOP_NVARIANTS && ((mask >> v) & 1u) && hop_variant_fits(v, nrhs);
+    };
     if (g->force_variant >= 0) return compiled(g->force_variant) ? g->force_variant : HOP_DIRECT;
     const int t = g->tuned[P][rebuild ? 1 : 0][epi][nrhs > 1 ? 1 : 0];
     if (compiled(t)) return t;

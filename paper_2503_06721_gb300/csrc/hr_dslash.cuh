@@ -260,14 +260,18 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const HopParams prm)
 //                     or 3 (D_R <= 4) blocks of 128 threads per SM
 //   HOP_STAGED_TIGHT  the same held to 3 blocks per SM (D_R > 4 only)
 //   HOP_STAGED_LINKS  the staged kernel with the link records staged too
+//   HOP_MRHS          hop_mrhs_kernel: a block of 4 right-hand sides shares
+//                     each tile's link records (nrhs >= 2 only)
 // FP64 and DF64 have the direct kernel only: they are bound by FP64 (or
 // float-float) arithmetic, not by the memory system.
-enum { HOP_DIRECT = 0, HOP_STAGED = 1, HOP_STAGED_TIGHT = 2, HOP_STAGED_LINKS = 3, HOP_NVARIANTS = 4 };
+enum { HOP_DIRECT = 0, HOP_STAGED = 1, HOP_STAGED_TIGHT = 2, HOP_STAGED_LINKS = 3, HOP_MRHS = 4, HOP_NVARIANTS = 5 };
 // bit v set: variant v is compiled for (N, REP, P)
 __host__ __device__ constexpr unsigned hop_variant_mask(int N, int REP, int P)
 {
-    return (P == HR_F64 || P == HR_DF64) ? 0x1u : rep_dim(N, REP) <= 4 ? 0xBu : 0xFu;
+    return (P == HR_F64 || P == HR_DF64) ? 0x1u : rep_dim(N, REP) <= 4 ? 0x1Bu : 0x1Fu;
 }
+// whether variant v can serve a launch of nrhs right-hand sides
+__host__ __device__ constexpr bool hop_variant_fits(int v, int nrhs) { return v != HOP_MRHS || nrhs >= 2; }
 
 // host-side launchers, instantiated per (N, REP, P) in hr_dslash_inst.cu
 template <int N, int REP, int P>

@@ -2,7 +2,7 @@
 // kernel for one (N, representation, precision).  The build compiles this
 // file once per combination with -DHR_INST_N=<N> -DHR_INST_REP=<rep>
 // -DHR_INST_P=<prec> so the instantiations compile in parallel.
-#include "hr_dslash_staged.cuh"
+#include "hr_dslash_mrhs.cuh"
 
 namespace hr {
 
@@ -65,6 +65,23 @@ static hr_status launch_links_epi(const HopParams &prm, int epi, dim3 grid, cuda
     }
 }
 
+template <int N, int REP, int P, bool RB, int EPI>
+static hr_status launch_mrhs(const HopParams &prm, cudaStream_t stream)
+{
+    constexpr int NCH = link_nchunk(P, rep_real(REP) && !RB, RB ? N * N : rep_dim(N, REP) * rep_dim(N, REP));
+    constexpr size_t smem = MrhsShape<P, rep_dim(N, REP), EPI, NCH>::SMEM;
+    constexpr int b = (int)((size_t)227 * 1024 / (smem + 8192));
+    constexpr int MINB = b < 1 ? 1 : b > 4 ? 4 : b;
+    auto kern = hop_mrhs_kernel<N, REP, P, RB, EPI, MINB>;
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess) return cuda_fail(attr, "cudaFuncSetAttribute(hop_mrhs_kernel)");
+    const unsigned groups = (unsigned)((prm.nrhs + MRHS_WARPS - 1) / MRHS_WARPS);
+    kern<<<(unsigned)prm.g.ntiles * groups, 32 * MRHS_WARPS, smem, stream>>>(prm);
+    HR_LAUNCH_CHECK("hop_mrhs_kernel");
+    return HR_OK;
+}
+
 template <int N, int REP, int P, bool RB>
 static hr_status launch_epi(const HopParams &prm, int epi, int variant, cudaStream_t stream)
 {
@@ -94,6 +111,20 @@ static hr_status launch_epi(const HopParams &prm, int epi, int variant, cudaStre
     }
     if constexpr ((mask >> HOP_STAGED_LINKS) & 1u) {
         if (variant == HOP_STAGED_LINKS) return launch_links_epi<N, REP, P, RB>(prm, epi, grid, stream);
+    }
+    if constexpr ((mask >> HOP_MRHS) & 1u) {
+        if (variant == HOP_MRHS) {
+            if (prm.nrhs < 2) {
+                set_error("the multi-RHS hop variant needs nrhs >= 2");
+                return HR_ERR_INVALID;
+            }
+            switch (epi) {
+            case EPI_STORE: return launch_mrhs<N, REP, P, RB, EPI_STORE>(prm, stream);
+            case EPI_STORE_NORM: return launch_mrhs<N, REP, P, RB, EPI_STORE_NORM>(prm, stream);
+            case EPI_CG_UPDATE: return launch_mrhs<N, REP, P, RB, EPI_CG_UPDATE>(prm, stream);
+            default: set_error("bad epilogue %d", epi); return HR_ERR_INVALID;
+            }
+        }
     }
     if constexpr (P == HR_DF64) {
         if constexpr (!RB) hop_kernel<N, REP, P, false, EPI_STORE><<<grid, block, 0, stream>>>(prm);

@@ -2,8 +2,9 @@
 //
 // The hopping kernel exists as a direct variant (each lane loads its own
 // neighbour records) and as shared-memory-staged variants (the warp moves
-// its 32 records cooperatively) at two register budgets and with the link
-// records staged as well.  All compute the same bits.  Which is fastest
+// its 32 records cooperatively) at two register budgets, with the link
+// records staged as well, and for blocks of right-hand sides sharing each
+// loaded link.  All compute the same bits.  Which is fastest
 // depends on the representation (record sizes, registers), the precision,
 // the link mode, the epilogue and the lattice, so the choice is measured: every variant of every epilogue is
 // launched on zero-filled scratch fields of the handle's lattice, timed with
@@ -75,8 +76,10 @@ static hr_status tune_mode(hr_gauge *g, int P, int nrhs, cudaStream_t s, float *
     const int PC = P == HR_F64 ? HR_F64 : HR_F32;   // r and x of a fused CG update
     const size_t fP = align_up(field_rhs_bytes(vh, D, P) * nrhs, 256);
     const size_t fC = align_up(field_rhs_bytes(vh, D, PC) * nrhs, 256);
-    const long nblk = (vh + 127) / 128;
-    const size_t bpart = align_up(sizeof(double) * (size_t)nrhs * (nblk + 1), 256);
+    // per right-hand side: one partial per block of 128 sites, or per 32-site
+    // tile for the multi-RHS variant
+    const long ntiles = (vh + HR_TILE - 1) / HR_TILE;
+    const size_t bpart = align_up(sizeof(double) * (size_t)nrhs * (ntiles + 1), 256);
     const size_t bcnt = align_up(sizeof(unsigned) * nrhs, 256);
     const size_t bstate = align_up(sizeof(CgState) * nrhs, 256);
     const size_t bred = align_up(sizeof(double) * nrhs, 256);
@@ -139,7 +142,7 @@ static hr_status tune_mode(hr_gauge *g, int P, int nrhs, cudaStream_t s, float *
         float best = 0;
         int best_v = -1;
         for (int v = 0; v < HOP_NVARIANTS; v++) {
-            if (!((mask >> v) & 1u)) continue;
+            if (!((mask >> v) & 1u) || !hop_variant_fits(v, nrhs)) continue;
             hr_status st = launch(epi, v);   // warm-up (and first-use setup)
             if (st != HR_OK) return st;
             HR_CUDA_CHECK(cudaEventRecord(ev.a, s));
@@ -180,7 +183,7 @@ hr_status hr_tune(hr_gauge *g, hr_prec prec, int nrhs, void *stream)
 
 hr_status hr_gauge_set_tuning(hr_gauge *g, int autotune, int variant)
 {
-    if (!g || (autotune != 0 && autotune != 1) || variant < -1 || variant > HR_HOP_STAGED_LINKS) {
+    if (!g || (autotune != 0 && autotune != 1) || variant < -1 || variant > HR_HOP_MRHS) {
         set_error("hr_gauge_set_tuning: bad arguments");
         return HR_ERR_INVALID;
     }

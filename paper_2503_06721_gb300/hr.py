@@ -24,7 +24,7 @@ REPS = {"FUND": FUND, "ADJ": ADJ, "SYM": SYM, "ASYM": ASYM, "2AS": ASYM}
 F64, F32, F16, BF16, DF64 = 0, 1, 2, 3, 4
 PRECS = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16, "df64": DF64}
 EVEN, ODD, FULL, EO_PRECOND = 0, 1, 2, 3
-HOP_DIRECT, HOP_STAGED, HOP_STAGED_TIGHT, HOP_STAGED_LINKS = 0, 1, 2, 3
+HOP_DIRECT, HOP_STAGED, HOP_STAGED_TIGHT, HOP_STAGED_LINKS, HOP_MRHS = 0, 1, 2, 3, 4
 EPI_STORE, EPI_STORE_NORM, EPI_CG_UPDATE = 0, 1, 2
 LINKS_STORED, LINKS_REBUILD, LINKS_AUTO = 0, 1, 2
 

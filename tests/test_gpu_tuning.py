@@ -37,8 +37,9 @@ def _gauge(hr, N, rep, dims=DIMS, m0=-0.23, rebuild=False):
     return lat, g
 
 
-def _variants(lat):
-    return [0, 1, 3] if lat.D <= 4 else [0, 1, 2, 3]
+def _variants(lat, nrhs=1):
+    v = [0, 1, 3] if lat.D <= 4 else [0, 1, 2, 3]
+    return v + [4] if nrhs > 1 else v
 
 
 def _written_bytes(hr, lat, par, prec, y):
@@ -85,7 +86,7 @@ def test_variants_bitwise_solve(hr, N, rep, rebuild):
     nrhs = 3
     b = G.to_gpu(H.spinor(lat.volume // 2, lat.D, 8, nrhs=nrhs))
     runs = {}
-    for v in _variants(lat):
+    for v in _variants(lat, nrhs):
         g.set_tuning(autotune=False, variant=v)
         x, res, st = g.cg_solve(hr.EO_PRECOND, b, nrhs=nrhs, tol=1e-10, inner=hr.F32, inner_tol=1e-4)
         assert st == 0
@@ -103,7 +104,7 @@ def test_tune_records_a_compiled_variant(hr):
         for nrhs in (1, 4):
             g.tune(prec, nrhs=nrhs)
             for epi in (hr.EPI_STORE, hr.EPI_STORE_NORM, hr.EPI_CG_UPDATE):
-                assert g.hop_variant(prec, epi, nrhs) in _variants(lat)
+                assert g.hop_variant(prec, epi, nrhs) in _variants(lat, nrhs)
     # FP64 has the direct kernel only; tuning it is a no-op
     g.tune(hr.F64)
     assert g.hop_variant(hr.F64, hr.EPI_CG_UPDATE, 1) == hr.HOP_DIRECT
@@ -118,7 +119,7 @@ def test_tune_records_a_compiled_variant(hr):
 
 def test_tuning_arguments_checked(hr):
     lat, g = _gauge(hr, 3, "SYM")
-    for bad in ((2, -1), (1, 4), (1, -2)):
+    for bad in ((2, -1), (1, 5), (1, -2)):
         with pytest.raises(hr.HrError) as e:
             g.set_tuning(*bad)
         assert e.value.status == -1
@@ -151,3 +152,33 @@ def test_auto_link_mode(hr, oracle_mod):
     with pytest.raises(hr.HrError):
         g2.set_link_mode(hr.LINKS_AUTO)
     g2.close()
+
+
+@pytest.mark.parametrize("N,rep", [(3, "SYM"), (4, "FUND"), (3, "ADJ")])
+@pytest.mark.parametrize("prec", [1, 2], ids=["f32", "f16"])
+def test_variants_bitwise_multi_rhs_apply(hr, N, rep, prec):
+    """A block of 5 right-hand sides (one full group of 4 and a ragged group)
+    through every selector: all variants, the multi-RHS one included, give
+    the bits of the direct kernel."""
+    lat, g = _gauge(hr, N, rep)
+    nrhs = 5
+    psi = H.spinor(lat.volume, lat.D, 6, nrhs=nrhs)
+    out = {}
+    for v in _variants(lat, nrhs):
+        g.set_tuning(autotune=False, variant=v)
+        res = []
+        for par in (hr.EVEN, hr.ODD, hr.FULL, hr.EO_PRECOND):
+            in_par = hr.FULL if par == hr.FULL else hr.EVEN
+            x = G.to_gpu(psi if par == hr.FULL else psi[:, : lat.volume // 2])
+            xin = G.prec_fields(hr, lat, in_par, x, prec, nrhs)
+            for dagger in (False, True):
+                y = g.apply(par, prec, xin, nrhs=nrhs, dagger=dagger)
+                if prec == hr.F32:
+                    res.append(y.view(torch.uint8).cpu().numpy().copy())
+                else:
+                    res.append(G.back_to_f64(hr, lat, in_par, y, prec, nrhs).cpu().numpy())
+        out[v] = res
+    for v in out:
+        for a, b in zip(out[0], out[v]):
+            assert np.array_equal(a, b), v
+    g.close()
