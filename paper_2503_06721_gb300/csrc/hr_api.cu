@@ -234,6 +234,30 @@ hr_status scratch_reserve(const hr_gauge *cg, int nrhs, cudaStream_t stream, Scr
     return HR_OK;
 }
 
+hr_status pinned_reserve(const hr_gauge *cg, size_t bytes, cudaStream_t stream, char **host, char **dev)
+{
+    hr_gauge *g = const_cast<hr_gauge *>(cg);
+    if (g->pinned_bytes < bytes) {
+        if (g->pinned) {
+            HR_CUDA_CHECK(cudaStreamSynchronize(stream));
+            cudaFreeHost(g->pinned);
+            g->pinned = nullptr;
+            g->pinned_bytes = 0;
+        }
+        void *p = nullptr;
+        cudaError_t e = cudaHostAlloc(&p, bytes, cudaHostAllocMapped | cudaHostAllocPortable);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaHostAlloc");
+        memset(p, 0, bytes);
+        g->pinned = p;
+        g->pinned_bytes = bytes;
+    }
+    void *d = nullptr;
+    HR_CUDA_CHECK(cudaHostGetDevicePointer(&d, g->pinned, 0));
+    *host = static_cast<char *>(g->pinned);
+    *dev = static_cast<char *>(d);
+    return HR_OK;
+}
+
 long max_blocks_for(const hr_gauge *g)
 {
     const long V = 2 * g->geom.vh;
@@ -630,8 +654,9 @@ hr_status hr_dirac_force(const hr_gauge *g, hr_parity sys, const void *X, const 
         if (st != HR_OK) return st;
         fx = make_view(g->ws, 2 * vh, D, HR_F64);
         fy = make_view(g->ws + fb, 2 * vh, D, HR_F64);
-        HR_CUDA_CHECK(cudaMemcpyAsync(fx.data, X, vh * 4 * D * 16, cudaMemcpyDeviceToDevice, s));
-        HR_CUDA_CHECK(cudaMemcpyAsync(fy.data, Y, vh * 4 * D * 16, cudaMemcpyDeviceToDevice, s));
+        st = kernel_copy(fx.data, X, (size_t)vh * 4 * D * 16, s);
+        if (st == HR_OK) st = kernel_copy(fy.data, Y, (size_t)vh * 4 * D * 16, s);
+        if (st != HR_OK) return st;
         FieldView xe = half_view(fx, 0, vh, D, HR_F64), xo = half_view(fx, 1, vh, D, HR_F64);
         FieldView ye = half_view(fy, 0, vh, D, HR_F64), yo = half_view(fy, 1, vh, D, HR_F64);
         const hr_link_mode keep = g->mode;

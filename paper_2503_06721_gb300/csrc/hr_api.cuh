@@ -29,6 +29,9 @@ hr_status ws_reserve(const hr_gauge *g, size_t bytes, cudaStream_t stream);
 Scratch carve_scratch(char *&p, int nrhs, long max_blocks);
 size_t scratch_bytes(int nrhs, long max_blocks);
 long max_blocks_for(const hr_gauge *g);
+// the handle's host-mapped pinned buffer of at least `bytes` (grown on
+// demand): host address in *host, device address in *dev
+hr_status pinned_reserve(const hr_gauge *g, size_t bytes, cudaStream_t stream, char **host, char **dev);
 // the handle's reduction scratch for nrhs right-hand sides (grown and zeroed on demand)
 hr_status scratch_reserve(const hr_gauge *g, int nrhs, cudaStream_t stream, Scratch *out);
 

@@ -1,4 +1,7 @@
 // hr_blas.cu -- solver linear algebra kernels (see hr_blas.cuh).
+#include <algorithm>
+#include <cstdint>
+
 #include "hr_blas.cuh"
 
 namespace hr {
@@ -9,6 +12,65 @@ using Cplx = typename St<P>::R;
 // compute-type precision that holds r and x of a solve whose operator
 // fields are stored in P: F64 for P = F64, F32 otherwise
 __host__ __device__ constexpr int work_prec(int P) { return P == HR_F64 ? HR_F64 : HR_F32; }
+
+__global__ void __launch_bounds__(BLAS_THREADS) k_copy_words(unsigned *__restrict__ dst,
+                                                             const unsigned *__restrict__ src, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+__global__ void __launch_bounds__(BLAS_THREADS) k_copy_vec(uint4 *__restrict__ dst, const uint4 *__restrict__ src,
+                                                           size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+__global__ void __launch_bounds__(BLAS_THREADS) k_zero_vec(uint4 *__restrict__ dst, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = make_uint4(0, 0, 0, 0);
+}
+__global__ void __launch_bounds__(BLAS_THREADS) k_zero_words(unsigned *__restrict__ dst, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = 0;
+}
+
+static unsigned copy_grid(size_t n)
+{
+    const size_t b = (n + BLAS_THREADS - 1) / BLAS_THREADS;
+    return (unsigned)std::min<size_t>(b, 152 * 8);
+}
+
+hr_status kernel_copy(void *dst, const void *src, size_t bytes, cudaStream_t st)
+{
+    if (bytes == 0) return HR_OK;
+    const bool vec = bytes % 16 == 0 && (reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) % 16 == 0;
+    if (vec) {
+        const size_t n = bytes / 16;
+        k_copy_vec<<<copy_grid(n), BLAS_THREADS, 0, st>>>(static_cast<uint4 *>(dst), static_cast<const uint4 *>(src), n);
+    } else {
+        const size_t n = bytes / 4;
+        k_copy_words<<<copy_grid(n), BLAS_THREADS, 0, st>>>(static_cast<unsigned *>(dst),
+                                                             static_cast<const unsigned *>(src), n);
+    }
+    HR_LAUNCH_CHECK("kernel_copy");
+    return HR_OK;
+}
+
+hr_status kernel_zero(void *dst, size_t bytes, cudaStream_t st)
+{
+    if (bytes == 0) return HR_OK;
+    if (bytes % 16 == 0 && reinterpret_cast<uintptr_t>(dst) % 16 == 0) {
+        const size_t n = bytes / 16;
+        k_zero_vec<<<copy_grid(n), BLAS_THREADS, 0, st>>>(static_cast<uint4 *>(dst), n);
+    } else {
+        const size_t n = bytes / 4;
+        k_zero_words<<<copy_grid(n), BLAS_THREADS, 0, st>>>(static_cast<unsigned *>(dst), n);
+    }
+    HR_LAUNCH_CHECK("kernel_zero");
+    return HR_OK;
+}
 
 template <int D, int PD, int PS>
 __global__ void __launch_bounds__(BLAS_THREADS) k_convert(const BlasParams bp)

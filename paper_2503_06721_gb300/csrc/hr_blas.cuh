@@ -21,6 +21,14 @@ struct BlasParams {
     int cap;                  // iteration cap written into the state by init kernels
 };
 
+// Word copies and fills done by a kernel instead of the copy engines, so
+// that the solver's small host round trips (through host-mapped pinned
+// memory) and its device-side copies never queue behind bulk transfers that
+// the caller runs on other streams.  Sizes are in bytes, multiples of 4;
+// pointers 4-byte aligned (16-byte aligned for the bulk form).
+hr_status kernel_copy(void *dst, const void *src, size_t bytes, cudaStream_t st);
+hr_status kernel_zero(void *dst, size_t bytes, cudaStream_t st);
+
 // a <- convert(b) * (sv ? sv[rhs] : s)            (any precisions)
 hr_status blas_convert(int D, int Pdst, int Psrc, const BlasParams &bp, cudaStream_t st);
 // a(F64) <- b(F64) - c(F64);  reduce |a|^2, |b|^2 into state (rr, b2, stop2 = tol2*b2)

@@ -62,7 +62,22 @@ struct Inst {
     // and, for the even/odd system, D_oe x (c.t1) and (D^dag)_oe D x (t64)
     bool fused_ok;
     FieldView fx, fy;          // full fields (x, D_oe x) and (D x, (D^dag)_oe D x)
+    // host-mapped pinned mailbox for the small host round trips, moved by
+    // kernels (never by the copy engines, which the caller may keep busy):
+    // mb is the host address, mbd the device address of the same bytes
+    char *mb, *mbd;
 };
+
+// mailbox layout (bytes) for up to MAX_MB_RHS right-hand sides
+constexpr int MAX_MB_RHS = 1024;
+constexpr size_t MB_RED = 0;                                                  // [nrhs][2] double
+constexpr size_t MB_SV = MB_RED + 16 * MAX_MB_RHS;                            // [2 nrhs] double
+constexpr size_t MB_STATE = MB_SV + 16 * MAX_MB_RHS;                          // [nrhs] CgState
+constexpr size_t MB_BODIES = MB_STATE + sizeof(CgState) * MAX_MB_RHS;         // unsigned
+constexpr size_t MB_BYTES = MB_BODIES + 64;
+// the inner graph's loop-body counter sits in the first instance's reduction
+// tickets ([8 nrhs] of them), past the ones the kernels use ([0, nrhs))
+constexpr int BODIES_SLOT = 4;
 
 hr_status apply_A(const Ctx &c, int P, const FieldView &v, const FieldView &out, const FieldView &q,
                   const FieldView &t)
@@ -218,18 +233,22 @@ cudaStream_t branch_stream(int i)
 struct InnerGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    unsigned *bodies = nullptr;   // device counter
+    unsigned *bodies = nullptr;   // device counter (in the first instance's scratch)
+    unsigned *bodies_host = nullptr, *bodies_dev = nullptr;
     long long per_body = 0;       // kernels in one loop body
     ~InnerGraph()
     {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
-        if (bodies) cudaFree(bodies);
     }
 
     hr_status build(std::vector<Inst> &ins)
     {
-        HR_CUDA_CHECK(cudaMalloc(&bodies, sizeof(unsigned)));
+        // nothing here allocates or frees device memory: either would
+        // synchronise the whole device, including the caller's other streams
+        bodies = ins[0].c.sc.counters + BODIES_SLOT * ins[0].c.nrhs;
+        bodies_host = reinterpret_cast<unsigned *>(ins[0].mb + MB_BODIES);
+        bodies_dev = reinterpret_cast<unsigned *>(ins[0].mbd + MB_BODIES);
         HR_CUDA_CHECK(cudaGraphCreate(&graph, 0));
         cudaGraphConditionalHandle h;
         HR_CUDA_CHECK(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
@@ -295,26 +314,29 @@ struct InnerGraph {
 
     hr_status run(cudaStream_t s)
     {
-        HR_CUDA_CHECK(cudaMemsetAsync(bodies, 0, sizeof(unsigned), s));
+        hr_status st = kernel_zero(bodies, sizeof(unsigned), s);
+        if (st != HR_OK) return st;
         HR_CUDA_CHECK(cudaGraphLaunch(exec, s));
-        return HR_OK;
+        // the loop-body count travels to the host with the states
+        return kernel_copy(bodies_dev, bodies, sizeof(unsigned), s);
     }
     // after the stream has synchronised: count the kernels the loop ran
-    hr_status account(cudaStream_t s)
+    hr_status account()
     {
-        unsigned n = 0;
-        HR_CUDA_CHECK(cudaMemcpy(&n, bodies, sizeof(unsigned), cudaMemcpyDeviceToHost));
-        count_launch((long long)n * per_body);
+        count_launch((long long)*bodies_host * per_body);
         return HR_OK;
     }
 };
 
-hr_status read_states(const Inst &in, std::vector<CgState> &out)
+// solver states -> the instance's mailbox (read on the host after a sync)
+hr_status read_states(const Inst &in)
+{
+    return kernel_copy(in.mbd + MB_STATE, in.c.sc.state, sizeof(CgState) * in.c.nrhs, in.c.s);
+}
+void take_states(const Inst &in, std::vector<CgState> &out)
 {
     out.resize(in.c.nrhs);
-    HR_CUDA_CHECK(cudaMemcpyAsync(out.data(), in.c.sc.state, sizeof(CgState) * in.c.nrhs, cudaMemcpyDeviceToHost,
-                                  in.c.s));
-    return HR_OK;
+    memcpy(out.data(), in.mb + MB_STATE, sizeof(CgState) * in.c.nrhs);
 }
 
 // carve the instance's vectors out of its handle's workspace
@@ -347,6 +369,12 @@ hr_status prepare(Inst &in, const hr_gauge *g, hr_parity sys, const void *b, voi
     hr_status st = ws_reserve(g, need, s);
     if (st != HR_OK) return st;
     st = scratch_reserve(g, nrhs, s, &c.sc);
+    if (st != HR_OK) return st;
+    if (nrhs > MAX_MB_RHS) {
+        set_error("CG: at most %d right-hand sides per instance", MAX_MB_RHS);
+        return HR_ERR_INVALID;
+    }
+    st = pinned_reserve(g, MB_BYTES, s, &in.mb, &in.mbd);
     if (st != HR_OK) return st;
     c.sc_ns = c.sc;
     c.sc_ns.state = nullptr;
@@ -404,7 +432,7 @@ hr_status solve_all(std::vector<Inst> &ins, const hr_cg_params *prm, cudaStream_
     const double tol = prm->tol_rel;
     for (auto &in : ins)
         if (!prm->use_initial_guess)
-            HR_CUDA_CHECK(cudaMemsetAsync(in.vx.data, 0, in.vx.rhs_stride * in.c.nrhs, s));
+            if (hr_status zs = kernel_zero(in.vx.data, in.vx.rhs_stride * in.c.nrhs, s); zs != HR_OK) return zs;
     // pick the hopping-kernel variants of the inner precision before the
     // iterations are captured into a graph
     for (auto &in : ins) {
@@ -435,11 +463,15 @@ hr_status solve_all(std::vector<Inst> &ins, const hr_cg_params *prm, cudaStream_
         }
         for (size_t i = 0; i < ins.size(); i++) {
             if (ins[i].done) continue;
-            red[i].resize(2 * ins[i].c.nrhs);
-            HR_CUDA_CHECK(cudaMemcpyAsync(red[i].data(), ins[i].c.sc.red, sizeof(double) * 2 * ins[i].c.nrhs,
-                                          cudaMemcpyDeviceToHost, s));
+            st = kernel_copy(ins[i].mbd + MB_RED, ins[i].c.sc.red, sizeof(double) * 2 * ins[i].c.nrhs, s);
+            if (st != HR_OK) return st;
         }
         HR_CUDA_CHECK(cudaStreamSynchronize(s));
+        for (size_t i = 0; i < ins.size(); i++) {
+            if (ins[i].done) continue;
+            red[i].resize(2 * ins[i].c.nrhs);
+            memcpy(red[i].data(), ins[i].mb + MB_RED, sizeof(double) * 2 * ins[i].c.nrhs);
+        }
         // a float-float residual that meets the tolerance is confirmed in FP64,
         // which the instance then keeps using
         bool rerun = false;
@@ -452,12 +484,15 @@ hr_status solve_all(std::vector<Inst> &ins, const hr_cg_params *prm, cudaStream_
             in.df = false;
             st = true_residual(in, tol, cap, false);
             in.fused_ok = true;
+            if (st == HR_OK) st = kernel_copy(in.mbd + MB_RED, in.c.sc.red, sizeof(double) * 2 * in.c.nrhs, s);
             if (st != HR_OK) return st;
-            HR_CUDA_CHECK(cudaMemcpyAsync(red[i].data(), in.c.sc.red, sizeof(double) * 2 * in.c.nrhs,
-                                          cudaMemcpyDeviceToHost, s));
             rerun = true;
         }
-        if (rerun) HR_CUDA_CHECK(cudaStreamSynchronize(s));
+        if (rerun) {
+            HR_CUDA_CHECK(cudaStreamSynchronize(s));
+            for (size_t i = 0; i < ins.size(); i++)
+                if (!ins[i].done) memcpy(red[i].data(), ins[i].mb + MB_RED, sizeof(double) * 2 * ins[i].c.nrhs);
+        }
         bool any_active = false;
         double worst = 0;
         for (size_t i = 0; i < ins.size(); i++) {
@@ -502,8 +537,11 @@ hr_status solve_all(std::vector<Inst> &ins, const hr_cg_params *prm, cudaStream_
                     sv[k] = (ok || !(rr > 0) || !std::isfinite(rr)) ? 0.0 : 1.0 / std::sqrt(rr);
                     sv[c.nrhs + k] = sv[k] == 0.0 ? 0.0 : std::sqrt(rr);
                 }
-                HR_CUDA_CHECK(cudaMemcpyAsync(c.sc.sv, sv.data(), sizeof(double) * 2 * c.nrhs, cudaMemcpyHostToDevice,
-                                              s));
+                // the previous outer step's copy of the mailbox has completed
+                // (the stream was synchronised since)
+                memcpy(in.mb + MB_SV, sv.data(), sizeof(double) * 2 * c.nrhs);
+                st = kernel_copy(c.sc.sv, in.mbd + MB_SV, sizeof(double) * 2 * c.nrhs, s);
+                if (st != HR_OK) return st;
                 bp.a = in.r32;
                 bp.b = in.r64;
                 bp.c = in.x32;
@@ -522,11 +560,12 @@ hr_status solve_all(std::vector<Inst> &ins, const hr_cg_params *prm, cudaStream_
         if (st != HR_OK) return st;
         int ran = 0;
         for (size_t i = 0; i < ins.size(); i++) {
-            st = read_states(ins[i], stt[i]);
+            st = read_states(ins[i]);
             if (st != HR_OK) return st;
         }
         HR_CUDA_CHECK(cudaStreamSynchronize(s));
-        st = ig.account(s);
+        for (size_t i = 0; i < ins.size(); i++) take_states(ins[i], stt[i]);
+        st = ig.account();
         if (st != HR_OK) return st;
         for (size_t i = 0; i < ins.size(); i++) {
             Inst &in = ins[i];
@@ -647,10 +686,10 @@ extern "C" hr_status hr_cg_solve_force(const hr_gauge *g, hr_parity sys, const v
         if (st != HR_OK) return st;
     }
     const size_t fb = field_rhs_bytes(c.ns, c.D, HR_F64);
-    if (Y) HR_CUDA_CHECK(cudaMemcpyAsync(Y, in.q64.data, fb, cudaMemcpyDeviceToDevice, s));
+    if (Y && (st = kernel_copy(Y, in.q64.data, fb, s)) != HR_OK) return st;
     if (sys == HR_FULL) return force_full(g, in.vx, in.q64, coeff, reinterpret_cast<double *>(F), s);
     // even/odd: minus the full-operator force on X' = (x, D_oe x), Y' = (Dhat x, (D^dag)_oe Dhat x)
-    HR_CUDA_CHECK(cudaMemcpyAsync(in.fx.data, x, fb, cudaMemcpyDeviceToDevice, s));
+    if ((st = kernel_copy(in.fx.data, x, fb, s)) != HR_OK) return st;
     return force_full(g, in.fx, in.fy, -coeff, reinterpret_cast<double *>(F), s);
 }
 

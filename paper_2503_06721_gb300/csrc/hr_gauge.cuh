@@ -28,7 +28,7 @@ struct hr_gauge {
     char *scr;
     size_t scr_bytes;
     int *err;             // device flag set by a bounded wait that gave up
-    void *pinned;         // host staging for solver state (pinned)
+    void *pinned;         // host-mapped pinned mailbox for the solver's small host transfers
     size_t pinned_bytes;
     int device;
     // hopping-kernel variant per [precision][rebuilt links][epilogue][nrhs > 1]
