@@ -433,7 +433,7 @@ def batched_compare(hr, synth, dev, stream, rep="ASYM"):
         lat = hr.Lattice(wl.N, rep, dims, wl.bc, m0)
         V = lat.volume
         gauges.append(hr.Gauge(lat, synth.random_links(V, wl.N, wl.eps, wl.seed + i, device=dev),
-                               precs=("f64", "f32")))
+                               precs=("f64", "f32", "df64")))
         if n == 12:
             b = torch.zeros((12, V // 2, 4, lat.D), dtype=torch.complex128, device=dev)
             for s in range(4):
@@ -448,13 +448,16 @@ def batched_compare(hr, synth, dev, stream, rep="ASYM"):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = {"workload": f"SU(4) {rep} 24^3x48 (12 point sources) + 8^4, 12^4, 16^3x32 (4 rhs each)",
            "rhs_total": sum(nr)}
-    for name, inner in (("batched_mixed_fp32", hr.F32), ("batched_fp64", hr.F64)):
+    for name, inner, resid in (("batched_mixed_fp32", hr.F32, hr.F64), ("batched_mixed_fp32_df64res", hr.F32, hr.DF64),
+                               ("batched_fp64", hr.F64, hr.F64)):
         xs = [torch.zeros_like(b) for b in bs]
-        hr.cg_solve_batched(gauges, hr.EO_PRECOND, bs, xs, nr, tol=1e-3, inner=inner, check=False)
+        hr.cg_solve_batched(gauges, hr.EO_PRECOND, bs, xs, nr, tol=1e-3, inner=inner, residual=resid,
+                            check=False)
         xs = [torch.zeros_like(b) for b in bs]
         torch.cuda.synchronize()
         e0.record(stream)
-        res, st = hr.cg_solve_batched(gauges, hr.EO_PRECOND, bs, xs, nr, tol=TOL, inner=inner, check=False)
+        res, st = hr.cg_solve_batched(gauges, hr.EO_PRECOND, bs, xs, nr, tol=TOL, inner=inner, residual=resid,
+                                      check=False)
         e1.record(stream)
         torch.cuda.synchronize()
         out[name] = {"ms": round(e0.elapsed_time(e1), 2), "status": hr.STATUS.get(st, st),
@@ -475,6 +478,8 @@ def batched_compare(hr, synth, dev, stream, rep="ASYM"):
                               "total_iters": its}
     out["speedup_batched_mixed_vs_sequential_fp64"] = round(
         out["sequential_fp64"]["ms"] / out["batched_mixed_fp32"]["ms"], 2)
+    out["speedup_batched_mixed_df64res_vs_sequential_fp64"] = round(
+        out["sequential_fp64"]["ms"] / out["batched_mixed_fp32_df64res"]["ms"], 2)
     for g in gauges:
         g.close()
     return out

@@ -243,9 +243,12 @@ typedef struct {
     hr_prec residual;     /* arithmetic of the defect-correction true residuals
                              (inner != HR_F64 only): HR_F64 (0, the default) or
                              HR_DF64, float-float with the handle's DF64 links,
-                             which must be stored.  With HR_DF64 a residual that
-                             meets tol_rel is confirmed once in FP64, so the
-                             reported true_rel_residual is always the FP64 one. */
+                             which must be stored.  With HR_DF64 the
+                             intermediate residuals are float-float; the one
+                             the last inner solve is expected to bring within
+                             tol_rel, and any float-float one that meets it,
+                             are formed in FP64, so the reported
+                             true_rel_residual is always an FP64 one. */
 } hr_cg_params;
 
 typedef struct {

@@ -57,7 +57,9 @@ struct Inst {
     hr_cg_result *res;
     std::vector<int> iters;
     bool done;
-    bool df;                   // true residuals in float-float (until one meets the tolerance)
+    bool df_ok;                // float-float true residuals requested (and DF64 links held)
+    bool df;                   // the current true residual is formed in float-float
+    double pred_rel;           // expected true residual after the running inner solve
     // fused force: the last FP64 true residual of the final x leaves D x (q64)
     // and, for the even/odd system, D_oe x (c.t1) and (D^dag)_oe D x (t64)
     bool fused_ok;
@@ -413,7 +415,9 @@ hr_status prepare(Inst &in, const hr_gauge *g, hr_parity sys, const void *b, voi
     in.res = res;
     in.iters.assign(nrhs, 0);
     in.done = false;
-    in.df = mixed && Pres == HR_DF64;
+    in.df_ok = mixed && Pres == HR_DF64;
+    in.df = false;
+    in.pred_rel = 1.0;
     for (int k = 0; k < nrhs; k++) {
         res[k].iters = 0;
         res[k].outer_iters = 0;
@@ -457,6 +461,9 @@ hr_status solve_all(std::vector<Inst> &ins, const hr_cg_params *prm, cudaStream_
         for (auto &in : ins) {
             if (in.done) continue;
             const bool x_zero = outer == 0 && !prm->use_initial_guess;
+            // float-float for the intermediate residuals; FP64 for the one the
+            // last inner solve is expected to bring to the tolerance
+            in.df = in.df_ok && !(in.pred_rel <= 4.0 * tol);
             st = true_residual(in, tol, cap, x_zero);
             if (st != HR_OK) return st;
             in.fused_ok = !x_zero && !in.df;
@@ -472,8 +479,7 @@ hr_status solve_all(std::vector<Inst> &ins, const hr_cg_params *prm, cudaStream_
             red[i].resize(2 * ins[i].c.nrhs);
             memcpy(red[i].data(), ins[i].mb + MB_RED, sizeof(double) * 2 * ins[i].c.nrhs);
         }
-        // a float-float residual that meets the tolerance is confirmed in FP64,
-        // which the instance then keeps using
+        // a float-float residual that meets the tolerance is confirmed in FP64
         bool rerun = false;
         for (size_t i = 0; i < ins.size(); i++) {
             Inst &in = ins[i];
@@ -531,6 +537,11 @@ hr_status solve_all(std::vector<Inst> &ins, const hr_cg_params *prm, cudaStream_
                 st = blas_convert(c.D, HR_F64, HR_F64, bp, s);
             } else {
                 std::vector<double> sv(2 * c.nrhs);
+                in.pred_rel = 0.0;
+                for (int k = 0; k < c.nrhs; k++) {
+                    const double rel_k = in.res[k].true_rel_residual;
+                    if (!(rel_k <= tol)) in.pred_rel = std::max(in.pred_rel, rel_k * itol);
+                }
                 for (int k = 0; k < c.nrhs; k++) {
                     const double rr = red[i][2 * k];
                     const bool ok = in.res[k].true_rel_residual <= tol;

@@ -251,6 +251,118 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const HopParams prm)
     }
 }
 
+// The float-float (DF64) hop, for stored links and a plain store.  Each df
+// product-sum takes about 15 FP32 instructions, so with the 8 hops unrolled
+// as in hop_kernel the code no longer fits the instruction caches (ncu: most
+// issue slots stall on "no instruction").  Here the hop loop stays rolled:
+// one hop body serves all 8 directions, with the direction-dependent spin
+// permutation and phases chosen at run time (uniform across the warp).
+template <int N, int REP>
+__global__ void __launch_bounds__(128) hop_df64_kernel(const HopParams prm)
+{
+    using S = St<HR_DF64>;
+    using R = typename S::R;
+    constexpr int D = rep_dim(N, REP);
+    constexpr bool REAL = rep_real(REP);
+    using SIO = SpinorIO<HR_DF64, D>;
+    using LIO = LinkIO<HR_DF64, REAL, D * D>;
+
+    const Geom &g = prm.g;
+    const int rhs = prm.rhs_inner ? (int)(blockIdx.x % prm.nrhs) : (int)blockIdx.y;
+    const int bx = prm.rhs_inner ? (int)(blockIdx.x / prm.nrhs) : (int)blockIdx.x;
+    const long i = (long)bx * blockDim.x + threadIdx.x;
+    if (i >= g.vh) return;
+    const R sg = prm.dagger ? (R)-1 : (R)1;
+    cx<R> acc[4][D];
+#pragma unroll
+    for (int s = 0; s < 4; s++)
+#pragma unroll
+        for (int c = 0; c < D; c++) acc[s][c] = {0, 0};
+    const Site st = site_of(g, i, prm.out_parity);
+    const long tile = i / HR_TILE;
+    const int lane = (int)(i % HR_TILE);
+#pragma unroll 1
+    for (int k = 0; k < 8; k++) {
+        const int mu = k & 3;
+        const bool fwd = k < 4;
+        const long nb = neighbour(g, st, mu, fwd ? +1 : -1);
+        const R sp = fwd ? -sg : sg;
+        // lower spin component paired with upper r: 2 + r, or 3 - r for mu = 1, 2
+        const bool swap = mu == 1 || mu == 2;
+        const int ph0 = ephase(mu, 0), ph1 = ephase(mu, 1);
+        cx<R> psi[4][D];
+        SIO::load(prm.in, rhs, nb, psi);
+        cx<R> h[2][D];
+#pragma unroll
+        for (int c = 0; c < D; c++) {
+            const cx<R> dn0 = swap ? psi[3][c] : psi[2][c];
+            const cx<R> dn1 = swap ? psi[2][c] : psi[3][c];
+            h[0][c] = psi[0][c] + sp * ipow(ph0, dn0);
+            h[1][c] = psi[1][c] + sp * ipow(ph1, dn1);
+        }
+        const uint4 *lp = LIO::slot_ptr(prm.links, tile, k, lane);
+        cx<R> chi[2][D];
+        if constexpr (REAL) {
+            R W[D * D];
+            LIO::load(lp, W);
+#pragma unroll
+            for (int row = 0; row < D; row++) {
+                cx<R> s0 = {0, 0}, s1 = {0, 0};
+#pragma unroll
+                for (int col = 0; col < D; col++) {
+                    rmac(s0, W[row * D + col], h[0][col]);
+                    rmac(s1, W[row * D + col], h[1][col]);
+                }
+                chi[0][row] = s0;
+                chi[1][row] = s1;
+            }
+        } else {
+            cx<R> W[D * D];
+            LIO::load(lp, W);
+#pragma unroll
+            for (int row = 0; row < D; row++) {
+                cx<R> s0 = {0, 0}, s1 = {0, 0};
+#pragma unroll
+                for (int col = 0; col < D; col++) {
+                    cmac(s0, W[row * D + col], h[0][col]);
+                    cmac(s1, W[row * D + col], h[1][col]);
+                }
+                chi[0][row] = s0;
+                chi[1][row] = s1;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < D; c++) {
+            acc[0][c] = acc[0][c] + chi[0][c];
+            acc[1][c] = acc[1][c] + chi[1][c];
+            const cx<R> t0 = sp * ipow(4 - ph0, chi[0][c]);
+            const cx<R> t1 = sp * ipow(4 - ph1, chi[1][c]);
+            if (swap) {
+                acc[3][c] = acc[3][c] + t0;
+                acc[2][c] = acc[2][c] + t1;
+            } else {
+                acc[2][c] = acc[2][c] + t0;
+                acc[3][c] = acc[3][c] + t1;
+            }
+        }
+    }
+    const R a = (R)prm.a, b = (R)prm.b;
+    if (prm.diag.data) {
+        cx<R> d[4][D];
+        SIO::load(prm.diag, rhs, i, d);
+#pragma unroll
+        for (int s = 0; s < 4; s++)
+#pragma unroll
+            for (int c = 0; c < D; c++) acc[s][c] = axpby(a, acc[s][c], b, d[s][c]);
+    } else {
+#pragma unroll
+        for (int s = 0; s < 4; s++)
+#pragma unroll
+            for (int c = 0; c < D; c++) acc[s][c] = a * acc[s][c];
+    }
+    SIO::store(prm.out, rhs, i, acc);
+}
+
 // Kernel variants of one hopping launch.  Every variant computes the same
 // bits; which one is fastest depends on N, R, precision, link mode, epilogue,
 // lattice and right-hand-side count, and the autotuner picks among them.

@@ -127,7 +127,7 @@ static hr_status launch_epi(const HopParams &prm, int epi, int variant, cudaStre
         }
     }
     if constexpr (P == HR_DF64) {
-        if constexpr (!RB) hop_kernel<N, REP, P, false, EPI_STORE><<<grid, block, 0, stream>>>(prm);
+        if constexpr (!RB) hop_df64_kernel<N, REP><<<grid, block, 0, stream>>>(prm);
     } else {
         switch (epi) {
         case EPI_STORE: hop_kernel<N, REP, P, RB, EPI_STORE><<<grid, block, 0, stream>>>(prm); break;
@@ -136,7 +136,7 @@ static hr_status launch_epi(const HopParams &prm, int epi, int variant, cudaStre
         default: set_error("bad epilogue %d", epi); return HR_ERR_INVALID;
         }
     }
-    HR_LAUNCH_CHECK("hop_kernel");
+    HR_LAUNCH_CHECK(P == HR_DF64 ? "hop_df64_kernel" : "hop_kernel");
     return HR_OK;
 }
 
