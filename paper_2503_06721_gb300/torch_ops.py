@@ -11,6 +11,7 @@ hand-written:
   x = A^{-1} b, A = D^dag D  lam = A^{-1} g (a second solve, no stored iterations)
                             grad_b = lam,             grad_omega = 1/2 [F(lam, Dx) + F(x, D lam)]
   S = <phi, A^{-1} phi>     grad_phi = 2 A^{-1} phi,  grad_omega = F(X, D X), X = A^{-1} phi
+                            (computed with the solve, hr_cg_solve_force)
 
 where F(X, Y) = d/de [-2 Re <Y, D X>] (hr_dirac_force) and D is D_m for the
 FULL system or Dhat for the even/odd one.  Complex gradients follow PyTorch's
@@ -80,8 +81,15 @@ class _ActionFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, phi, omega, gauge, sys, tol, inner):
         _check_zero(omega)
-        X, res, st = gauge.cg_solve(sys, phi.contiguous(), tol=tol, inner=inner)
         ctx.gauge, ctx.sys = gauge, sys
+        F = None
+        if ctx.needs_input_grad[1]:
+            # the force needs D X and its neighbours, which the solve's final
+            # true residual already applied: solve and force in one call
+            X, F, _, res, st = gauge.cg_solve_force(sys, phi.contiguous(), tol=tol, inner=inner, coeff=1.0)
+        else:
+            X, res, st = gauge.cg_solve(sys, phi.contiguous(), tol=tol, inner=inner)
+        ctx.force = F
         ctx.save_for_backward(X)
         S = torch.vdot(phi.reshape(-1), X.reshape(-1)).real
         return S
@@ -89,11 +97,8 @@ class _ActionFn(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gS):
         (X,) = ctx.saved_tensors
-        gauge, sys = ctx.gauge, ctx.sys
         grad_phi = 2.0 * gS * X if ctx.needs_input_grad[0] else None
-        grad_omega = None
-        if ctx.needs_input_grad[1]:
-            grad_omega = gauge.force(sys, X, _D(gauge, sys, X), coeff=1.0) * gS
+        grad_omega = ctx.force * gS if ctx.needs_input_grad[1] else None
         return grad_phi, grad_omega, None, None, None, None
 
 
