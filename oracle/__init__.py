@@ -95,6 +95,7 @@ def _load():
             "or_sum_double_double": (D, [P, ctypes.c_long]),
             "or_norm2": (D, [P, ctypes.c_long]),
             "or_cg": (I, [LP, P, I, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]),
+            "or_cg_shifted": (I, [LP, P, I, D, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]),
             "or_force": (None, [LP, P, P, P, P]),
             "or_num_threads": (I, []),
             "or_hop_sites": (None, [LP, P, I, P, P, ctypes.c_long, P, I]),
@@ -252,16 +253,27 @@ def norm2(a) -> float:
     return _load().or_norm2(_p(a), a.size)
 
 
-def cg(L: Lat, UR, sys: int, b, x0=None, tol: float = 1e-10, max_iter: int = 10000):
-    """CG on A x = b with A = D^dag D (sys 0, full fields) or Dhat^dag Dhat (sys 1,
-    even half fields).  Returns (x, converged, iterations, true relative residual)."""
+def cg(L: Lat, UR, sys: int, b, x0=None, tol: float = 1e-10, max_iter: int = 10000,
+       sigma: float = 0.0):
+    """CG on (A + sigma) x = b with A = D^dag D (sys 0, full fields) or Dhat^dag Dhat
+    (sys 1, even half fields).  Returns (x, converged, iterations, true relative
+    residual)."""
     UR, b = _c(UR), _c(b)
     x = np.zeros_like(b) if x0 is None else _c(x0).copy()
     it = ctypes.c_int(0)
     rr = ctypes.c_double(0.0)
-    rc = _load().or_cg(ctypes.byref(L), _p(UR), int(sys), _p(b), _p(x), float(tol),
-                       int(max_iter), ctypes.byref(it), ctypes.byref(rr))
+    rc = _load().or_cg_shifted(ctypes.byref(L), _p(UR), int(sys), float(sigma), _p(b), _p(x),
+                               float(tol), int(max_iter), ctypes.byref(it), ctypes.byref(rr))
     return x, rc == 0, it.value, rr.value
+
+
+def cg_multishift(L: Lat, UR, sys: int, b, shifts, tol: float = 1e-10, max_iter: int = 10000):
+    """The multi-shift inversion of the RHMC (Sec. 4.3.2) by its definition: one
+    shifted CG solve (A + sigma_k) x_k = b per shift.  Returns (x[nshift, ...],
+    converged[nshift], iterations[nshift], true relative residuals[nshift])."""
+    out = [cg(L, UR, sys, b, tol=tol, max_iter=max_iter, sigma=s) for s in shifts]
+    return (np.stack([o[0] for o in out]), [o[1] for o in out], [o[2] for o in out],
+            [o[3] for o in out])
 
 
 def force(L: Lat, UR, X, Y) -> np.ndarray:

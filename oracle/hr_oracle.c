@@ -590,9 +590,12 @@ double or_norm2(const orc *u, long n)
 /* ------------------------------------------------------------------ */
 /* Sec. 4.1.2: conjugate gradient on the normal equations                */
 /* ------------------------------------------------------------------ */
-static void apply_normal(const or_lat *L, const orc *UR, int sys,
+/* out = (A + sigma) in with A = D^dag D (sys 0) or Dhat^dag Dhat (sys 1) */
+static void apply_normal(const or_lat *L, const orc *UR, int sys, double sigma,
                          const orc *in, orc *out, orc *tmp)
 {
+    long V = or_volume(L);
+    long n = (sys == 0 ? V : V / 2) * 4L * or_rep_dim(L->N, L->rep);
     if (sys == 0) {
         or_dirac_full(L, UR, in, tmp, 0);
         or_dirac_full(L, UR, tmp, out, 1);
@@ -600,10 +603,20 @@ static void apply_normal(const or_lat *L, const orc *UR, int sys,
         or_dhat(L, UR, in, tmp, 0);
         or_dhat(L, UR, tmp, out, 1);
     }
+    if (sigma != 0)
+        for (long i = 0; i < n; i++) out[i] += sigma * in[i];
 }
 
 int or_cg(const or_lat *L, const orc *UR, int sys, const orc *b, orc *x,
           double tol, int max_iter, int *iters, double *true_rel_res)
+{
+    return or_cg_shifted(L, UR, sys, 0.0, b, x, tol, max_iter, iters,
+                         true_rel_res);
+}
+
+int or_cg_shifted(const or_lat *L, const orc *UR, int sys, double sigma,
+                  const orc *b, orc *x, double tol, int max_iter, int *iters,
+                  double *true_rel_res)
 {
     long V = or_volume(L);
     int D = or_rep_dim(L->N, L->rep);
@@ -622,14 +635,14 @@ int or_cg(const or_lat *L, const orc *UR, int sys, const orc *b, orc *x,
     }
     while (!done) {
         /* (re)start from the true residual r = b - A x */
-        apply_normal(L, UR, sys, x, Ap, tmp);
+        apply_normal(L, UR, sys, sigma, x, Ap, tmp);
         for (long i = 0; i < n; i++) r[i] = b[i] - Ap[i];
         rel = sqrt(or_norm2(r, n)) / bnorm;
         if (rel <= tol || k >= max_iter) break;
         memcpy(p, r, n * sizeof(orc));
         double rr = or_norm2(r, n);
         while (k < max_iter) {
-            apply_normal(L, UR, sys, p, Ap, tmp);
+            apply_normal(L, UR, sys, sigma, p, Ap, tmp);
             double pAp = creal(or_dot(p, Ap, n));
             double alpha = rr / pAp;
             for (long i = 0; i < n; i++) {
@@ -644,7 +657,7 @@ int or_cg(const or_lat *L, const orc *UR, int sys, const orc *b, orc *x,
             rr = rr_new;
         }
         if (k >= max_iter) {
-            apply_normal(L, UR, sys, x, Ap, tmp);
+            apply_normal(L, UR, sys, sigma, x, Ap, tmp);
             for (long i = 0; i < n; i++) r[i] = b[i] - Ap[i];
             rel = sqrt(or_norm2(r, n)) / bnorm;
             done = 1;

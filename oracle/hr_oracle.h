@@ -116,6 +116,14 @@ double or_norm2(const orc *u, long n);
  * Returns 0 on convergence, 1 otherwise. */
 int or_cg(const or_lat *L, const orc *UR, int sys, const orc *b, orc *x,
           double tol, int max_iter, int *iters, double *true_rel_res);
+/* The same textbook CG on the shifted system (A + sigma) x = b, sigma >= 0.
+ * The multi-shift inversion of the RHMC (Sec. 4.3.2) solves
+ * (Q^2 + beta_k) x_k = phi for every pole beta_k of the rational
+ * approximation; its definition is one such solve per shift, which is what
+ * this function provides (sigma = 0 is or_cg). */
+int or_cg_shifted(const or_lat *L, const orc *UR, int sys, double sigma,
+                  const orc *b, orc *x, double tol, int max_iter, int *iters,
+                  double *true_rel_res);
 
 /* ---- fermion force (Sec. 2.5, HMC) ----
  * F[x][mu][a] = d/de  S(U_F(x,mu) -> exp(i e T^a) U_F(x,mu)) at e = 0 for
