@@ -345,6 +345,7 @@ def run_ours(args, rank, world, local_rank):
 
     # time to 1e-10: plain FP64 CG vs defect correction with low-precision inner solves
     cg = None
+    multishift = None
     if rank == 0 and not args.no_cg_compare:
         g2 = hr.Gauge(lat, U, precs=("f64", "f32", "f16", "bf16", "df64"), stored=True, rebuild=True)
         g2.set_link_mode(hr.LINKS_AUTO)
@@ -368,6 +369,8 @@ def run_ours(args, rank, world, local_rank):
                         "status": r[0]["status"]}
         for name, _, _ in cg_variants[1:]:
             cg[name]["speedup_vs_fp64"] = round(cg["fp64"]["ms"] / cg[name]["ms"], 2)
+        if not args.no_multishift:
+            multishift = multishift_compare(hr, g2, phi, stream)
         g2.close()
 
     batched = None
@@ -410,6 +413,7 @@ def run_ours(args, rank, world, local_rank):
             "e2e": e2e,
             "cg": cg,
             "batched": batched,
+            "multishift": multishift,
             "cpu_baseline": cpu,
         }
         print(json.dumps(out), flush=True)
@@ -417,6 +421,49 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+    return out
+
+
+# the poles of an RHMC rational approximation span the operator's spectrum;
+# eight geometrically spaced shifts from 1e-3 to 10 stand in for them
+MS_SHIFTS = [10.0 ** (-3 + 4 * k / 7) for k in range(8)]
+
+
+def multishift_compare(hr, g, phi, stream):
+    """(A + sigma_k) x_k = phi for the 8 shifts, A = Dhat^dag Dhat of the bench
+    lattice, to a true residual of 1e-10 each: multi-shift CG in FP64 and
+    with FP32 iterations + FP64 correction, against plain FP64 shifted CG
+    solving one shift after another (the definition of the multi-shift
+    inversion)."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"shifts": [float(f"{s:.6g}") for s in MS_SHIFTS]}
+    for name, inner in (("multishift_fp64", hr.F64), ("multishift_mixed_fp32", hr.F32)):
+        g.cg_solve_multishift(hr.EO_PRECOND, phi, MS_SHIFTS, tol=1e-3, inner=inner, check=False)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        x, res, st = g.cg_solve_multishift(hr.EO_PRECOND, phi, MS_SHIFTS, tol=TOL, inner=inner,
+                                           inner_tol=1e-5, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"ms": round(e0.elapsed_time(e1), 2), "status": hr.STATUS.get(st, st),
+                     "iters": [r[0]["iters"] for r in res],
+                     "outer": [r[0]["outer_iters"] for r in res],
+                     "max_true_rel_residual": max(r[0]["true_rel_residual"] for r in res)}
+        del x
+    torch.cuda.synchronize()
+    e0.record(stream)
+    worst, its = 0.0, []
+    for s in MS_SHIFTS:
+        x, res, st = g.cg_solve_multishift(hr.EO_PRECOND, phi, [s], tol=TOL, inner=hr.F64, check=False)
+        worst = max(worst, res[0][0]["true_rel_residual"])
+        its.append(res[0][0]["iters"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["sequential_fp64"] = {"ms": round(e0.elapsed_time(e1), 2), "iters": its,
+                              "max_true_rel_residual": worst}
+    for name in ("multishift_fp64", "multishift_mixed_fp32"):
+        out[f"speedup_{name}_vs_sequential_fp64"] = round(out["sequential_fp64"]["ms"] / out[name]["ms"], 2)
     return out
 
 
@@ -660,6 +707,8 @@ def main():
     ap.add_argument("--no-cg-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-FP64 solve comparison")
+    ap.add_argument("--no-multishift", action="store_true",
+                    help="skip the multi-shift-vs-sequential shifted solve comparison")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--mode", choices=["step", "deo", "force"], default="step",
                     help="deo: only D_eo applications; force: only the fermion force (profiler captures)")

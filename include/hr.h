@@ -297,6 +297,37 @@ hr_status hr_cg_solve_force(const hr_gauge *g, hr_parity sys, const void *b,
                             hr_cg_result *res, void *Y, double coeff,
                             void *F, void *stream);
 
+/* Multi-shift CG (Sec. 4.1.2, Supported Inverters; Sec. 4.3.2, the RHMC's
+ * (Q^2 + beta_k)^{-1} phi for every pole beta_k): solves
+ *     (A + shifts[k]) x_k = b        for k = 0 .. nshift-1
+ * with A = D_m^dag D_m (sys = HR_FULL, FULL fields) or Dhat^dag Dhat
+ * (HR_EO_PRECOND, even half fields), all shifts in one Krylov space.
+ *   b       DEVICE, FP64 fields of nrhs right-hand sides [nrhs][sites][4][D]
+ *   x       DEVICE, FP64 output [nshift][nrhs][sites][4][D] (shift-major);
+ *           overwritten, must not overlap b
+ *   shifts  HOST array of nshift finite values >= 0, in any order (the
+ *           smallest is the base system); 1 <= nshift <= 64,
+ *           nrhs * nshift <= 4096
+ *   params  tol_rel: every shift stops at |b - (A + shifts[k]) x_k| / |b|
+ *           <= tol_rel, recomputed in FP64.  inner = HR_F64: FP64
+ *           iterations; HR_F32: FP32 iterations to max(inner_tol, tol_rel),
+ *           then FP64 defect correction of each shift by single-shift FP32
+ *           solves of all unconverged shifts together.  max_iter bounds the
+ *           multi-shift iterations and, separately, the correction
+ *           iterations.  use_initial_guess must be 0 and residual HR_F64.
+ *   res     HOST array [nshift][nrhs]: iters = iterations until the shift
+ *           met its tolerance plus its correction iterations; outer_iters =
+ *           corrections; true_rel_residual in FP64; status.
+ * The handle needs FP64 links and those of the inner precision.  BLOCKS
+ * until every shift has converged or failed.
+ * Errors: HR_ERR_NOT_CONVERGED, HR_ERR_NONFINITE (a non-positive or
+ * non-finite reduction), HR_ERR_INVALID, HR_ERR_NOMEM, HR_ERR_CUDA. */
+hr_status hr_cg_solve_multishift(const hr_gauge *g, hr_parity sys,
+                                 const void *b, void *x, int nrhs,
+                                 const double *shifts, int nshift,
+                                 const hr_cg_params *params,
+                                 hr_cg_result *res, void *stream);
+
 /* ------------------------------------------------------------------ */
 /* Fermion force (Sec. 2.5)                                              */
 /* ------------------------------------------------------------------ */

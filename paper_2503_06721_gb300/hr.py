@@ -37,7 +37,8 @@ EXPORTS = ["hr_represent_gauge", "hr_gauge_update", "hr_gauge_set_link_mode", "h
            "hr_tune", "hr_gauge_set_tuning", "hr_gauge_hop_variant", "hr_gauge_link_mode",
            "hr_field_bytes", "hr_field_convert", "hr_field_dot", "hr_field_dot_static",
            "hr_dirac_apply", "hr_dirac_dagger",
-           "hr_cg_solve", "hr_cg_solve_batched", "hr_cg_solve_force", "hr_dirac_force", "hr_rep_dim", "hr_generators",
+           "hr_cg_solve", "hr_cg_solve_batched", "hr_cg_solve_force", "hr_cg_solve_multishift",
+           "hr_dirac_force", "hr_rep_dim", "hr_generators",
            "hr_status_string", "hr_last_error", "hr_launch_count"]
 
 
@@ -100,6 +101,8 @@ def load():
                                     ctypes.POINTER(I), ctypes.POINTER(CgParams),
                                     ctypes.POINTER(CgResult), P]),
         "hr_dirac_force": (I, [P, I, P, P, D, P, P]),
+        "hr_cg_solve_multishift": (I, [P, I, P, P, I, ctypes.POINTER(D), I, ctypes.POINTER(CgParams),
+                                       ctypes.POINTER(CgResult), P]),
         "hr_cg_solve_force": (I, [P, I, P, P, ctypes.POINTER(CgParams), ctypes.POINTER(CgResult), P, D, P, P]),
         "hr_rep_dim": (I, [I, I]),
         "hr_generators": (I, [I, ctypes.POINTER(D)]),
@@ -314,6 +317,26 @@ class Gauge:
         out = [dict(iters=r.iters, outer_iters=r.outer_iters, true_rel_residual=r.true_rel_residual,
                     status=STATUS.get(r.status, r.status)) for r in res]
         return x, F, Y, out, st
+
+    def cg_solve_multishift(self, sys: int, b, shifts, x=None, nrhs: int = 1, tol: float = 1e-10,
+                            max_iter: int = 10000, inner: int = F64, inner_tol: float = 1e-5,
+                            stream=None, check: bool = True):
+        """x[k] = (A + shifts[k])^-1 b for every shift (hr_cg_solve_multishift).
+        x has shape (nshift,) + b.shape; the results are [nshift][nrhs]."""
+        shifts = [float(s) for s in shifts]
+        ns = len(shifts)
+        if x is None:
+            x = torch.empty((ns,) + tuple(b.shape), dtype=b.dtype, device=b.device)
+        p = CgParams(tol, max_iter, inner, inner_tol, 0, F64)
+        res = (CgResult * (ns * nrhs))()
+        sh = (ctypes.c_double * ns)(*shifts)
+        st = load().hr_cg_solve_multishift(self.handle, sys, _ptr(b), _ptr(x), nrhs, sh, ns,
+                                           ctypes.byref(p), res, _stream(stream))
+        if check:
+            _check(st)
+        out = [dict(iters=r.iters, outer_iters=r.outer_iters, true_rel_residual=r.true_rel_residual,
+                    status=STATUS.get(r.status, r.status)) for r in res]
+        return x, [out[k * nrhs:(k + 1) * nrhs] for k in range(ns)], st
 
     def force(self, sys: int, X, Y, coeff: float = 1.0, F=None, stream=None):
         if F is None:
