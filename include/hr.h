@@ -328,6 +328,18 @@ hr_status hr_cg_solve_multishift(const hr_gauge *g, hr_parity sys,
                                  const hr_cg_params *params,
                                  hr_cg_result *res, void *stream);
 
+/* y = a0 b + sum_k a[k] x_k over FP64 fields of parity par: with the
+ * multi-shift solutions x_k = (A + b_k)^{-1} b this is the RHMC's rational
+ * function r(A) b = a0 b + sum_k a_k (A + b_k)^{-1} b (Sec. 4.3.2).
+ *   b, y  DEVICE [nrhs][sites][4][D]; y may be b, must not overlap x
+ *   x     DEVICE [nterms][nrhs][sites][4][D] (hr_cg_solve_multishift's layout)
+ *   a     HOST array of nterms doubles; 0 <= nterms <= 64
+ * Asynchronous on stream. */
+hr_status hr_field_lincomb(const hr_lattice_desc *lat, hr_parity par,
+                           double a0, const void *b, int nterms,
+                           const double *a, const void *x, void *y, int nrhs,
+                           void *stream);
+
 /* ------------------------------------------------------------------ */
 /* Fermion force (Sec. 2.5)                                              */
 /* ------------------------------------------------------------------ */

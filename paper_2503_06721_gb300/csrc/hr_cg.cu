@@ -319,8 +319,10 @@ struct InnerGraph {
         hr_status st = kernel_zero(bodies, sizeof(unsigned), s);
         if (st != HR_OK) return st;
         HR_CUDA_CHECK(cudaGraphLaunch(exec, s));
-        // the loop-body count travels to the host with the states
-        return kernel_copy(bodies_dev, bodies, sizeof(unsigned), s);
+        // the loop-body count travels to the host with the states; the slot
+        // is a reduction ticket of other launches, so it goes back to zero
+        st = kernel_copy(bodies_dev, bodies, sizeof(unsigned), s);
+        return st == HR_OK ? kernel_zero(bodies, sizeof(unsigned), s) : st;
     }
     // after the stream has synchronised: count the kernels the loop ran
     hr_status account()

@@ -432,6 +432,39 @@ __global__ void __launch_bounds__(MS_THREADS) k_ms_outer(const MsArgs a)
     }
 }
 
+// y = a0 b + sum_k a_k x_k (FP64; x_k of right-hand side j at (k nrhs + j))
+struct LincombArgs {
+    long n;               // complex numbers per field
+    int nterms, nrhs;
+    size_t stride;
+    const char *b, *x;
+    char *y;
+    double a0;
+    double a[MS_MAX_SHIFTS];
+};
+
+__global__ void __launch_bounds__(MS_THREADS) k_lincomb(const LincombArgs a)
+{
+    const int j = blockIdx.y;
+    const char *bj = a.b + (size_t)j * a.stride;
+    char *yj = a.y + (size_t)j * a.stride;
+    MS_LOOP(v, a.n)
+    {
+        const size_t off = (size_t)v * 16;
+        double b[2], y[2];
+        ld16(bj + off, b);
+        y[0] = a.a0 * b[0];
+        y[1] = a.a0 * b[1];
+        for (int k = 0; k < a.nterms; k++) {
+            double x[2];
+            ld16(a.x + ((size_t)k * a.nrhs + j) * a.stride + off, x);
+            y[0] = fma(a.a[k], x[0], y[0]);
+            y[1] = fma(a.a[k], x[1], y[1]);
+        }
+        st16(yj + off, y);
+    }
+}
+
 // ------------------------------- host side --------------------------------
 
 struct MsCtx {
@@ -606,7 +639,9 @@ struct MsGraph {
         hr_status st = kernel_zero(bodies, sizeof(unsigned), s);
         if (st != HR_OK) return st;
         HR_CUDA_CHECK(cudaGraphLaunch(exec, s));
-        return kernel_copy(bodies_dev, bodies, sizeof(unsigned), s);
+        // the counter slot is a reduction ticket of other launches: back to zero
+        st = kernel_copy(bodies_dev, bodies, sizeof(unsigned), s);
+        return st == HR_OK ? kernel_zero(bodies, sizeof(unsigned), s) : st;
     }
     void account() { count_launch((long long)*bodies_host * per_body); }
 };
@@ -932,4 +967,40 @@ extern "C" hr_status hr_cg_solve_multishift(const hr_gauge *g, hr_parity sys, co
     if (overall == HR_ERR_NOT_CONVERGED) set_error("multi-shift CG stopped above tolerance");
     if (overall == HR_ERR_NONFINITE) set_error("multi-shift CG met a non-finite or non-positive reduction");
     return overall;
+}
+
+extern "C" hr_status hr_field_lincomb(const hr_lattice_desc *lat, hr_parity par, double a0, const void *b,
+                                      int nterms, const double *a, const void *x, void *y, int nrhs, void *stream)
+{
+    hr_status st = check_lattice(lat);
+    if (st != HR_OK) return st;
+    if (!b || !y || nrhs < 1 || nterms < 0 || nterms > MS_MAX_SHIFTS || (nterms > 0 && (!a || !x)) ||
+        (par != HR_EVEN && par != HR_ODD && par != HR_FULL)) {
+        set_error("hr_field_lincomb: bad arguments (0 <= nterms <= %d, nrhs >= 1)", MS_MAX_SHIFTS);
+        return HR_ERR_INVALID;
+    }
+    const long V = lat_volume(*lat);
+    const long ns = par == HR_FULL ? V : V / 2;
+    const int D = rep_dim(lat->N, lat->rep);
+    const size_t stride = field_rhs_bytes(ns, D, HR_F64);
+    if (nterms > 0 && static_cast<char *>(y) < static_cast<const char *>(x) + stride * nterms * nrhs &&
+        static_cast<const char *>(x) < static_cast<char *>(y) + stride * nrhs) {
+        set_error("hr_field_lincomb: y must not overlap x");
+        return HR_ERR_INVALID;
+    }
+    LincombArgs la;
+    memset(&la, 0, sizeof la);
+    la.n = ns * 4 * D;
+    la.nterms = nterms;
+    la.nrhs = nrhs;
+    la.stride = stride;
+    la.b = static_cast<const char *>(b);
+    la.x = static_cast<const char *>(x);
+    la.y = static_cast<char *>(y);
+    la.a0 = a0;
+    for (int k = 0; k < nterms; k++) la.a[k] = a[k];
+    const long blocks = std::max(1L, std::min((la.n + MS_THREADS - 1) / MS_THREADS, 152L * 8));
+    k_lincomb<<<dim3((unsigned)blocks, (unsigned)nrhs), MS_THREADS, 0, reinterpret_cast<cudaStream_t>(stream)>>>(la);
+    HR_LAUNCH_CHECK("k_lincomb");
+    return HR_OK;
 }

@@ -38,7 +38,7 @@ EXPORTS = ["hr_represent_gauge", "hr_gauge_update", "hr_gauge_set_link_mode", "h
            "hr_field_bytes", "hr_field_convert", "hr_field_dot", "hr_field_dot_static",
            "hr_dirac_apply", "hr_dirac_dagger",
            "hr_cg_solve", "hr_cg_solve_batched", "hr_cg_solve_force", "hr_cg_solve_multishift",
-           "hr_dirac_force", "hr_rep_dim", "hr_generators",
+           "hr_field_lincomb", "hr_dirac_force", "hr_rep_dim", "hr_generators",
            "hr_status_string", "hr_last_error", "hr_launch_count"]
 
 
@@ -103,6 +103,7 @@ def load():
         "hr_dirac_force": (I, [P, I, P, P, D, P, P]),
         "hr_cg_solve_multishift": (I, [P, I, P, P, I, ctypes.POINTER(D), I, ctypes.POINTER(CgParams),
                                        ctypes.POINTER(CgResult), P]),
+        "hr_field_lincomb": (I, [LP, I, D, P, I, ctypes.POINTER(D), P, P, I, P]),
         "hr_cg_solve_force": (I, [P, I, P, P, ctypes.POINTER(CgParams), ctypes.POINTER(CgResult), P, D, P, P]),
         "hr_rep_dim": (I, [I, I]),
         "hr_generators": (I, [I, ctypes.POINTER(D)]),
@@ -212,6 +213,30 @@ def field_dot(lat: Lattice, parity: int, prec: int, a, b, nrhs: int = 1, stream=
     _check(load().hr_field_dot(ctypes.byref(d), parity, prec, _ptr(a), _ptr(b), nrhs, out,
                                _stream(stream)))
     return [complex(out[2 * k], out[2 * k + 1]) for k in range(nrhs)]
+
+
+def field_lincomb(lat: Lattice, parity: int, a0: float, b, coeffs, x, y=None, nrhs: int = 1, stream=None):
+    """y = a0 b + sum_k coeffs[k] x[k] (FP64 fields; x as cg_solve_multishift returns it)."""
+    d = lat.desc()
+    n = len(coeffs)
+    if y is None:
+        y = torch.empty_like(b)
+    arr = (ctypes.c_double * max(n, 1))(*[float(c) for c in coeffs])
+    _check(load().hr_field_lincomb(ctypes.byref(d), parity, float(a0), _ptr(b), n, arr, _ptr(x), _ptr(y),
+                                   nrhs, _stream(stream)))
+    return y
+
+
+def rational_apply(g, sys: int, b, approx, nrhs: int = 1, tol: float = 1e-10, inner: int = F64,
+                   inner_tol: float = 1e-5, stream=None):
+    """r(A) b = a0 b + sum_k a_k (A + b_k)^-1 b for a RationalApprox (the RHMC's
+    heat-bath and action terms, Sec. 4.3.2): one multi-shift inversion over the
+    poles, then one linear-combination kernel.  Returns (y, x_k, results)."""
+    x, res, st = g.cg_solve_multishift(sys, b, approx.poles, nrhs=nrhs, tol=tol, inner=inner,
+                                       inner_tol=inner_tol, stream=stream)
+    par = FULL if sys == FULL else EVEN
+    y = field_lincomb(g.lat, par, approx.a0, b, approx.residues, x, nrhs=nrhs, stream=stream)
+    return y, x, res
 
 
 def _prec_mask(precs) -> int:

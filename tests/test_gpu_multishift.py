@@ -140,3 +140,63 @@ def test_multishift_bad_arguments(hr, case):
                           ([0.0] * 65, hr.F64)):
         with pytest.raises(hr.HrError):
             g.cg_solve_multishift(hr.EO_PRECOND, b, shifts, inner=inner)
+
+
+def test_field_lincomb(hr, case):
+    """y = a0 b + sum_k a_k x_k against numpy, every parity, aliasing y = b."""
+    lat, L, UR, g = case
+    for par in (hr.EVEN, hr.FULL):
+        ns = lat.nsites(par)
+        b = H.spinor(ns, lat.D, 89, nrhs=2)
+        x = np.stack([H.spinor(ns, lat.D, 90 + k, nrhs=2) for k in range(3)])
+        a = [0.5, -1.25, 3.0]
+        want = 0.75 * b + sum(c * xk for c, xk in zip(a, x))
+        y = hr.field_lincomb(lat, par, 0.75, G.to_gpu(b), a, G.to_gpu(x), nrhs=2)
+        np.testing.assert_allclose(y.cpu().numpy(), want, rtol=0, atol=1e-14 * np.abs(want).max())
+        bd = G.to_gpu(b)
+        hr.field_lincomb(lat, par, 0.75, bd, a, G.to_gpu(x), y=bd, nrhs=2)
+        np.testing.assert_allclose(bd.cpu().numpy(), want, rtol=0, atol=1e-14 * np.abs(want).max())
+    # no terms: y = a0 b
+    b = H.spinor(lat.nsites(hr.EVEN), lat.D, 97)
+    y = hr.field_lincomb(lat, hr.EVEN, -2.0, G.to_gpu(b), [], None)
+    np.testing.assert_array_equal(y.cpu().numpy(), -2.0 * b)
+
+
+@pytest.mark.parametrize("inner", [0, 1], ids=["f64", "f32"])
+def test_rational_apply(hr, oracle_mod, case, inner):
+    """The RHMC's r(A) b with Zolotarev poles and residues (Sec. 4.3.2) against
+    the oracle's definition a0 b + sum_k a_k (A + b_k)^-1 b (one shifted CG per
+    pole)."""
+    from paper_2503_06721_gb300 import rational
+    lat, L, UR, g = case
+    m4 = 4 + L.m0
+    ra = rational.zolotarev_inv_sqrt(8, 1e-3, (m4 * m4 + 16) ** 2)
+    b = H.spinor(lat.nsites(hr.EVEN), lat.D, 101)
+    y, x, res = hr.rational_apply(g, hr.EO_PRECOND, G.to_gpu(b), ra, tol=1e-11, inner=inner)
+    assert all(r[0]["status"] == "HR_OK" for r in res)
+    xo, ok, its, rr = oracle_mod.cg_multishift(L, UR, 1, b, ra.poles, tol=1e-12)
+    assert all(ok)
+    want = ra.a0 * b + sum(a * xk for a, xk in zip(ra.residues, xo))
+    got = y.cpu().numpy()
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-9
+
+
+def test_solver_counters_left_clean(hr, oracle_mod, case):
+    """A solve leaves the handle's reduction tickets at zero: a CG with one
+    right-hand side, then a 2-shift solve, then a 10-shift solve (whose systems
+    4 and 8 reduce on the tickets the earlier graphs counted loop bodies in)
+    must all agree with the oracle."""
+    lat, L, UR, g = case
+    b = H.spinor(lat.nsites(hr.EVEN), lat.D, 103)
+    bd = G.to_gpu(b)
+    g.cg_solve(hr.EO_PRECOND, bd, tol=1e-10)
+    g.cg_solve_multishift(hr.EO_PRECOND, bd, [0.0, 0.5], tol=1e-10)
+    shifts = [0.01 * 2 ** k for k in range(10)]
+    x, res, st = g.cg_solve_multishift(hr.EO_PRECOND, bd, shifts, tol=1e-10)
+    assert st == 0
+    xs = x.cpu().numpy()
+    for k, s in enumerate(shifts):
+        r = b - _shifted_apply(oracle_mod, L, UR, 3, xs[k], s)
+        true_rel = np.linalg.norm(r) / np.linalg.norm(b)
+        assert true_rel <= 1e-10 * 1.001, (k, true_rel)
+        assert abs(res[k][0]["true_rel_residual"] - true_rel) <= 0.05 * true_rel + 1e-15, (k, res[k][0])
