@@ -97,6 +97,8 @@ def _load():
             "or_cg": (I, [LP, P, I, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]),
             "or_cg_shifted": (I, [LP, P, I, D, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]),
             "or_force": (None, [LP, P, P, P, P]),
+            "or_plaquette_action": (D, [LP, P, D]),
+            "or_gauge_force": (None, [LP, P, D, P]),
             "or_num_threads": (I, []),
             "or_hop_sites": (None, [LP, P, I, P, P, ctypes.c_long, P, I]),
             "or_hop_local": (None, [LP, P, P, P, P, I]),
@@ -282,6 +284,112 @@ def force(L: Lat, UR, X, Y) -> np.ndarray:
     F = np.zeros((volume(L), 4, L.N * L.N - 1), np.float64)
     _load().or_force(ctypes.byref(L), _p(UR), _p(X), _p(Y), _p(F))
     return F
+
+
+# ---- HMC building blocks (Sec. 2.4, Sec. 2.5, Sec. 4.2) ----
+
+T_FUND = 0.5   # Tr T^a T^b = T_F delta^ab for the fundamental generators
+
+
+def plaquette_action(L: Lat, UF, beta: float) -> float:
+    """S_g = beta sum_{x, mu<nu} (1 - Re tr P_mu_nu(x) / N) (Eq. plaquette)."""
+    UF = _c(UF)
+    return _load().or_plaquette_action(ctypes.byref(L), _p(UF), float(beta))
+
+
+def gauge_force(L: Lat, UF, beta: float) -> np.ndarray:
+    """d/de S_g along exp(i e T^a) U_mu(x); F[V, 4, N*N-1]."""
+    UF = _c(UF)
+    F = np.zeros((volume(L), 4, L.N * L.N - 1), np.float64)
+    _load().or_gauge_force(ctypes.byref(L), _p(UF), float(beta), _p(F))
+    return F
+
+
+def su_algebra(N: int, pi) -> np.ndarray:
+    """sum_a pi^a T^a for pi[..., N*N-1] (Hermitian N x N matrices)."""
+    T = generators(N)
+    return np.einsum("...a,aij->...ij", np.asarray(pi, np.float64), T)
+
+
+def link_update(L: Lat, UF, pi, eps: float) -> np.ndarray:
+    """U_mu(x) <- exp(i eps pi^a T^a) U_mu(x) (dU/dtau = pi U, Sec. 2.5), the
+    exponential of the Hermitian eps pi^a T^a by its eigendecomposition."""
+    H = eps * su_algebra(L.N, pi)
+    w, Q = np.linalg.eigh(H)
+    E = np.einsum("...ij,...j,...kj->...ik", Q, np.exp(1j * w), Q.conj())
+    return np.einsum("...ij,...jk->...ik", E, _c(UF))
+
+
+def kinetic_energy(pi) -> float:
+    """H_pi = T_F/2 sum_{x,mu,a} pi^a(x,mu)^2 (Sec. 2.5)."""
+    p = np.ascontiguousarray(pi, np.float64).ravel()
+    return 0.5 * T_FUND * sum_neumaier(p * p)
+
+
+def fermion_action_eo(L: Lat, UR, phi_e, tol: float = 1e-14) -> float:
+    """S_f = phi^dag (Dhat^dag Dhat)^-1 phi for an even-site pseudofermion
+    (two flavours, even/odd preconditioned: det Q^2 = det Dhat^dag Dhat up to a
+    constant, Sec. 4.3.3)."""
+    x, ok, it, rr = cg(L, UR, 1, phi_e, tol=tol, max_iter=100000)
+    if not ok:
+        raise RuntimeError("oracle CG did not converge")
+    return float(np.real(np.vdot(phi_e.ravel(), x.ravel())))
+
+
+def fermion_force_eo(L: Lat, UR, phi_e, tol: float = 1e-14) -> np.ndarray:
+    """d/de S_f along exp(i e T^a) U_mu(x) for S_f = phi^dag (Dhat^dag Dhat)^-1 phi:
+    with x = (Dhat^dag Dhat)^-1 phi and y = Dhat x, dS_f = -2 Re <y, dDhat x>, and
+    -2 Re <y, Dhat x> is minus the full-operator form -2 Re <Y', D X'> on
+    X' = (x, D_oe x), Y' = (y, (D^dag)_oe y) (the diagonal terms do not depend on U)."""
+    x, ok, it, rr = cg(L, UR, 1, phi_e, tol=tol, max_iter=100000)
+    if not ok:
+        raise RuntimeError("oracle CG did not converge")
+    y = dhat(L, UR, x)
+    Xp = merge(L, x, hop_parity(L, UR, 1, x))
+    Yp = merge(L, y, hop_parity(L, UR, 1, y, dagger=True))
+    return -force(L, UR, Xp, Yp)
+
+
+def hamiltonian(L: Lat, UF, pi, beta: float, phi_e=None, tol: float = 1e-14):
+    """(H_pi, S_g, S_f) of Sec. 2.5 (S_f = 0 without a pseudofermion)."""
+    Sf = 0.0
+    if phi_e is not None:
+        Sf = fermion_action_eo(L, represent_field(L, UF), phi_e, tol)
+    return kinetic_energy(pi), plaquette_action(L, UF, beta), Sf
+
+
+# second-order minimum-norm (Omelyan) integrator parameter lambda
+OMELYAN_LAMBDA = 0.1931833275037836
+
+
+def md_trajectory(L: Lat, UF, pi, beta: float, tau: float, nsteps: int, phi_e=None,
+                  integrator: str = "omelyan", tol: float = 1e-14):
+    """Molecular dynamics (Sec. 2.5, Sec. 4.2): Hamilton's equations dU/dtau = pi U,
+    dpi/dtau = F with F^a = -(1/T_F) dS/de^a, integrated over tau in nsteps steps
+    by leapfrog (PQP) or the 2nd-order Omelyan scheme (PQPQP,
+    P(l h) Q(h/2) P((1-2l) h) Q(h/2) P(l h)).  Returns the new (U, pi)."""
+    U = np.array(UF, np.complex128, copy=True)
+    p = np.array(pi, np.float64, copy=True)
+    h = tau / nsteps
+
+    def P(eps):
+        F = gauge_force(L, U, beta)
+        if phi_e is not None:
+            F = F + fermion_force_eo(L, represent_field(L, U), phi_e, tol)
+        p[...] = p - (eps / T_FUND) * F
+
+    def Q(eps):
+        U[...] = link_update(L, U, p, eps)
+
+    for _ in range(nsteps):
+        if integrator == "leapfrog":
+            P(h / 2); Q(h); P(h / 2)
+        elif integrator == "omelyan":
+            lam = OMELYAN_LAMBDA
+            P(lam * h); Q(h / 2); P((1 - 2 * lam) * h); Q(h / 2); P(lam * h)
+        else:
+            raise ValueError(integrator)
+    return U, p
 
 
 # ---- parity helpers (pure index bookkeeping) ----

@@ -726,6 +726,97 @@ void or_force(const or_lat *L, const orc *UR, const orc *X, const orc *Y,
     free(TR);
 }
 
+/* ------------------------------------------------------------------ */
+/* Wilson gauge action and its force (Sec. 2.4 Eq. plaquette, Sec. 2.5)  */
+/* ------------------------------------------------------------------ */
+/* P_{mu nu}(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag.  The gauge
+ * field is periodic in every direction (the fermion boundary signs live in
+ * the represented links only). */
+static void plaquette(const or_lat *L, const orc *UF, long x, int mu, int nu,
+                      orc *P)
+{
+    int N = L->N;
+    long xm = or_neighbour(L, x, mu, +1), xn = or_neighbour(L, x, nu, +1);
+    const orc *U1 = UF + ((size_t)x * 4 + mu) * N * N;
+    const orc *U2 = UF + ((size_t)xm * 4 + nu) * N * N;
+    const orc *U3 = UF + ((size_t)xn * 4 + mu) * N * N;
+    const orc *U4 = UF + ((size_t)x * 4 + nu) * N * N;
+    orc a[OR_MAXD * OR_MAXD], b[OR_MAXD * OR_MAXD], d[OR_MAXD * OR_MAXD];
+    mat_mul(N, U1, U2, a);
+    mat_dag(N, U3, d);
+    mat_mul(N, a, d, b);
+    mat_dag(N, U4, d);
+    mat_mul(N, b, d, P);
+}
+
+double or_plaquette_action(const or_lat *L, const orc *UF, double beta)
+{
+    long V = or_volume(L);
+    int N = L->N;
+    double *site = malloc(V * sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (long x = 0; x < V; x++) {
+        orc P[OR_MAXD * OR_MAXD];
+        double s = 0;
+        for (int mu = 0; mu < 4; mu++)
+            for (int nu = mu + 1; nu < 4; nu++) {
+                plaquette(L, UF, x, mu, nu, P);
+                s += 1.0 - creal(mat_trace(N, P)) / N;
+            }
+        site[x] = s;
+    }
+    double S = beta * or_sum_neumaier(site, V);
+    free(site);
+    return S;
+}
+
+/* F[x][mu][a] = d/de S_g(U_mu(x) -> exp(i e T^a) U_mu(x)) at e = 0.  The
+ * plaquettes that hold U_mu(x) give Re tr(U_mu(x) W) with the staple sum
+ *   W = sum_{nu != mu} [ U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
+ *                      + U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu) ],
+ * so  F^a = -(beta/N) Re tr(i T^a U_mu(x) W). */
+void or_gauge_force(const or_lat *L, const orc *UF, double beta, double *F)
+{
+    long V = or_volume(L);
+    int N = L->N, ng = N * N - 1;
+    orc *T = malloc((size_t)ng * N * N * sizeof(orc));
+    or_generators(N, T);
+#pragma omp parallel for schedule(static)
+    for (long x = 0; x < V; x++) {
+        orc W[OR_MAXD * OR_MAXD], a[OR_MAXD * OR_MAXD], b[OR_MAXD * OR_MAXD],
+            d[OR_MAXD * OR_MAXD], M[OR_MAXD * OR_MAXD];
+        for (int mu = 0; mu < 4; mu++) {
+            for (int k = 0; k < N * N; k++) W[k] = 0;
+            long xm = or_neighbour(L, x, mu, +1);
+            for (int nu = 0; nu < 4; nu++) {
+                if (nu == mu) continue;
+                long xn = or_neighbour(L, x, nu, +1);
+                long xdn = or_neighbour(L, x, nu, -1);
+                long xmdn = or_neighbour(L, xm, nu, -1);
+                /* upper staple */
+                mat_dag(N, UF + ((size_t)xn * 4 + mu) * N * N, d);
+                mat_mul(N, UF + ((size_t)xm * 4 + nu) * N * N, d, a);
+                mat_dag(N, UF + ((size_t)x * 4 + nu) * N * N, d);
+                mat_mul(N, a, d, b);
+                for (int k = 0; k < N * N; k++) W[k] += b[k];
+                /* lower staple */
+                mat_dag(N, UF + ((size_t)xmdn * 4 + nu) * N * N, a);
+                mat_dag(N, UF + ((size_t)xdn * 4 + mu) * N * N, d);
+                mat_mul(N, a, d, b);
+                mat_mul(N, b, UF + ((size_t)xdn * 4 + nu) * N * N, a);
+                for (int k = 0; k < N * N; k++) W[k] += a[k];
+            }
+            mat_mul(N, UF + ((size_t)x * 4 + mu) * N * N, W, M);
+            for (int g = 0; g < ng; g++) {
+                mat_mul(N, T + (size_t)g * N * N, M, a);
+                F[((size_t)x * 4 + mu) * ng + g] =
+                    -(beta / N) * creal(I * mat_trace(N, a));
+            }
+        }
+    }
+    free(T);
+}
+
 int or_num_threads(void)
 {
 #ifdef _OPENMP

@@ -136,6 +136,15 @@ int or_cg_shifted(const or_lat *L, const orc *UR, int sys, double sigma,
 void or_force(const or_lat *L, const orc *UR, const orc *X, const orc *Y,
               double *F);
 
+/* ---- Wilson gauge action (Sec. 2.4, Eq. plaquette) and its force ----
+ * S_g = beta sum_{x, mu<nu} (1 - Re tr P_{mu nu}(x) / N), the gauge field
+ * periodic in every direction.  F[x][mu][a] = d/de S_g(U_mu(x) ->
+ * exp(i e T^a) U_mu(x)) at e = 0 = -(beta/N) Re tr(i T^a U_mu(x) W_mu(x)),
+ * W the sum of the six staples (Sec. 2.5 writes this, divided by -T_F, as
+ * the gauge force F_G). */
+double or_plaquette_action(const or_lat *L, const orc *UF, double beta);
+void or_gauge_force(const or_lat *L, const orc *UF, double beta, double *F);
+
 /* ---- helpers ---- */
 void or_split_parity(const or_lat *L, const orc *full, orc *even, orc *odd);
 void or_merge_parity(const or_lat *L, const orc *even, const orc *odd,

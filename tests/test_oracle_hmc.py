@@ -1,0 +1,176 @@
+"""Pins of the oracle's HMC building blocks (Sec. 2.4 Eq. plaquette, Sec. 2.5,
+Sec. 4.2): the Wilson plaquette action against a closed-form abelian field
+and gauge invariance, its force and the even/odd fermion force against
+central finite differences of the actions, the link update against closed
+forms and scipy's matrix exponential, and the molecular-dynamics integrators
+against the two properties the paper tests its integrators by: the
+Hamiltonian violation falls as the step size squared (Table 2: leapfrog and
+2nd-order Omelyan) and the trajectory is reversible."""
+import numpy as np
+import pytest
+
+from tests import _helpers as H
+
+BETA = 2.2
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+def _momenta(V, N, seed):
+    # e^{-H_pi} with H_pi = T_F/2 sum pi^2: pi^a ~ N(0, 1/T_F)
+    return _rng(seed).normal(size=(V, 4, N * N - 1)) / np.sqrt(0.5)
+
+
+def test_plaquette_action_closed_forms(oracle_mod):
+    N, dims = 2, (4, 6, 2, 2)
+    L = oracle_mod.lat(N, "FUND", dims, (1, 1, 1, 1), 0.0)
+    V = int(np.prod(dims))
+    U = np.tile(np.eye(N, dtype=np.complex128), (V, 4, 1, 1))
+    assert oracle_mod.plaquette_action(L, U, BETA) == 0.0
+    # U_0(x) = diag(e^{i th x1}, e^{-i th x1}), th = 2 pi k / L1, all other links 1:
+    # only the (0,1) plaquettes differ from 1, each with Re tr P = 2 cos th
+    th = 2 * np.pi * 2 / dims[1]
+    x1 = H.coords(dims)[:, 1]
+    U[:, 0, 0, 0] = np.exp(1j * th * x1)
+    U[:, 0, 1, 1] = np.exp(-1j * th * x1)
+    S = oracle_mod.plaquette_action(L, U, BETA)
+    assert abs(S - BETA * V * (1 - np.cos(th))) < 1e-12 * BETA * V
+
+
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_plaquette_action_gauge_invariant(oracle_mod, N):
+    dims = (4, 2, 2, 4)
+    L = oracle_mod.lat(N, "FUND", dims, (1, 1, 1, 1), 0.0)
+    V = int(np.prod(dims))
+    U = H.links(dims, N, 0.7, seed=107)
+    g = H.su_n(V, N, 109, eps=1.5)
+    Ug = np.empty_like(U)
+    c = H.coords(dims)
+    stride = np.array([dims[1] * dims[2] * dims[3], dims[2] * dims[3], dims[3], 1])
+    for mu in range(4):
+        cn = c.copy()
+        cn[:, mu] = (cn[:, mu] + 1) % dims[mu]
+        xn = cn @ stride
+        Ug[:, mu] = np.einsum("xij,xjk,xlk->xil", g, U[:, mu], g[xn].conj())
+    S = oracle_mod.plaquette_action(L, U, BETA)
+    assert S > 0
+    assert abs(oracle_mod.plaquette_action(L, Ug, BETA) - S) < 1e-12 * S
+
+
+def _perturb(oracle_mod, N, U, x, mu, a, eps):
+    T = oracle_mod.generators(N)
+    w, Q = np.linalg.eigh(eps * T[a])
+    E = (Q * np.exp(1j * w)) @ Q.conj().T
+    Up = U.copy()
+    Up[x, mu] = E @ U[x, mu]
+    return Up
+
+
+@pytest.mark.parametrize("N", [2, 3])
+def test_gauge_force_finite_differences(oracle_mod, N):
+    dims = (4, 2, 2, 2)
+    L = oracle_mod.lat(N, "FUND", dims, (1, 1, 1, 1), 0.0)
+    V = int(np.prod(dims))
+    U = H.links(dims, N, 0.8, seed=113)
+    F = oracle_mod.gauge_force(L, U, BETA)
+    eps = 1e-5
+    rng = _rng(127)
+    for _ in range(12):
+        x, mu, a = int(rng.integers(V)), int(rng.integers(4)), int(rng.integers(N * N - 1))
+        Sp = oracle_mod.plaquette_action(L, _perturb(oracle_mod, N, U, x, mu, a, eps), BETA)
+        Sm = oracle_mod.plaquette_action(L, _perturb(oracle_mod, N, U, x, mu, a, -eps), BETA)
+        fd = (Sp - Sm) / (2 * eps)
+        assert abs(fd - F[x, mu, a]) < 1e-7 * max(1.0, abs(fd)), (x, mu, a, fd, F[x, mu, a])
+
+
+def test_fermion_force_eo_finite_differences(oracle_mod):
+    N, rep = 2, "ADJ"
+    dims = (4, 2, 2, 2)
+    L = oracle_mod.lat(N, rep, dims, (-1, 1, 1, 1), 0.2)
+    V = int(np.prod(dims))
+    D = oracle_mod.rep_dim(N, rep)
+    U = H.links(dims, N, 0.6, seed=131)
+    phi = H.spinor(V // 2, D, 137)
+    F = oracle_mod.fermion_force_eo(L, oracle_mod.represent_field(L, U), phi)
+    eps = 1e-5
+    rng = _rng(139)
+    for _ in range(8):
+        x, mu, a = int(rng.integers(V)), int(rng.integers(4)), int(rng.integers(N * N - 1))
+        Sp = oracle_mod.fermion_action_eo(L, oracle_mod.represent_field(
+            L, _perturb(oracle_mod, N, U, x, mu, a, eps)), phi)
+        Sm = oracle_mod.fermion_action_eo(L, oracle_mod.represent_field(
+            L, _perturb(oracle_mod, N, U, x, mu, a, -eps)), phi)
+        fd = (Sp - Sm) / (2 * eps)
+        assert abs(fd - F[x, mu, a]) < 1e-6 * max(1.0, abs(fd)), (x, mu, a, fd, F[x, mu, a])
+
+
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_link_update_exponential(oracle_mod, N):
+    from scipy.linalg import expm
+    dims = (2, 2, 2, 2)
+    L = oracle_mod.lat(N, "FUND", dims, (1, 1, 1, 1), 0.0)
+    V = 16
+    U = H.links(dims, N, 0.9, seed=149)
+    pi = _momenta(V, N, 151)
+    eps = 0.37
+    Un = oracle_mod.link_update(L, U, pi, eps)
+    X = oracle_mod.su_algebra(N, pi)
+    for x in (0, 5, 11):
+        for mu in range(4):
+            np.testing.assert_allclose(Un[x, mu], expm(1j * eps * X[x, mu]) @ U[x, mu], atol=1e-13)
+    I = np.eye(N)
+    np.testing.assert_allclose(np.einsum("xmij,xmkj->xmik", Un, Un.conj()), np.broadcast_to(I, Un.shape),
+                               atol=1e-13)
+    np.testing.assert_allclose(np.linalg.det(Un), 1.0, atol=1e-13)
+    if N == 2:
+        # exp(i eps pi^a sigma^a / 2) = cos(|v|/2) + i sin(|v|/2) v.sigma/|v|, v = eps pi
+        sig = [np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]), np.array([[1, 0], [0, -1]])]
+        v = eps * pi[3, 2]
+        n = np.linalg.norm(v)
+        E = np.cos(n / 2) * I + 1j * np.sin(n / 2) * sum(v[k] / n * sig[k] for k in range(3))
+        np.testing.assert_allclose(Un[3, 2], E @ U[3, 2], atol=1e-14)
+
+
+def _hmc_setup(oracle_mod, fermions):
+    N, rep = 2, "FUND"
+    dims = (4, 4, 2, 2)
+    L = oracle_mod.lat(N, rep, dims, (-1, 1, 1, 1), 0.3)
+    V = int(np.prod(dims))
+    U = H.links(dims, N, 0.5, seed=157)
+    pi = _momenta(V, N, 163)
+    phi = None
+    if fermions:
+        # heat bath: phi = Dhat^dag eta with eta Gaussian, so that S_f = |eta|^2
+        eta = H.spinor(V // 2, oracle_mod.rep_dim(N, rep), 167)
+        phi = oracle_mod.dhat(L, oracle_mod.represent_field(L, U), eta, dagger=True)
+    return L, U, pi, phi
+
+
+def _dH(oracle_mod, L, U, pi, phi, tau, nsteps, integrator):
+    H0 = sum(oracle_mod.hamiltonian(L, U, pi, BETA, phi))
+    U1, p1 = oracle_mod.md_trajectory(L, U, pi, BETA, tau, nsteps, phi, integrator)
+    return sum(oracle_mod.hamiltonian(L, U1, p1, BETA, phi)) - H0
+
+
+@pytest.mark.parametrize("integrator", ["leapfrog", "omelyan"])
+@pytest.mark.parametrize("fermions", [False, True], ids=["gauge", "gauge+fermion"])
+def test_md_energy_violation_scales_as_step_squared(oracle_mod, integrator, fermions):
+    L, U, pi, phi = _hmc_setup(oracle_mod, fermions)
+    tau = 0.5
+    # the minimum-norm Omelyan scheme has a small step^2 coefficient, so its
+    # step^4 terms matter longer: it is held to the ratio on finer steps
+    steps = (4, 8, 16) if integrator == "leapfrog" else (8, 16, 32)
+    d = [abs(_dH(oracle_mod, L, U, pi, phi, tau, n, integrator)) for n in steps]
+    r1, r2 = d[0] / d[1], d[1] / d[2]
+    assert 3.0 < r1 < 5.2 and 3.6 < r2 < 4.4, (d, r1, r2)
+
+
+@pytest.mark.parametrize("integrator", ["leapfrog", "omelyan"])
+def test_md_reversible(oracle_mod, integrator):
+    L, U, pi, phi = _hmc_setup(oracle_mod, True)
+    U1, p1 = oracle_mod.md_trajectory(L, U, pi, BETA, 0.4, 5, phi, integrator)
+    U2, p2 = oracle_mod.md_trajectory(L, U1, -p1, BETA, 0.4, 5, phi, integrator)
+    assert np.abs(U2 - U).max() < 1e-11
+    assert np.abs(p2 + pi).max() < 1e-10 * np.abs(pi).max()
