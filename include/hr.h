@@ -341,6 +341,68 @@ hr_status hr_field_lincomb(const hr_lattice_desc *lat, hr_parity par,
                            void *stream);
 
 /* ------------------------------------------------------------------ */
+/* HMC building blocks (Sec. 2.4, Sec. 2.5, Sec. 4.2)                    */
+/* ------------------------------------------------------------------ */
+/* Conventions (Sec. 2.5): H = H_pi + S_g + S_f, H_pi = T_F/2 sum pi^2
+ * (T_F = 1/2), dU/dtau = pi U with pi = i pi^a T^a, dpi^a/dtau = F^a =
+ * -(1/T_F) dS/de^a, dS/de^a the derivative along exp(i e T^a) U_mu(x).
+ * U_fund: DEVICE FP64 [V][4][N][N] complex (the layout of
+ * hr_represent_gauge), periodic in every direction.  pi and forces: DEVICE
+ * FP64 [V][4][N*N-1].  N = 2, 3 or 4. */
+
+/* S_g = beta sum_{x, mu<nu} (1 - Re tr P_{mu nu}(x) / N), the Wilson action
+ * of the plaquette P_{mu nu}(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag
+ * U_nu(x)^dag (Eq. plaquette).  *S is a HOST double; synchronises stream. */
+hr_status hr_gauge_action(const hr_lattice_desc *lat, const void *U_fund,
+                          double beta, double *S, void *stream);
+
+/* F[x][mu][a] += coeff * dS_g/de^a = coeff * (-(beta/N)) Re tr(i T^a
+ * U_mu(x) W_mu(x)), W the sum of the six staples; coeff = -1/T_F gives the
+ * gauge force F_G of Sec. 2.5, coeff = -h/T_F a momentum step of length h. */
+hr_status hr_gauge_force(const hr_lattice_desc *lat, const void *U_fund,
+                         double beta, double coeff, double *F, void *stream);
+
+/* U_mu(x) <- exp(i eps pi^a(x,mu) T^a) U_mu(x) for every link (the gauge
+ * step of Hamilton's equations, Sec. 2.5). */
+hr_status hr_link_update(const hr_lattice_desc *lat, void *U_fund,
+                         const double *pi, double eps, void *stream);
+
+/* *H = T_F/2 sum pi^2 (HOST double; synchronises stream). */
+hr_status hr_momenta_energy(const hr_lattice_desc *lat, const double *pi,
+                            double *H, void *stream);
+
+typedef enum { HR_MD_LEAPFROG = 0, HR_MD_OMELYAN2 = 1 } hr_md_integrator;
+
+typedef struct {
+    double beta;                 /* Wilson gauge coupling */
+    double tau;                  /* trajectory length */
+    int nsteps;                  /* integration steps */
+    hr_md_integrator integrator; /* PQP, or P(l h) Q(h/2) P((1-2l)h) Q(h/2)
+                                    P(l h) with l = 0.1931833... (Sec. 4.2) */
+    hr_parity sys;               /* fermion action phi^dag A^-1 phi with
+                                    A = Dhat^dag Dhat (HR_EO_PRECOND, phi
+                                    even) or D^dag D (HR_FULL) */
+    hr_cg_params cg;             /* the fermion-force solves */
+} hr_md_params;
+
+typedef struct {
+    int force_evals;               /* fermion force evaluations */
+    int cg_iters;                  /* summed over them */
+    double max_true_rel_residual;  /* worst force solve */
+    hr_status status;
+} hr_md_stats;
+
+/* One molecular-dynamics trajectory of length tau: updates U_fund and pi in
+ * place, and leaves g representing the new U_fund.  phi (DEVICE pseudofermion,
+ * FP64 field of sys) may be NULL for the pure gauge theory; otherwise g must
+ * hold stored FP64 links (and those of p->cg.inner) and each momentum step
+ * runs hr_cg_solve_force.  Adjacent momentum steps are merged (leapfrog
+ * takes nsteps + 1 force evaluations, Omelyan 2 nsteps + 1).  BLOCKS. */
+hr_status hr_md_trajectory(hr_gauge *g, void *U_fund, double *pi,
+                           const void *phi, const hr_md_params *p,
+                           hr_md_stats *stats, void *stream);
+
+/* ------------------------------------------------------------------ */
 /* Fermion force (Sec. 2.5)                                              */
 /* ------------------------------------------------------------------ */
 /* F[x][mu][a] += coeff * d/de S(U_F(x,mu) -> exp(i e T^a) U_F(x,mu)) at e=0

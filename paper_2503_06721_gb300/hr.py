@@ -38,7 +38,8 @@ EXPORTS = ["hr_represent_gauge", "hr_gauge_update", "hr_gauge_set_link_mode", "h
            "hr_field_bytes", "hr_field_convert", "hr_field_dot", "hr_field_dot_static",
            "hr_dirac_apply", "hr_dirac_dagger",
            "hr_cg_solve", "hr_cg_solve_batched", "hr_cg_solve_force", "hr_cg_solve_multishift",
-           "hr_field_lincomb", "hr_dirac_force", "hr_rep_dim", "hr_generators",
+           "hr_field_lincomb", "hr_dirac_force", "hr_gauge_action", "hr_gauge_force", "hr_link_update",
+           "hr_momenta_energy", "hr_md_trajectory", "hr_rep_dim", "hr_generators",
            "hr_status_string", "hr_last_error", "hr_launch_count"]
 
 
@@ -62,6 +63,20 @@ class CgParams(ctypes.Structure):
 class CgResult(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int),
                 ("true_rel_residual", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+class MdParams(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("tau", ctypes.c_double), ("nsteps", ctypes.c_int),
+                ("integrator", ctypes.c_int), ("sys", ctypes.c_int), ("cg", CgParams)]
+
+
+class MdStats(ctypes.Structure):
+    _fields_ = [("force_evals", ctypes.c_int), ("cg_iters", ctypes.c_int),
+                ("max_true_rel_residual", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+MD_LEAPFROG, MD_OMELYAN2 = 0, 1
+T_FUND = 0.5
 
 
 _lib = None
@@ -104,6 +119,11 @@ def load():
         "hr_cg_solve_multishift": (I, [P, I, P, P, I, ctypes.POINTER(D), I, ctypes.POINTER(CgParams),
                                        ctypes.POINTER(CgResult), P]),
         "hr_field_lincomb": (I, [LP, I, D, P, I, ctypes.POINTER(D), P, P, I, P]),
+        "hr_gauge_action": (I, [LP, P, D, ctypes.POINTER(D), P]),
+        "hr_gauge_force": (I, [LP, P, D, D, P, P]),
+        "hr_link_update": (I, [LP, P, P, D, P]),
+        "hr_momenta_energy": (I, [LP, P, ctypes.POINTER(D), P]),
+        "hr_md_trajectory": (I, [P, P, P, P, ctypes.POINTER(MdParams), ctypes.POINTER(MdStats), P]),
         "hr_cg_solve_force": (I, [P, I, P, P, ctypes.POINTER(CgParams), ctypes.POINTER(CgResult), P, D, P, P]),
         "hr_rep_dim": (I, [I, I]),
         "hr_generators": (I, [I, ctypes.POINTER(D)]),
@@ -237,6 +257,68 @@ def rational_apply(g, sys: int, b, approx, nrhs: int = 1, tol: float = 1e-10, in
     par = FULL if sys == FULL else EVEN
     y = field_lincomb(g.lat, par, approx.a0, b, approx.residues, x, nrhs=nrhs, stream=stream)
     return y, x, res
+
+
+# ---- HMC building blocks (Sec. 2.4, 2.5, 4.2) ----
+
+def gauge_action(lat: Lattice, U_fund, beta: float, stream=None) -> float:
+    """S_g = beta sum (1 - Re tr P / N) (hr_gauge_action)."""
+    d = lat.desc()
+    out = ctypes.c_double(0.0)
+    _check(load().hr_gauge_action(ctypes.byref(d), _ptr(U_fund), float(beta), ctypes.byref(out),
+                                  _stream(stream)))
+    return out.value
+
+
+def gauge_force(lat: Lattice, U_fund, beta: float, coeff: float = 1.0, F=None, stream=None):
+    """F += coeff * dS_g/de^a (hr_gauge_force); F[V, 4, N*N-1] FP64."""
+    if F is None:
+        F = torch.zeros((lat.volume, 4, lat.N ** 2 - 1), dtype=torch.float64, device=U_fund.device)
+    d = lat.desc()
+    _check(load().hr_gauge_force(ctypes.byref(d), _ptr(U_fund), float(beta), float(coeff), _ptr(F),
+                                 _stream(stream)))
+    return F
+
+
+def link_update(lat: Lattice, U_fund, pi, eps: float, stream=None):
+    """U <- exp(i eps pi^a T^a) U in place (hr_link_update)."""
+    d = lat.desc()
+    _check(load().hr_link_update(ctypes.byref(d), _ptr(U_fund), _ptr(pi), float(eps), _stream(stream)))
+    return U_fund
+
+
+def momenta_energy(lat: Lattice, pi, stream=None) -> float:
+    """T_F/2 sum pi^2 (hr_momenta_energy)."""
+    d = lat.desc()
+    out = ctypes.c_double(0.0)
+    _check(load().hr_momenta_energy(ctypes.byref(d), _ptr(pi), ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def md_trajectory(g, U_fund, pi, phi, beta: float, tau: float, nsteps: int, integrator: int = MD_OMELYAN2,
+                  sys: int = EO_PRECOND, tol: float = 1e-10, inner: int = F64, inner_tol: float = 1e-5,
+                  chrono: bool = False, stream=None) -> dict:
+    """One MD trajectory in place on (U_fund, pi), g re-represented (hr_md_trajectory)."""
+    p = MdParams(float(beta), float(tau), int(nsteps), int(integrator), int(sys),
+                 CgParams(tol, 100000, inner, inner_tol, int(chrono), F64))
+    st = MdStats()
+    _check(load().hr_md_trajectory(g.handle, _ptr(U_fund), _ptr(pi), _ptr(phi), ctypes.byref(p),
+                                   ctypes.byref(st), _stream(stream)))
+    return dict(force_evals=st.force_evals, cg_iters=st.cg_iters,
+                max_true_rel_residual=st.max_true_rel_residual)
+
+
+def fermion_action(g, sys: int, phi, tol: float = 1e-12, inner: int = F64, stream=None) -> float:
+    """S_f = phi^dag A^-1 phi: one solve (hr_cg_solve) and one dot product (hr_field_dot)."""
+    x, res, st = g.cg_solve(sys, phi, tol=tol, inner=inner, stream=stream)
+    par = FULL if sys == FULL else EVEN
+    return field_dot(g.lat, par, F64, phi, x, stream=stream)[0].real
+
+
+def hamiltonian(g, U_fund, pi, phi, beta: float, sys: int = EO_PRECOND, tol: float = 1e-12, stream=None):
+    """(H_pi, S_g, S_f) of Sec. 2.5 for the links g represents (= U_fund)."""
+    Sf = fermion_action(g, sys, phi, tol, stream=stream) if phi is not None else 0.0
+    return momenta_energy(g.lat, pi, stream), gauge_action(g.lat, U_fund, beta, stream), Sf
 
 
 def _prec_mask(precs) -> int:
