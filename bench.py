@@ -373,6 +373,10 @@ def run_ours(args, rank, world, local_rank):
             multishift = multishift_compare(hr, g2, phi, stream, wl.m0)
         g2.close()
 
+    hmc = None
+    if rank == 0 and not args.no_hmc:
+        hmc = hmc_measure(hr, lat, U, dev, stream)
+
     batched = None
     if rank == 0 and not args.no_batched:
         g.close()
@@ -414,6 +418,7 @@ def run_ours(args, rank, world, local_rank):
             "cg": cg,
             "batched": batched,
             "multishift": multishift,
+            "hmc": hmc,
             "cpu_baseline": cpu,
         }
         print(json.dumps(out), flush=True)
@@ -476,6 +481,41 @@ def multishift_compare(hr, g, phi, stream, m0):
     out["rational_apply_mixed_fp32_ms"] = round(e0.elapsed_time(e1), 2)
     del x, y
     return out
+
+
+def hmc_measure(hr, lat, U, dev, stream, beta=5.5, tau=0.5, nsteps=4):
+    """One molecular-dynamics trajectory of the two-flavour HMC (Sec. 2.5,
+    Sec. 4.2) on the bench lattice: Wilson gauge action at beta, even/odd
+    pseudofermion from the heat bath phi = Dhat^dag eta, 2nd-order Omelyan
+    integrator, each force solve mixed FP32/FP64 to 1e-10 in the automatic link
+    mode.  Momenta and eta are seeded Gaussians."""
+    import torch
+    U3 = U.clone()
+    g3 = hr.Gauge(lat, U3, precs=("f64", "f32"), stored=True, rebuild=True)
+    g3.set_link_mode(hr.LINKS_AUTO)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2503067210 + 31)
+    ng = lat.N * lat.N - 1
+    pi = torch.randn((lat.volume, 4, ng), dtype=torch.float64, device=dev, generator=gen) / (hr.T_FUND ** 0.5)
+    eta = torch.randn((lat.volume // 2, 4, lat.D), dtype=torch.complex128, device=dev, generator=gen)
+    phi = g3.apply(hr.EO_PRECOND, hr.F64, eta, dagger=True)
+    H0 = hr.hamiltonian(g3, U3, pi, phi, beta, tol=1e-11, inner=hr.F32)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    st = hr.md_trajectory(g3, U3, pi, phi, beta, tau, nsteps, integrator=hr.MD_OMELYAN2, tol=1e-10,
+                          inner=hr.F32, inner_tol=1e-5)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    H1 = hr.hamiltonian(g3, U3, pi, phi, beta, tol=1e-11, inner=hr.F32)
+    g3.close()
+    return {"workload": f"two-flavour HMC trajectory, beta {beta}, tau {tau}, {nsteps} Omelyan steps, "
+                        "FP32-inner / FP64 force solves to 1e-10",
+            "trajectory_ms": round(ms, 1), "ms_per_force_eval": round(ms / max(1, st["force_evals"]), 1),
+            "force_evals": st["force_evals"], "cg_iters": st["cg_iters"],
+            "max_true_rel_residual": st["max_true_rel_residual"],
+            "H0": [round(h, 4) for h in H0], "dH": round(sum(H1) - sum(H0), 6)}
 
 
 def batched_compare(hr, synth, dev, stream, rep="ASYM"):
@@ -718,6 +758,7 @@ def main():
     ap.add_argument("--no-cg-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-FP64 solve comparison")
+    ap.add_argument("--no-hmc", action="store_true", help="skip the HMC trajectory measurement")
     ap.add_argument("--no-multishift", action="store_true",
                     help="skip the multi-shift-vs-sequential shifted solve comparison")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

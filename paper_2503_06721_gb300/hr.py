@@ -315,9 +315,10 @@ def fermion_action(g, sys: int, phi, tol: float = 1e-12, inner: int = F64, strea
     return field_dot(g.lat, par, F64, phi, x, stream=stream)[0].real
 
 
-def hamiltonian(g, U_fund, pi, phi, beta: float, sys: int = EO_PRECOND, tol: float = 1e-12, stream=None):
+def hamiltonian(g, U_fund, pi, phi, beta: float, sys: int = EO_PRECOND, tol: float = 1e-12, inner: int = F64,
+                stream=None):
     """(H_pi, S_g, S_f) of Sec. 2.5 for the links g represents (= U_fund)."""
-    Sf = fermion_action(g, sys, phi, tol, stream=stream) if phi is not None else 0.0
+    Sf = fermion_action(g, sys, phi, tol, inner=inner, stream=stream) if phi is not None else 0.0
     return momenta_energy(g.lat, pi, stream), gauge_action(g.lat, U_fund, beta, stream), Sf
 
 
