@@ -392,6 +392,147 @@ def md_trajectory(L: Lat, UF, pi, beta: float, tau: float, nsteps: int, phi_e=No
     return U, p
 
 
+# ---- clover improvement (Sec. 5.1.2, Eqs. clover-term, field-strength-tensor) ----
+
+def _neighbours(L: Lat):
+    """nb[s, x, mu] = lex index of x + s mu (s = 0: +mu, s = 1: -mu), periodic."""
+    dims = [L.dims[i] for i in range(4)]
+    t, x, y, z = np.meshgrid(*[np.arange(d) for d in dims], indexing="ij")
+    c = np.stack([t, x, y, z], axis=-1).reshape(-1, 4)
+    stride = np.array([dims[1] * dims[2] * dims[3], dims[2] * dims[3], dims[3], 1])
+    nb = np.empty((2, len(c), 4), np.int64)
+    for mu in range(4):
+        for s, d in ((0, 1), (1, -1)):
+            e = c.copy()
+            e[:, mu] = (e[:, mu] + d) % dims[mu]
+            nb[s, :, mu] = e @ stride
+    return nb
+
+
+def sigma(mu: int, nu: int) -> np.ndarray:
+    """sigma_mu_nu = (i/2) [gamma_mu, gamma_nu] (Hermitian)."""
+    g1, g2 = gamma(mu), gamma(nu)
+    return 0.5j * (g1 @ g2 - g2 @ g1)
+
+
+def clover_leaves(L: Lat, UR) -> np.ndarray:
+    """Q[x, mu, nu] = the four plaquettes of the (mu, nu) plane with a corner at
+    x (Eq. clover-term), each as the closed loop that starts and ends at x,
+    traversed mu before nu; in the representation of UR (whose boundary signs
+    cancel around every closed loop)."""
+    UR = _c(UR)
+    V, D = UR.shape[0], UR.shape[-1]
+    nb = _neighbours(L)
+    dag = lambda A: np.conj(np.swapaxes(A, -1, -2))
+    mm = lambda *Ms: _chain(Ms)
+    Q = np.zeros((V, 4, 4, D, D), np.complex128)
+    for mu in range(4):
+        for nu in range(4):
+            if mu == nu:
+                continue
+            xp_mu, xp_nu = nb[0, :, mu], nb[0, :, nu]
+            xm_mu, xm_nu = nb[1, :, mu], nb[1, :, nu]
+            xm_mu_p_nu = nb[0, xm_mu, nu]          # x - mu + nu
+            xm_mu_m_nu = nb[1, xm_mu, nu]          # x - mu - nu
+            xm_nu_p_mu = nb[0, xm_nu, mu]          # x - nu + mu
+            U = lambda x, d: UR[x, d]
+            Q[:, mu, nu] = (
+                mm(U(np.arange(V), mu), U(xp_mu, nu), dag(U(xp_nu, mu)), dag(U(np.arange(V), nu)))
+                + mm(U(np.arange(V), nu), dag(U(xm_mu_p_nu, mu)), dag(U(xm_mu, nu)), U(xm_mu, mu))
+                + mm(dag(U(xm_mu, mu)), dag(U(xm_mu_m_nu, nu)), U(xm_mu_m_nu, mu), U(xm_nu, nu))
+                + mm(dag(U(xm_nu, nu)), U(xm_nu, mu), U(xm_nu_p_mu, nu), dag(U(np.arange(V), mu))))
+    return Q
+
+
+def _chain(Ms):
+    out = Ms[0]
+    for M in Ms[1:]:
+        out = np.einsum("...ij,...jk->...ik", out, M)
+    return out
+
+
+def field_strength(L: Lat, UR) -> np.ndarray:
+    """F_mu_nu(x) = (Q_mu_nu(x) - Q_mu_nu(x)^dag) / 8 (Eq. field-strength-tensor)."""
+    Q = clover_leaves(L, UR)
+    return (Q - np.conj(np.swapaxes(Q, -1, -2))) / 8.0
+
+
+def clover_term(L: Lat, UR, csw: float, exponential: bool = False) -> np.ndarray:
+    """The site-diagonal block C(x) [V, 4D, 4D] (index spin * D + colour) of
+    D_ee + D_oo (Sec. 5.1.2):  (4 + m) + csw (i/4) sum_{mu,nu} sigma_mu_nu F_mu_nu,
+    or its exponential form (4 + m) exp(csw / (4 + m) (i/4) sum sigma F)."""
+    F = field_strength(L, UR)
+    V, D = F.shape[0], F.shape[-1]
+    X = np.zeros((V, 4 * D, 4 * D), np.complex128)
+    for mu in range(4):
+        for nu in range(4):
+            if mu != nu:
+                X += 0.25j * np.einsum("st,xab->xsatb", sigma(mu, nu), F[:, mu, nu]).reshape(V, 4 * D, 4 * D)
+    m4 = 4.0 + L.m0
+    I = np.eye(4 * D)
+    if not exponential:
+        return m4 * I + csw * X
+    w, Qe = np.linalg.eigh(csw / m4 * X)
+    return m4 * np.einsum("xij,xj,xkj->xik", Qe, np.exp(w), Qe.conj())
+
+
+def _site_mv(C, psi):
+    V = C.shape[0]
+    return np.einsum("xij,xj->xi", C, psi.reshape(V, -1)).reshape(psi.shape)
+
+
+def dirac_full_clover(L: Lat, UR, C, psi, dagger: bool = False) -> np.ndarray:
+    """D_m with the clover diagonal: C(x) psi(x) + the hopping terms of Eq. D_m^R
+    (C is Hermitian, so D^dag keeps C)."""
+    psi = _c(psi)
+    return dirac_full(L, UR, psi, dagger) - (4.0 + L.m0) * psi + _site_mv(C, psi)
+
+
+def dhat_clover(L: Lat, UR, C, in_e, dagger: bool = False) -> np.ndarray:
+    """Dhat = C_ee - D_eo C_oo^-1 D_oe on even half fields (Sec. 4.3.3 with a
+    site-dependent diagonal); Dhat^dag = C_ee - (D^dag)_eo C_oo^-1 (D^dag)_oe."""
+    e_sites, o_sites = _parity_sites(L)
+    Ce, Co = C[e_sites], C[o_sites]
+    t = hop_parity(L, UR, 1, _c(in_e), dagger)
+    t = np.linalg.solve(Co, t.reshape(len(o_sites), -1)[..., None])[..., 0].reshape(t.shape)
+    return _site_mv(Ce, _c(in_e)) - hop_parity(L, UR, 0, t, dagger)
+
+
+def _parity_sites(L: Lat):
+    """lex indices of the even and the odd sites, in half-index (lex // 2) order."""
+    par = parity_of_sites(L)
+    lex = np.arange(volume(L))
+    return lex[par == 0], lex[par == 1]
+
+
+def cg_apply(apply_A, b, tol: float = 1e-12, max_iter: int = 10000):
+    """Textbook CG on a Hermitian positive definite operator given as a
+    function, restarted from the true residual until |b - A x| / |b| <= tol.
+    Returns (x, converged, iterations, true relative residual)."""
+    b = _c(b)
+    x = np.zeros_like(b)
+    bn = np.linalg.norm(b)
+    k = 0
+    while True:
+        r = b - apply_A(x)
+        rel = np.linalg.norm(r) / bn
+        if rel <= tol or k >= max_iter:
+            return x, rel <= tol, k, rel
+        p = r.copy()
+        rr = np.vdot(r, r).real
+        while k < max_iter:
+            Ap = apply_A(p)
+            alpha = rr / np.vdot(p, Ap).real
+            x = x + alpha * p
+            r = r - alpha * Ap
+            k += 1
+            rr_new = np.vdot(r, r).real
+            if np.sqrt(rr_new) / bn <= tol:
+                break
+            p = r + (rr_new / rr) * p
+            rr = rr_new
+
+
 # ---- parity helpers (pure index bookkeeping) ----
 
 def parity_of_sites(L: Lat) -> np.ndarray:
