@@ -115,6 +115,28 @@ hr_status hr_represent_gauge(const hr_lattice_desc *lat, const void *U_fund,
  * update, Sec. 5.3.1: "only necessary after every gauge update"). */
 hr_status hr_gauge_update(hr_gauge *g, const void *U_fund, void *stream);
 
+/* Clover improvement (Sec. 5.1.2) and exponential clover (Sec. 5.1.3): the
+ * diagonal of D_m becomes, per site,
+ *   HR_CLOVER_PLAIN:  (4+m) + csw (i/4) sum_{mu,nu} sigma_mu_nu F_mu_nu
+ *   HR_CLOVER_EXP:    (4+m) exp(csw/(4+m) (i/4) sum_{mu,nu} sigma_mu_nu F_mu_nu)
+ * with sigma_mu_nu = (i/2)[gamma_mu, gamma_nu] and F_mu_nu = (Q - Q^dag)/8,
+ * Q the four plaquettes of the (mu,nu) plane through x (Eq. clover-term),
+ * each as the closed loop through x, in the fermion representation.
+ * hr_gauge_set_clover builds the term (and its inverse) from U_fund (the
+ * links g was built from; hr_gauge_update rebuilds it with the new links);
+ * HR_CLOVER_NONE removes it.  With a clover term: hr_dirac_apply /
+ * hr_dirac_dagger give D_m (HR_FULL) and Dhat = C_ee - D_eo C_oo^-1 D_oe
+ * (HR_EO_PRECOND) in FP64 and FP32 (the hopping blocks HR_EVEN / HR_ODD
+ * are unchanged); hr_cg_solve and hr_cg_solve_multishift solve with it
+ * (inner FP64 or FP32, x started from 0); hr_cg_solve_batched,
+ * hr_cg_solve_force and hr_dirac_force return HR_ERR_UNSUPPORTED (the
+ * clover term's force is not provided).  Needs FP64 links in g; the FP32
+ * records are built when g holds FP32 links.
+ * Errors: HR_ERR_NONFINITE if a clover block is singular. */
+typedef enum { HR_CLOVER_NONE = 0, HR_CLOVER_PLAIN = 1, HR_CLOVER_EXP = 2 } hr_clover_mode;
+hr_status hr_gauge_set_clover(hr_gauge *g, const void *U_fund, double csw,
+                              hr_clover_mode mode, void *stream);
+
 /* Chooses STORED, REBUILD or AUTO links for later operator calls on g.
  * HR_ERR_INVALID if that storage (both, for AUTO) was not requested at
  * creation.  The force always reads the stored FP64 links. */

@@ -31,7 +31,7 @@ PAIRS = [(2, "HR_FUND"), (2, "HR_ADJ"), (2, "HR_SYM"), (3, "HR_FUND"), (3, "HR_A
 
 def _units():
     units = []
-    for src in ("hr_api.cu", "hr_cg.cu", "hr_mscg.cu", "hr_hmc.cu", "hr_blas.cu", "hr_static.cu", "hr_tune.cu"):
+    for src in ("hr_api.cu", "hr_cg.cu", "hr_mscg.cu", "hr_hmc.cu", "hr_clover.cu", "hr_blas.cu", "hr_static.cu", "hr_tune.cu"):
         units.append((CSRC / src, OBJDIR / (Path(src).stem + ".o"), []))
     for n, rep in PAIRS:
         tag = f"{n}_{rep.lower()[3:]}"

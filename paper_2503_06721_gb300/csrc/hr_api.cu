@@ -469,7 +469,10 @@ hr_status hr_represent_gauge(const hr_lattice_desc *lat, const void *U_fund, uns
 hr_status hr_gauge_update(hr_gauge *g, const void *U_fund, void *stream)
 {
     if (!g || !U_fund) { set_error("hr_gauge_update: NULL argument"); return HR_ERR_INVALID; }
-    return represent_dispatch(*g, reinterpret_cast<const double2 *>(U_fund), reinterpret_cast<cudaStream_t>(stream));
+    hr_status st = represent_dispatch(*g, reinterpret_cast<const double2 *>(U_fund), reinterpret_cast<cudaStream_t>(stream));
+    // the clover term follows the links
+    if (st == HR_OK && g->clover_mode) st = clover_build(g, U_fund, reinterpret_cast<cudaStream_t>(stream));
+    return st;
 }
 
 hr_status hr_gauge_set_link_mode(hr_gauge *g, hr_link_mode mode)
@@ -500,6 +503,8 @@ hr_status hr_gauge_destroy(hr_gauge *g)
             if (g->fund[P][par]) cudaFree(g->fund[P][par]);
         }
     if (g->TR) cudaFree(g->TR);
+    for (int P = 0; P < HR_NPREC; P++)
+        if (g->cl[P]) cudaFree(g->cl[P]);
     if (g->err) cudaFree(g->err);
     if (g->ws) cudaFree(g->ws);
     if (g->scr) cudaFree(g->scr);
@@ -533,12 +538,22 @@ static hr_status apply_impl(const hr_gauge *g, hr_parity par, hr_prec prec, cons
         FieldView vi = make_view(const_cast<void *>(in), vh, D, prec), vo = make_view(out, vh, D, prec);
         return hop(g, prec, par == HR_EVEN ? 0 : 1, dagger, vi, vo, nullptr, -0.5, 0.0, nrhs, s, EPI_STORE);
     }
+    if (g->clover_mode && prec != HR_F64 && prec != HR_F32) {
+        set_error("with a clover term D_m and Dhat are available in FP64 and FP32 only");
+        return HR_ERR_UNSUPPORTED;
+    }
     if (par == HR_FULL) {
         FieldView fi = make_view(const_cast<void *>(in), 2 * vh, D, prec), fo = make_view(out, 2 * vh, D, prec);
         for (int p = 0; p < 2; p++) {
             FieldView ih = half_view(fi, 1 - p, vh, D, prec), dh = half_view(fi, p, vh, D, prec);
             FieldView oh = half_view(fo, p, vh, D, prec);
-            st = hop(g, prec, p, dagger, ih, oh, &dh, -0.5, m4, nrhs, s, EPI_STORE);
+            if (g->clover_mode) {
+                // out_p = C_pp in_p + hops (C is Hermitian: the same for D^dag)
+                st = clover_apply(g, prec, p, 0, dh, oh, nrhs, s);
+                if (st == HR_OK) st = hop(g, prec, p, dagger, ih, oh, &oh, -0.5, 1.0, nrhs, s, EPI_STORE);
+            } else {
+                st = hop(g, prec, p, dagger, ih, oh, &dh, -0.5, m4, nrhs, s, EPI_STORE);
+            }
             if (st != HR_OK) return st;
         }
         return HR_OK;
@@ -551,6 +566,13 @@ static hr_status apply_impl(const hr_gauge *g, hr_parity par, hr_prec prec, cons
     FieldView vt = make_view(g->ws, vh, D, prec);
     st = hop(g, prec, 1, dagger, vi, vt, nullptr, -0.5, 0.0, nrhs, s, EPI_STORE);
     if (st != HR_OK) return st;
+    if (g->clover_mode) {
+        // Dhat = C_ee - D_eo C_oo^-1 D_oe
+        st = clover_apply(g, prec, 1, 1, vt, vt, nrhs, s);
+        if (st == HR_OK) st = clover_apply(g, prec, 0, 0, vi, vo, nrhs, s);
+        if (st != HR_OK) return st;
+        return hop(g, prec, 0, dagger, vt, vo, &vo, 0.5, 1.0, nrhs, s, EPI_STORE);
+    }
     return hop(g, prec, 0, dagger, vt, vo, &vi, 0.5, m4 * m4, nrhs, s, EPI_STORE);
 }
 
@@ -631,6 +653,10 @@ hr_status hr_field_dot(const hr_lattice_desc *lat, hr_parity par, hr_prec prec, 
 hr_status hr_dirac_force(const hr_gauge *g, hr_parity sys, const void *X, const void *Y, double coeff, void *F,
                          void *stream)
 {
+    if (g && g->clover_mode) {
+        set_error("hr_dirac_force: the clover term's force is not provided");
+        return HR_ERR_UNSUPPORTED;
+    }
     if (!g || !X || !Y || !F) { set_error("hr_dirac_force: NULL argument"); return HR_ERR_INVALID; }
     if (!(g->prec_mask & (1u << HR_F64)) || !g->rep[HR_F64][0]) {
         set_error("hr_dirac_force needs FP64 stored represented links in the handle");

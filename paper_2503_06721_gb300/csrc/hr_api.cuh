@@ -58,6 +58,14 @@ hr_status tune_hops(hr_gauge *g, int P, int nrhs, cudaStream_t stream);
 hr_status force_full(const hr_gauge *g, const FieldView &fx, const FieldView &fy, double c, double *F,
                      cudaStream_t s);
 
+// the clover diagonal (hr_clover.cu): build C and C^-1 from U_F for the
+// handle's clover_mode and csw (FP64 and, if the handle holds FP32, FP32);
+// apply out = C_pp in (kind 0) or C_pp^-1 in (kind 1) on the sites of parity
+// p (in == out allowed)
+hr_status clover_build(hr_gauge *g, const void *U_fund, cudaStream_t s);
+hr_status clover_apply(const hr_gauge *g, int P, int parity, int kind, const FieldView &in, const FieldView &out,
+                       int nrhs, cudaStream_t s);
+
 // number of kernel launches counted so far (graph contents counted when they run)
 long long launch_counter();
 

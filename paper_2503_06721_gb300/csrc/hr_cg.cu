@@ -661,6 +661,17 @@ extern "C" hr_status hr_cg_solve(const hr_gauge *g, hr_parity sys, const void *b
         return HR_ERR_INVALID;
     }
     if (b == x) { set_error("hr_cg_solve: b and x must not overlap"); return HR_ERR_INVALID; }
+    if (g->clover_mode) {
+        // the fused CG kernels carry the constant diagonal (4+m); with the
+        // site-dependent clover diagonal the solve runs on the multi-shift
+        // engine with the single shift 0 (the same CG iterates)
+        if (params->use_initial_guess || params->residual != HR_F64) {
+            set_error("hr_cg_solve with a clover term: start from x = 0 with FP64 residuals");
+            return HR_ERR_UNSUPPORTED;
+        }
+        const double zero = 0.0;
+        return hr_cg_solve_multishift(g, sys, b, x, nrhs, &zero, 1, params, res, stream);
+    }
     hr_status st = check_params(g, sys, params);
     if (st != HR_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -679,6 +690,10 @@ extern "C" hr_status hr_cg_solve_force(const hr_gauge *g, hr_parity sys, const v
         return HR_ERR_INVALID;
     }
     if (b == x) { set_error("hr_cg_solve_force: b and x must not overlap"); return HR_ERR_INVALID; }
+    if (g->clover_mode) {
+        set_error("hr_cg_solve_force: the clover term's force is not provided");
+        return HR_ERR_UNSUPPORTED;
+    }
     hr_status st = check_params(g, sys, params);
     if (st != HR_OK) return st;
     if (!g->rep[HR_F64][0]) {
@@ -721,6 +736,10 @@ extern "C" hr_status hr_cg_solve_batched(int n_inst, const hr_gauge *const *g, h
         if (!g[i] || !b[i] || !x[i] || nrhs[i] < 1 || b[i] == x[i]) {
             set_error("hr_cg_solve_batched: instance %d has a NULL pointer, nrhs < 1 or b == x", i);
             return HR_ERR_INVALID;
+        }
+        if (g[i]->clover_mode) {
+            set_error("hr_cg_solve_batched: instance %d has a clover term (use hr_cg_solve)", i);
+            return HR_ERR_UNSUPPORTED;
         }
         for (int j = 0; j < i; j++)
             if (g[j] == g[i]) {

@@ -37,6 +37,11 @@ struct hr_gauge {
     int force_variant;    // >= 0: every launch uses this variant (testing)
     signed char auto_mode[HR_NPREC];   // HR_LINKS_AUTO: the tuned mode per precision, -1 = not tuned
     int autotune;         // 1: the solver tunes its inner precision before iterating
+    // clover diagonal (Sec. 5.1.2-5.1.3): mode, coefficient and the C / C^-1 records
+    // per precision (FP64 and FP32 only), AoSoA [kind][parity][tile][block][entry][lane]
+    int clover_mode;
+    double csw;
+    void *cl[HR_NPREC];
 };
 
 namespace hr {

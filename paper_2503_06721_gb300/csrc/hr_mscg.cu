@@ -508,6 +508,39 @@ hr_status ms_apply(const MsCtx &c, int P, int nsys, const FieldView &v, const Fi
     hr_status st;
     const int D = c.D;
     const int epi_n = qa ? EPI_STORE_NORM : EPI_STORE;
+    if (c.g->clover_mode) {
+        // the site-dependent diagonal C (Hermitian): D = C + hops,
+        // Dhat = C_ee - D_eo C_oo^-1 D_oe, each diagonal product written first
+        // and taken up by the hop as its diagonal term
+        if (c.sys == HR_EO_PRECOND) {
+            for (int dag = 0; dag < 2; dag++) {
+                const FieldView &src = dag ? q : v;
+                const FieldView &dst = dag ? w : q;
+                st = hop(c.g, P, 1, dag, src, t, nullptr, -0.5, 0.0, nsys, c.s, EPI_STORE, sc);
+                if (st == HR_OK) st = clover_apply(c.g, P, 1, 1, t, t, nsys, c.s);
+                if (st == HR_OK) st = clover_apply(c.g, P, 0, 0, src, dst, nsys, c.s);
+                if (st == HR_OK)
+                    st = hop(c.g, P, 0, dag, t, dst, &dst, 0.5, 1.0, nsys, c.s, dag ? EPI_STORE : epi_n, sc,
+                             FIN_WRITE, nullptr, dag ? nullptr : qa);
+                if (st != HR_OK) return st;
+            }
+            return HR_OK;
+        }
+        for (int dag = 0; dag < 2; dag++) {
+            const FieldView &src = dag ? q : v;
+            const FieldView &dst = dag ? w : q;
+            for (int par = 0; par < 2; par++) {
+                FieldView in = half_view(src, 1 - par, c.vh, D, P), dg = half_view(src, par, c.vh, D, P);
+                FieldView o = half_view(dst, par, c.vh, D, P);
+                st = clover_apply(c.g, P, par, 0, dg, o, nsys, c.s);
+                if (st == HR_OK)
+                    st = hop(c.g, P, par, dag, in, o, &o, -0.5, 1.0, nsys, c.s, dag ? EPI_STORE : epi_n, sc, FIN_WRITE,
+                             nullptr, dag ? nullptr : (par == 0 ? qa : qb));
+                if (st != HR_OK) return st;
+            }
+        }
+        return HR_OK;
+    }
     if (c.sys == HR_EO_PRECOND) {
         st = hop(c.g, P, 1, 0, v, t, nullptr, -0.5, 0.0, nsys, c.s, EPI_STORE, sc);
         if (st == HR_OK) st = hop(c.g, P, 0, 0, t, q, &v, 0.5, c.m4 * c.m4, nsys, c.s, epi_n, sc, FIN_WRITE, nullptr, qa);

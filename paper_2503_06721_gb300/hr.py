@@ -39,7 +39,7 @@ EXPORTS = ["hr_represent_gauge", "hr_gauge_update", "hr_gauge_set_link_mode", "h
            "hr_dirac_apply", "hr_dirac_dagger",
            "hr_cg_solve", "hr_cg_solve_batched", "hr_cg_solve_force", "hr_cg_solve_multishift",
            "hr_field_lincomb", "hr_dirac_force", "hr_gauge_action", "hr_gauge_force", "hr_link_update",
-           "hr_momenta_energy", "hr_md_trajectory", "hr_rep_dim", "hr_generators",
+           "hr_momenta_energy", "hr_md_trajectory", "hr_gauge_set_clover", "hr_rep_dim", "hr_generators",
            "hr_status_string", "hr_last_error", "hr_launch_count"]
 
 
@@ -76,6 +76,7 @@ class MdStats(ctypes.Structure):
 
 
 MD_LEAPFROG, MD_OMELYAN2 = 0, 1
+CLOVER_NONE, CLOVER_PLAIN, CLOVER_EXP = 0, 1, 2
 T_FUND = 0.5
 
 
@@ -124,6 +125,7 @@ def load():
         "hr_link_update": (I, [LP, P, P, D, P]),
         "hr_momenta_energy": (I, [LP, P, ctypes.POINTER(D), P]),
         "hr_md_trajectory": (I, [P, P, P, P, ctypes.POINTER(MdParams), ctypes.POINTER(MdStats), P]),
+        "hr_gauge_set_clover": (I, [P, P, D, I, P]),
         "hr_cg_solve_force": (I, [P, I, P, P, ctypes.POINTER(CgParams), ctypes.POINTER(CgResult), P, D, P, P]),
         "hr_rep_dim": (I, [I, I]),
         "hr_generators": (I, [I, ctypes.POINTER(D)]),
@@ -346,6 +348,12 @@ class Gauge:
 
     def update(self, U_fund, stream=None):
         _check(load().hr_gauge_update(self.handle, _ptr(U_fund.contiguous()), _stream(stream)))
+
+    def set_clover(self, U_fund, csw: float, mode: int = CLOVER_PLAIN, stream=None):
+        """Adds the clover (or exponential clover) diagonal built from U_fund
+        (hr_gauge_set_clover); mode CLOVER_NONE removes it."""
+        _check(load().hr_gauge_set_clover(self.handle, _ptr(U_fund.contiguous() if U_fund is not None else None),
+                                          float(csw), int(mode), _stream(stream)))
 
     def set_link_mode(self, mode: int):
         _check(load().hr_gauge_set_link_mode(self.handle, mode))
