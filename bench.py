@@ -346,6 +346,7 @@ def run_ours(args, rank, world, local_rank):
     # time to 1e-10: plain FP64 CG vs defect correction with low-precision inner solves
     cg = None
     multishift = None
+    clover = None
     if rank == 0 and not args.no_cg_compare:
         g2 = hr.Gauge(lat, U, precs=("f64", "f32", "f16", "bf16", "df64"), stored=True, rebuild=True)
         g2.set_link_mode(hr.LINKS_AUTO)
@@ -371,6 +372,8 @@ def run_ours(args, rank, world, local_rank):
             cg[name]["speedup_vs_fp64"] = round(cg["fp64"]["ms"] / cg[name]["ms"], 2)
         if not args.no_multishift:
             multishift = multishift_compare(hr, g2, phi, stream, wl.m0)
+        if not args.no_clover:
+            clover = clover_measure(hr, g2, U, phi, stream)
         g2.close()
 
     hmc = None
@@ -419,6 +422,7 @@ def run_ours(args, rank, world, local_rank):
             "batched": batched,
             "multishift": multishift,
             "hmc": hmc,
+            "clover": clover,
             "cpu_baseline": cpu,
         }
         print(json.dumps(out), flush=True)
@@ -480,6 +484,50 @@ def multishift_compare(hr, g, phi, stream, m0):
     torch.cuda.synchronize()
     out["rational_apply_mixed_fp32_ms"] = round(e0.elapsed_time(e1), 2)
     del x, y
+    return out
+
+
+def clover_measure(hr, g, U, phi, stream, csw=1.0):
+    """The clover-improved operator (Sec. 5.1.2) on the bench lattice: the
+    build of C and C^-1 (FP64, both parities, FP64 and FP32 records), one Dhat
+    = C_ee - D_eo C_oo^-1 D_oe application in FP32 and FP64 against the plain
+    Dhat, and a solve of Dhat^dag Dhat x = phi to 1e-10 with FP32 inner
+    iterations and FP64 correction."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=1):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {"csw": csw}
+    x32 = phi.to(torch.complex64)
+    for name, prec, xin in (("dhat_f32_ms", hr.F32, x32), ("dhat_f64_ms", hr.F64, phi)):
+        out["plain_" + name] = round(timed(lambda: g.apply(hr.EO_PRECOND, prec, xin), 10), 3)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    g.set_clover(U, csw, hr.CLOVER_PLAIN)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["build_ms"] = round(e0.elapsed_time(e1), 2)
+    for name, prec, xin in (("dhat_f32_ms", hr.F32, x32), ("dhat_f64_ms", hr.F64, phi)):
+        out["clover_" + name] = round(timed(lambda: g.apply(hr.EO_PRECOND, prec, xin), 10), 3)
+    g.cg_solve(hr.EO_PRECOND, phi, tol=1e-3, inner=hr.F32, check=False)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    x, res, st = g.cg_solve(hr.EO_PRECOND, phi, tol=TOL, inner=hr.F32, inner_tol=1e-5, check=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["cg_mixed_fp32"] = {"ms": round(e0.elapsed_time(e1), 2), "iters": res[0]["iters"],
+                            "outer": res[0]["outer_iters"], "true_rel_residual": res[0]["true_rel_residual"],
+                            "status": hr.STATUS.get(st, st)}
+    g.set_clover(None, 0.0, hr.CLOVER_NONE)
     return out
 
 
@@ -759,6 +807,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-FP64 solve comparison")
     ap.add_argument("--no-hmc", action="store_true", help="skip the HMC trajectory measurement")
+    ap.add_argument("--no-clover", action="store_true", help="skip the clover-operator measurement")
     ap.add_argument("--no-multishift", action="store_true",
                     help="skip the multi-shift-vs-sequential shifted solve comparison")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
