@@ -386,6 +386,11 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.empty_cache()
         batched = batched_compare(hr, synth, dev, stream)
 
+    largen = None
+    if rank == 0 and not args.no_largen:
+        torch.cuda.empty_cache()
+        largen = largen_sweep(hr, synth, dev, stream)
+
     out = None
     if rank == 0:
         cpu = None if (world > 1 or args.no_cpu_baseline) else cpu_baseline(wl, budget_s=args.cpu_seconds)
@@ -423,6 +428,7 @@ def run_ours(args, rank, world, local_rank):
             "multishift": multishift,
             "hmc": hmc,
             "clover": clover,
+            "large_n_fund_f32_deo": largen,
             "cpu_baseline": cpu,
         }
         print(json.dumps(out), flush=True)
@@ -484,6 +490,46 @@ def multishift_compare(hr, g, phi, stream, m0):
     torch.cuda.synchronize()
     out["rational_apply_mixed_fp32_ms"] = round(e0.elapsed_time(e1), 2)
     del x, y
+    return out
+
+
+def largen_sweep(hr, synth, dev, stream, dims=(48, 24, 24, 24)):
+    """D_eo bandwidth of the fundamental representation as N grows (Sec. 6.2,
+    the large-N study): SU(3) and SU(4) with the site-parallel kernel (the
+    tuned variant), SU(5), SU(6) and SU(8) with the colour-parallel kernel; FP32
+    stored links, m0 = -0.1, links exp(i 0.4 H), a 24^3 x 48 lattice (every
+    launch moves 0.26-1.5 GB, above L2).  GB/s of compulsory bytes."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"lattice": list(dims)}
+    for N in (3, 4, 5, 6, 8):
+        lat = hr.Lattice(N, "FUND", dims, (-1, 1, 1, 1), -0.1)
+        U = synth.random_links(lat.volume, N, 0.4, 2503067210 + 40 + N, device=dev)
+        g = hr.Gauge(lat, U, precs=("f64", "f32"))
+        del U
+        vh = lat.volume // 2
+        x = synth.gaussian_spinor(vh, N, 3, device=dev).to(torch.complex64)
+        y = torch.empty_like(x)
+        if N <= 4:
+            g.tune(hr.F32)
+        for _ in range(3):
+            g.apply(hr.EVEN, hr.F32, x, out=y)
+        torch.cuda.synchronize()
+        reps = 20
+        e0.record(stream)
+        for _ in range(reps):
+            g.apply(hr.EVEN, hr.F32, x, out=y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        byts = hop_bytes(N, False, hr.F32, vh)
+        out[f"su{N}"] = {"kernel": ("colour-parallel" if N >= 5 else
+                                    f"site-parallel variant {g.hop_variant(hr.F32, hr.EPI_STORE, 1)}"),
+                         "ms": round(ms, 4), "GBs": round(byts / (ms * 1e-3) / 1e9, 1),
+                         "frac_of_hbm": round(byts / (ms * 1e-3) / 1e9 / _peaks()[0], 4)}
+        g.close()
+        del x, y
+        torch.cuda.empty_cache()
     return out
 
 
@@ -808,6 +854,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-FP64 solve comparison")
     ap.add_argument("--no-hmc", action="store_true", help="skip the HMC trajectory measurement")
     ap.add_argument("--no-clover", action="store_true", help="skip the clover-operator measurement")
+    ap.add_argument("--no-largen", action="store_true", help="skip the large-N fundamental D_eo sweep")
     ap.add_argument("--no-multishift", action="store_true",
                     help="skip the multi-shift-vs-sequential shifted solve comparison")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

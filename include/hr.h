@@ -81,7 +81,11 @@ typedef enum {
 typedef enum { HR_LINKS_STORED = 0, HR_LINKS_REBUILD = 1, HR_LINKS_AUTO = 2 } hr_link_mode;
 
 typedef struct {
-    int N;          /* SU(N), 2 <= N <= 4 */
+    int N;          /* SU(N): N = 2, 3, 4 with the representations FUND,
+                       ADJ, SYM (N = 2, 3), ASYM (N = 3, 4); N = 5, 6, 8 with
+                       FUND only, run by the colour-parallel hopping kernel
+                       (Sec. 6.2): FP64 / FP32 stored links, solves on the
+                       multi-shift engine, no batched or fused solve + force */
     hr_rep rep;
     int dims[4];    /* T, X, Y, Z (all even) */
     int bc[4];      /* +1 periodic, -1 antiperiodic fermion boundary (Sec. 5.3.1) */

@@ -27,6 +27,8 @@ NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "--expt-relaxed-constexpr", "-Xc
 PRECS = ["HR_F64", "HR_F32", "HR_F16", "HR_BF16", "HR_DF64"]
 PAIRS = [(2, "HR_FUND"), (2, "HR_ADJ"), (2, "HR_SYM"), (3, "HR_FUND"), (3, "HR_ADJ"), (3, "HR_SYM"),
          (3, "HR_ASYM"), (4, "HR_FUND"), (4, "HR_ASYM")]
+# large-N fundamental pairs: colour-parallel hopping kernel, FP64 and FP32
+LARGE_PAIRS = [(5, "HR_FUND"), (6, "HR_FUND"), (8, "HR_FUND")]
 
 
 def _units():
@@ -41,6 +43,13 @@ def _units():
             units.append((CSRC / "hr_dslash_inst.cu",
                           OBJDIR / f"hr_dslash_inst_{tag}_{prec.lower()[3:]}.o",
                           [f"-DHR_INST_N={n}", f"-DHR_INST_REP={rep}", f"-DHR_INST_P={prec}"]))
+    for n, rep in LARGE_PAIRS:
+        tag = f"{n}_{rep.lower()[3:]}"
+        units.append((CSRC / "hr_gauge_inst.cu", OBJDIR / f"hr_gauge_inst_{tag}.o",
+                      [f"-DHR_INST_N={n}", f"-DHR_INST_REP={rep}"]))
+        for prec in ("HR_F64", "HR_F32"):
+            units.append((CSRC / "hr_dslash_colour.cu", OBJDIR / f"hr_dslash_colour_{n}_{prec.lower()[3:]}.o",
+                          [f"-DHR_INST_N={n}", f"-DHR_INST_P={prec}"]))
     return units
 
 

@@ -47,10 +47,21 @@ long long launch_counter() { return g_launches.load(); }
     extern template hr_status force_launch<N_, R_>(const ForceParams &, cudaStream_t);
 HR_PAIRS(HR_DECL)
 
+// large-N fundamental pairs: represent and force as above, the hop by the
+// colour-parallel kernel (FP64 and FP32, stored links)
+#define HR_LARGE_PAIRS(X) X(5, HR_FUND) X(6, HR_FUND) X(8, HR_FUND)
+#define HR_DECL_LARGE(N_, R_)                                                                          \
+    extern template hr_status launch_colour<N_, HR_F64>(const HopParams &, int, cudaStream_t);         \
+    extern template hr_status launch_colour<N_, HR_F32>(const HopParams &, int, cudaStream_t);         \
+    extern template hr_status represent_launch<N_, R_>(const hr_gauge &, const double2 *, cudaStream_t); \
+    extern template hr_status force_launch<N_, R_>(const ForceParams &, cudaStream_t);
+HR_LARGE_PAIRS(HR_DECL_LARGE)
+
 bool pair_supported(int N, int rep)
 {
 #define HR_SUP(N_, R_) if (N == N_ && rep == R_) return true;
     HR_PAIRS(HR_SUP)
+    HR_LARGE_PAIRS(HR_SUP)
 #undef HR_SUP
     return false;
 }
@@ -70,6 +81,18 @@ hr_status hop_dispatch(int N, int rep, int P, const HopParams &prm, bool rebuild
     }
     HR_PAIRS(HR_HOP)
 #undef HR_HOP
+#define HR_HOP_LARGE(N_, R_)                                                                          \
+    if (N == N_ && rep == R_) {                                                                       \
+        if (rebuild || (P != HR_F64 && P != HR_F32)) {                                                \
+            set_error("SU(%d): the colour-parallel kernel takes stored FP64 or FP32 links", N);       \
+            return HR_ERR_UNSUPPORTED;                                                                \
+        }                                                                                             \
+        (void)variant;                                                                                \
+        return P == HR_F64 ? launch_colour<N_, HR_F64>(prm, epi, stream)                              \
+                           : launch_colour<N_, HR_F32>(prm, epi, stream);                             \
+    }
+    HR_LARGE_PAIRS(HR_HOP_LARGE)
+#undef HR_HOP_LARGE
     set_error("SU(%d) representation %d not compiled", N, rep);
     return HR_ERR_UNSUPPORTED;
 }
@@ -79,6 +102,7 @@ hr_status represent_dispatch(const hr_gauge &g, const double2 *UF, cudaStream_t 
 #define HR_REPR(N_, R_) \
     if (g.lat.N == N_ && g.lat.rep == R_) return represent_launch<N_, R_>(g, UF, stream);
     HR_PAIRS(HR_REPR)
+    HR_LARGE_PAIRS(HR_REPR)
 #undef HR_REPR
     set_error("SU(%d) representation %d not compiled", g.lat.N, (int)g.lat.rep);
     return HR_ERR_UNSUPPORTED;
@@ -89,6 +113,7 @@ hr_status force_dispatch(const hr_gauge &g, const ForceParams &fp, cudaStream_t 
 #define HR_FRC(N_, R_) \
     if (g.lat.N == N_ && g.lat.rep == R_) return force_launch<N_, R_>(fp, stream);
     HR_PAIRS(HR_FRC)
+    HR_LARGE_PAIRS(HR_FRC)
 #undef HR_FRC
     set_error("SU(%d) representation %d not compiled", g.lat.N, (int)g.lat.rep);
     return HR_ERR_UNSUPPORTED;
@@ -310,6 +335,7 @@ hr_status hop(const hr_gauge *g, int P, int out_parity, int dagger, const FieldV
 
 unsigned hop_variants_of(const hr_gauge *g, int P)
 {
+    if (large_n(g)) return 0x1u;   // the colour-parallel kernel only
     if (P == HR_F64 || P == HR_DF64) return 0x1u;
     return g->D <= 4 ? 0x1Bu : 0x1Fu;   // as hop_variant_mask for the handle's pair
 }

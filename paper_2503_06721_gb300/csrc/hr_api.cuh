@@ -42,6 +42,10 @@ hr_status hop(const hr_gauge *g, int P, int out_parity, int dagger, const FieldV
               double *red_out = nullptr, const FieldView *r = nullptr, const FieldView *x = nullptr,
               const FieldView *p = nullptr, int variant = -1);
 
+// the large-N fundamental pairs (N >= 5), run by the colour-parallel hopping
+// kernel without a fused CG-update epilogue
+inline bool large_n(const hr_gauge *g) { return g->lat.N >= 5; }
+
 // whether operator launches in precision P read fundamental links (rebuild)
 bool rebuild_for(const hr_gauge *g, int P);
 

@@ -306,6 +306,7 @@ static inline dim3 grid_of(const BlasParams &bp)
     case 2: { constexpr int DD = 2; BODY; } break; \
     case 3: { constexpr int DD = 3; BODY; } break; \
     case 4: { constexpr int DD = 4; BODY; } break; \
+    case 5: { constexpr int DD = 5; BODY; } break; \
     case 6: { constexpr int DD = 6; BODY; } break; \
     case 8: { constexpr int DD = 8; BODY; } break; \
     default: set_error("representation dimension %d not compiled", D_); return HR_ERR_UNSUPPORTED; \

@@ -661,10 +661,11 @@ extern "C" hr_status hr_cg_solve(const hr_gauge *g, hr_parity sys, const void *b
         return HR_ERR_INVALID;
     }
     if (b == x) { set_error("hr_cg_solve: b and x must not overlap"); return HR_ERR_INVALID; }
-    if (g->clover_mode) {
-        // the fused CG kernels carry the constant diagonal (4+m); with the
-        // site-dependent clover diagonal the solve runs on the multi-shift
-        // engine with the single shift 0 (the same CG iterates)
+    if (g->clover_mode || large_n(g)) {
+        // the fused CG kernels carry the constant diagonal (4+m) and exist for
+        // the site-parallel hops; with the site-dependent clover diagonal, or
+        // for the large-N pairs (colour-parallel hops), the solve runs on the
+        // multi-shift engine with the single shift 0 (the same CG iterates)
         if (params->use_initial_guess || params->residual != HR_F64) {
             set_error("hr_cg_solve with a clover term: start from x = 0 with FP64 residuals");
             return HR_ERR_UNSUPPORTED;
@@ -690,8 +691,9 @@ extern "C" hr_status hr_cg_solve_force(const hr_gauge *g, hr_parity sys, const v
         return HR_ERR_INVALID;
     }
     if (b == x) { set_error("hr_cg_solve_force: b and x must not overlap"); return HR_ERR_INVALID; }
-    if (g->clover_mode) {
-        set_error("hr_cg_solve_force: the clover term's force is not provided");
+    if (g->clover_mode || large_n(g)) {
+        set_error("hr_cg_solve_force: not provided with a clover term or for N >= 5 (use hr_cg_solve + "
+                  "hr_dirac_force for the latter)");
         return HR_ERR_UNSUPPORTED;
     }
     hr_status st = check_params(g, sys, params);
@@ -737,8 +739,8 @@ extern "C" hr_status hr_cg_solve_batched(int n_inst, const hr_gauge *const *g, h
             set_error("hr_cg_solve_batched: instance %d has a NULL pointer, nrhs < 1 or b == x", i);
             return HR_ERR_INVALID;
         }
-        if (g[i]->clover_mode) {
-            set_error("hr_cg_solve_batched: instance %d has a clover term (use hr_cg_solve)", i);
+        if (g[i]->clover_mode || large_n(g[i])) {
+            set_error("hr_cg_solve_batched: instance %d has a clover term or N >= 5 (use hr_cg_solve)", i);
             return HR_ERR_UNSUPPORTED;
         }
         for (int j = 0; j < i; j++)

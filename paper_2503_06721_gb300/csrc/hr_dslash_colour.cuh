@@ -1,0 +1,150 @@
+// hr_dslash_colour.cuh -- the colour-parallel hopping kernel for large N.
+//
+// Sec. 6.2 (single-GPU tests) reports that a kernel holding a whole site per
+// thread spills registers once the representation grows (N > 4 in the
+// fundamental), and that a kernel in which each thread computes one colour
+// component of one output site keeps the per-thread state small: the local
+// work becomes D_R-length dot products of a link row with the projected
+// neighbour spinor instead of D_R x D_R matrix-vector products.
+//
+// Here a thread block is one 32-site tile times N colour rows (thread
+// (row a, lane j) = site j of the tile, colour a), so every link-row load of
+// a warp reads 32 consecutive lanes of the AoSoA link record.  Per hop each
+// thread issues, together, the loads of its own colour of the neighbour
+// spinor and of the 16-byte chunks that hold its link row, one hop ahead of
+// their use (software pipelining), forms its component of the two projected
+// half-spinors h_r = (1 -+ gamma_mu) psi in shared memory, and after a
+// barrier forms chi_r[a] = sum_b U[a][b] h_r[b] of its own row and
+// reconstructs its four spin components.  Stored links only (the boundary
+// signs are in the records), FP64 and FP32, epilogues store and
+// store + |out|^2.
+#pragma once
+
+#include "hr_dslash.cuh"
+
+namespace hr {
+
+template <int N, int P, int EPI>
+__global__ void __launch_bounds__(32 * N) hop_colour_kernel(const HopParams prm)
+{
+    using R = typename St<P>::R;
+    using C2 = typename std::conditional<P == HR_F64, double2, float2>::type;
+    using LIO = LinkIO<P, false, N * N>;
+    const Geom &g = prm.g;
+    const int rhs = blockIdx.y;
+    if (prm.state && cg_idle(prm.state[rhs])) return;   // uniform per block
+    const int j = threadIdx.x & 31;      // site within the tile
+    const int a = threadIdx.x >> 5;      // colour row
+    const long tile = blockIdx.x;
+    const long i = tile * HR_TILE + j;
+    const bool active = i < g.vh;
+    const R sg = prm.dagger ? (R)-1 : (R)1;
+    constexpr int NC = 4 * N;                                 // complex numbers per spinor record
+    constexpr int MAXC = (N + LIO::VPC - 1) / LIO::VPC + 1;   // chunks a row can touch
+    __shared__ cx<R> hs[2][N][HR_TILE];
+
+    cx<R> acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    Site st;
+    if (active) st = site_of(g, i, prm.out_parity);
+    const char *in = prm.in.data + (size_t)rhs * prm.in.rhs_stride;
+    auto comp = [&](const char *base, long site, int s) -> cx<R> {
+        const C2 v = *reinterpret_cast<const C2 *>(base + ((size_t)site * NC + (size_t)s * N + a) * sizeof(C2));
+        return {(R)v.x, (R)v.y};
+    };
+    // the row's elements e = a N .. a N + N - 1 lie in chunks c0 .. c0 + nch - 1
+    const int e0 = a * N, c0 = e0 / LIO::VPC, nch = (e0 + N - 1) / LIO::VPC - c0 + 1;
+    // the loads of hop k: own colour of the neighbour spinor, the link row
+    auto fetch = [&](int k, cx<R> (&psi)[4], uint4 (&lv)[MAXC]) {
+        if (!active) return;
+        const long nb = neighbour(g, st, k & 3, k < 4 ? +1 : -1);
+#pragma unroll
+        for (int s = 0; s < 4; s++) psi[s] = comp(in, nb, s);
+        const uint4 *lp = LIO::slot_ptr(prm.links, tile, k, j) + (size_t)c0 * HR_TILE;
+#pragma unroll
+        for (int cc = 0; cc < MAXC; cc++)
+            if (cc < nch) lv[cc] = __ldg(lp + (size_t)cc * HR_TILE);
+    };
+    cx<R> psi[2][4];
+    uint4 lv[2][MAXC];
+    fetch(0, psi[0], lv[0]);
+    // software pipeline: the loads of hop k + 1 are in flight while hop k is formed
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const int cur = k & 1;
+        const int mu = k & 3;
+        const bool fwd = k < 4;
+        const R sp = fwd ? -sg : sg;
+        if (active) {
+#pragma unroll
+            for (int r = 0; r < 2; r++)
+                hs[r][a][j] = psi[cur][r] + sp * ipow(ephase(mu, r), psi[cur][2 + eperm(mu, r)]);
+        }
+        if (k + 1 < 8) fetch(k + 1, psi[cur ^ 1], lv[cur ^ 1]);
+        __syncthreads();
+        if (active) {
+            cx<R> chi[2] = {{0, 0}, {0, 0}};
+#pragma unroll
+            for (int cc = 0; cc < MAXC; cc++) {
+                if (cc >= nch) break;
+#pragma unroll
+                for (int q = 0; q < LIO::VPC; q++) {
+                    const int b = (c0 + cc) * LIO::VPC + q - e0;
+                    if (b < 0 || b >= N) continue;
+                    const cx<R> u = LIO::cunpack(lv[cur][cc], q);
+                    cmac(chi[0], u, hs[0][b][j]);
+                    cmac(chi[1], u, hs[1][b][j]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 2; r++) {
+                acc[r] = acc[r] + chi[r];
+                acc[2 + eperm(mu, r)] = acc[2 + eperm(mu, r)] + sp * ipow(4 - ephase(mu, r), chi[r]);
+            }
+        }
+        __syncthreads();
+    }
+    const R ca = (R)prm.a, cb = (R)prm.b;
+    R n2 = 0;
+    if (active) {
+        if (prm.diag.data) {
+            const char *dg = prm.diag.data + (size_t)rhs * prm.diag.rhs_stride;
+#pragma unroll
+            for (int s = 0; s < 4; s++) acc[s] = axpby(ca, acc[s], cb, comp(dg, i, s));
+        } else {
+#pragma unroll
+            for (int s = 0; s < 4; s++) acc[s] = ca * acc[s];
+        }
+        char *out = prm.out.data + (size_t)rhs * prm.out.rhs_stride;
+#pragma unroll
+        for (int s = 0; s < 4; s++) {
+            C2 v;
+            v.x = acc[s].re;
+            v.y = acc[s].im;
+            *reinterpret_cast<C2 *>(out + ((size_t)i * 4 * N + (size_t)s * N + a) * sizeof(C2)) = v;
+            norm_acc(n2, acc[s]);
+        }
+    }
+    if constexpr (EPI == EPI_STORE_NORM) {
+        double v[1] = {(double)n2};
+        double tot[1];
+        if (grid_reduce<1>(v, prm.partials + (size_t)rhs * gridDim.x, prm.counters + rhs, gridDim.x, blockIdx.x, tot))
+            hop_finalize(prm, rhs, tot[0]);
+    }
+}
+
+template <int N, int P>
+hr_status launch_colour(const HopParams &prm, int epi, cudaStream_t stream)
+{
+    const dim3 grid((unsigned)prm.g.ntiles, (unsigned)prm.nrhs);
+    switch (epi) {
+    case EPI_STORE: hop_colour_kernel<N, P, EPI_STORE><<<grid, 32 * N, 0, stream>>>(prm); break;
+    case EPI_STORE_NORM: hop_colour_kernel<N, P, EPI_STORE_NORM><<<grid, 32 * N, 0, stream>>>(prm); break;
+    default:
+        set_error("the colour-parallel hopping kernel has no fused CG-update epilogue");
+        return HR_ERR_UNSUPPORTED;
+    }
+    HR_LAUNCH_CHECK("hop_colour_kernel");
+    return HR_OK;
+}
+
+}  // namespace hr

@@ -68,6 +68,10 @@ struct ForceParams {
 template <int N, int REP>
 hr_status force_launch(const ForceParams &fp, cudaStream_t stream);
 
+// the colour-parallel hopping kernel of the large-N pairs (hr_dslash_colour.cuh)
+template <int N, int P>
+hr_status launch_colour(const HopParams &prm, int epi, cudaStream_t stream);
+
 // precision dispatch of the hop kernel for a runtime (N, rep)
 hr_status hop_dispatch(int N, int rep, int P, const HopParams &prm, bool rebuild, int epi, int variant,
                        cudaStream_t stream);

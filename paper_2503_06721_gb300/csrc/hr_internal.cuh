@@ -22,7 +22,7 @@
 
 #include "hr.h"
 
-#define HR_MAX_N 4
+#define HR_MAX_N 8
 #define HR_TILE 32
 #define HR_NPREC 5   // F64, F32, F16, BF16, DF64
 

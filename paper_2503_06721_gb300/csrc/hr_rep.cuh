@@ -32,8 +32,9 @@ __host__ __device__ constexpr int gen_col(int N, int a, int e)
 }
 __host__ __device__ inline double diag_norm(int l)
 {
-    // 1 / sqrt(2 l (l+1)) for l = 1, 2, 3
-    return l == 1 ? 0.5 : l == 2 ? 0.28867513459481288225 : 0.20412414523193150818;
+    // 1 / sqrt(2 l (l+1))
+    return l == 1 ? 0.5 : l == 2 ? 0.28867513459481288225 : l == 3 ? 0.20412414523193150818
+                                                                    : 1.0 / sqrt(2.0 * l * (l + 1));
 }
 template <class R>
 __host__ __device__ inline cx<R> gen_val(int N, int a, int e)

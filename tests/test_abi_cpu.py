@@ -37,7 +37,8 @@ def test_pure_host_calls(lib):
     assert lib.hr_rep_dim(3, hr.SYM) == 6
     assert lib.hr_rep_dim(3, hr.ADJ) == 8
     assert lib.hr_rep_dim(4, hr.ASYM) == 6
-    assert lib.hr_rep_dim(7, hr.FUND) == -1
+    assert lib.hr_rep_dim(9, hr.FUND) == -1
+    assert lib.hr_rep_dim(8, hr.FUND) == 8
     assert b"HR_ERR_INVALID" in lib.hr_status_string(-1)
     lat = hr.Lattice(3, "SYM", (8, 4, 4, 4))
     assert hr.field_bytes(lat, hr.EVEN, hr.F64) == 256 * 4 * 6 * 16
@@ -51,7 +52,7 @@ def test_pure_host_calls(lib):
 def test_generators_match_oracle(lib, oracle_mod):
     import numpy as np
     from paper_2503_06721_gb300 import hr
-    for N in (2, 3, 4):
+    for N in (2, 3, 4, 5, 6, 8):
         np.testing.assert_allclose(hr.generators(N), oracle_mod.generators(N), atol=1e-16)
 
 
@@ -66,9 +67,12 @@ def test_argument_errors_without_gpu(lib):
     assert lib.hr_represent_gauge(ctypes.byref(d), ctypes.c_void_p(16), 1, 1, None,
                                   ctypes.byref(out)) == -1
     d.dims[3] = 4
-    d.N = 5
+    d.N = 9
     assert lib.hr_represent_gauge(ctypes.byref(d), ctypes.c_void_p(16), 1, 1, None,
                                   ctypes.byref(out)) == -1
+    d.N = 5   # SU(5): the fundamental only
+    assert lib.hr_represent_gauge(ctypes.byref(d), ctypes.c_void_p(16), 1, 1, None,
+                                  ctypes.byref(out)) == -7
     d.N = 4
     d.rep = hr.ADJ   # SU(4) adjoint (D = 15) is not compiled
     assert lib.hr_represent_gauge(ctypes.byref(d), ctypes.c_void_p(16), 1, 1, None,

@@ -42,7 +42,7 @@ def test_gamma_clifford_and_gamma5(oracle_mod):
     np.testing.assert_allclose(g5, np.diag([1, 1, -1, -1]), atol=1e-15)
 
 
-@pytest.mark.parametrize("N", [2, 3, 4])
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 6, 8])
 def test_generators(oracle_mod, N):
     T = oracle_mod.generators(N)
     assert T.shape == (N * N - 1, N, N)
