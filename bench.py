@@ -494,7 +494,7 @@ def multishift_compare(hr, g, phi, stream, m0):
 
 
 def largen_sweep(hr, synth, dev, stream, dims=(48, 24, 24, 24)):
-    """D_eo bandwidth of the fundamental representation as N grows (Sec. 6.2,
+    """D_eo bandwidth of the fundamental representation as N grows (Sec. 8.2,
     the large-N study): SU(3) and SU(4) with the site-parallel kernel (the
     tuned variant), SU(5), SU(6) and SU(8) with the colour-parallel kernel; FP32
     stored links, m0 = -0.1, links exp(i 0.4 H), a 24^3 x 48 lattice (every

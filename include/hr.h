@@ -84,7 +84,7 @@ typedef struct {
     int N;          /* SU(N): N = 2, 3, 4 with the representations FUND,
                        ADJ, SYM (N = 2, 3), ASYM (N = 3, 4); N = 5, 6, 8 with
                        FUND only, run by the colour-parallel hopping kernel
-                       (Sec. 6.2): FP64 / FP32 stored links, solves on the
+                       (Sec. 8.2): FP64 / FP32 stored links, solves on the
                        multi-shift engine, no batched or fused solve + force */
     hr_rep rep;
     int dims[4];    /* T, X, Y, Z (all even) */

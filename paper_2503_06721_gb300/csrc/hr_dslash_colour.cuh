@@ -1,6 +1,6 @@
 // hr_dslash_colour.cuh -- the colour-parallel hopping kernel for large N.
 //
-// Sec. 6.2 (single-GPU tests) reports that a kernel holding a whole site per
+// Sec. 8.2 (single-GPU efficiency) reports that a kernel holding a whole site per
 // thread spills registers once the representation grows (N > 4 in the
 // fundamental), and that a kernel in which each thread computes one colour
 // component of one output site keeps the per-thread state small: the local

@@ -1,5 +1,5 @@
 """GPU parity of the large-N fundamental pairs SU(5), SU(6), SU(8), run by the
-colour-parallel hopping kernel (one thread per colour row of a site, Sec. 6.2),
+colour-parallel hopping kernel (one thread per colour row of a site, Sec. 8.2),
 with the oracle: every parity selector, plain and dagger, FP64 and FP32, on a
 lattice that spans several 32-site tiles and ends in a ragged tail; solves
 (which run on the multi-shift engine for these pairs); the fermion force; and
