@@ -27,7 +27,7 @@ struct hr_gauge {
     // that no field temporary ever overwrites the zeroed tickets
     char *scr;
     size_t scr_bytes;
-    int *err;             // device flag set by a bounded wait that gave up
+    int *err;             // device counter of failures found by kernels (singular clover blocks)
     void *pinned;         // host-mapped pinned mailbox for the solver's small host transfers
     size_t pinned_bytes;
     int device;

@@ -256,6 +256,9 @@ WORKLOADS = {
                                      -0.25, 0.4, seed=2503067213),
     "su4_asym_48x24x24x24": Workload("su4_asym_48x24x24x24", 4, "ASYM", (48, 24, 24, 24),
                                      -0.25, 0.4, seed=2503067213),
+    # SU(8) fundamental 24^3 x 48: the colour-parallel (large-N) kernel
+    "su8_fund_48x24x24x24": Workload("su8_fund_48x24x24x24", 8, "FUND", (48, 24, 24, 24),
+                                     -0.1, 0.4, seed=2503067218),
     # SU(3) sextet 16^3 x 32, force / differentiation configuration
     "su3_sym_32x16x16x16": Workload("su3_sym_32x16x16x16", 3, "SYM", (32, 16, 16, 16), -0.3,
                                     0.4, seed=2503067214),
