@@ -7,15 +7,18 @@
 // work becomes D_R-length dot products of a link row with the projected
 // neighbour spinor instead of D_R x D_R matrix-vector products.
 //
-// Here a thread block is one 32-site tile times N colour rows (thread
-// (row a, lane j) = site j of the tile, colour a), so every link-row load of
-// a warp reads 32 consecutive lanes of the AoSoA link record.  Per hop each
-// thread issues, together, the loads of its own colour of the neighbour
-// spinor and of the 16-byte chunks that hold its link row, one hop ahead of
-// their use (software pipelining), forms its component of the two projected
-// half-spinors h_r = (1 -+ gamma_mu) psi in shared memory, and after a
-// barrier forms chi_r[a] = sum_b U[a][b] h_r[b] of its own row and
-// reconstructs its four spin components.  Stored links only (the boundary
+// Here a thread block is one 32-site tile times N colour rows.  For the
+// link rows the threads are (row a, site j), site fastest, so every link-row
+// load of a warp reads 32 consecutive lanes of the AoSoA link record; for
+// the site-major spinors they are (site, colour), colour fastest, so that
+// consecutive threads read and write consecutive numbers of one record.  Per
+// hop each thread issues the loads of its neighbour-spinor colour and of the
+// 16-byte chunks of its link row one hop ahead of their use (software
+// pipelining), forms its component of the two projected half-spinors
+// h_r = (1 -+ gamma_mu) psi in shared memory, and after a barrier forms
+// chi_r[a] = sum_b U[a][b] h_r[b] of its own row and reconstructs its four
+// spin components; the results return through shared memory to the spinor
+// mapping for the stores.  Stored links only (the boundary
 // signs are in the records), FP64 and FP32, epilogues store and
 // store + |out|^2.
 #pragma once
@@ -24,8 +27,15 @@
 
 namespace hr {
 
+// resident blocks per SM asked of the register allocator in FP32: the
+// largest count whose register cap does not make ptxas spill (N = 5: 4
+// blocks of 160 threads; N = 6: 4 of 192; N = 8: 3 of 256, all <= 80
+// registers per thread); FP64 unconstrained
+template <int N, int P>
+constexpr int colour_minb() { return P == HR_F64 ? 1 : (N <= 6 ? 4 : 3); }
+
 template <int N, int P, int EPI>
-__global__ void __launch_bounds__(32 * N) hop_colour_kernel(const HopParams prm)
+__global__ void __launch_bounds__(32 * N, colour_minb<N, P>()) hop_colour_kernel(const HopParams prm)
 {
     using R = typename St<P>::R;
     using C2 = typename std::conditional<P == HR_F64, double2, float2>::type;
@@ -33,36 +43,48 @@ __global__ void __launch_bounds__(32 * N) hop_colour_kernel(const HopParams prm)
     const Geom &g = prm.g;
     const int rhs = blockIdx.y;
     if (prm.state && cg_idle(prm.state[rhs])) return;   // uniform per block
-    const int j = threadIdx.x & 31;      // site within the tile
-    const int a = threadIdx.x >> 5;      // colour row
     const long tile = blockIdx.x;
-    const long i = tile * HR_TILE + j;
-    const bool active = i < g.vh;
+    // link mapping (site fastest): thread = (row a, site j)
+    const int j = threadIdx.x & 31;
+    const int a = threadIdx.x >> 5;
+    // spinor mapping (colour fastest): thread = (site jA, colour aA), so that
+    // consecutive threads read and write consecutive numbers of one record
+    const int jA = threadIdx.x / N;
+    const int aA = threadIdx.x % N;
+    const bool active = tile * HR_TILE + j < g.vh;
+    const long iA = tile * HR_TILE + jA;
+    const bool activeA = iA < g.vh;
     const R sg = prm.dagger ? (R)-1 : (R)1;
     constexpr int NC = 4 * N;                                 // complex numbers per spinor record
     constexpr int MAXC = (N + LIO::VPC - 1) / LIO::VPC + 1;   // chunks a row can touch
-    __shared__ cx<R> hs[2][N][HR_TILE];
+    // one padding column: the colour-fastest accesses of a warp (same site,
+    // consecutive colours) then fall in different banks
+    __shared__ cx<R> hs[2][N][HR_TILE + 1];
+    __shared__ cx<R> os[4][N][HR_TILE + 1];
 
     cx<R> acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    Site st;
-    if (active) st = site_of(g, i, prm.out_parity);
+    Site stA;
+    if (activeA) stA = site_of(g, iA, prm.out_parity);
     const char *in = prm.in.data + (size_t)rhs * prm.in.rhs_stride;
     auto comp = [&](const char *base, long site, int s) -> cx<R> {
-        const C2 v = *reinterpret_cast<const C2 *>(base + ((size_t)site * NC + (size_t)s * N + a) * sizeof(C2));
+        const C2 v = *reinterpret_cast<const C2 *>(base + ((size_t)site * NC + (size_t)s * N + aA) * sizeof(C2));
         return {(R)v.x, (R)v.y};
     };
     // the row's elements e = a N .. a N + N - 1 lie in chunks c0 .. c0 + nch - 1
     const int e0 = a * N, c0 = e0 / LIO::VPC, nch = (e0 + N - 1) / LIO::VPC - c0 + 1;
-    // the loads of hop k: own colour of the neighbour spinor, the link row
+    // the loads of hop k: colour aA of site jA's neighbour, link row a of site j
     auto fetch = [&](int k, cx<R> (&psi)[4], uint4 (&lv)[MAXC]) {
-        if (!active) return;
-        const long nb = neighbour(g, st, k & 3, k < 4 ? +1 : -1);
+        if (activeA) {
+            const long nb = neighbour(g, stA, k & 3, k < 4 ? +1 : -1);
 #pragma unroll
-        for (int s = 0; s < 4; s++) psi[s] = comp(in, nb, s);
-        const uint4 *lp = LIO::slot_ptr(prm.links, tile, k, j) + (size_t)c0 * HR_TILE;
+            for (int s = 0; s < 4; s++) psi[s] = comp(in, nb, s);
+        }
+        if (active) {
+            const uint4 *lp = LIO::slot_ptr(prm.links, tile, k, j) + (size_t)c0 * HR_TILE;
 #pragma unroll
-        for (int cc = 0; cc < MAXC; cc++)
-            if (cc < nch) lv[cc] = __ldg(lp + (size_t)cc * HR_TILE);
+            for (int cc = 0; cc < MAXC; cc++)
+                if (cc < nch) lv[cc] = __ldg(lp + (size_t)cc * HR_TILE);
+        }
     };
     cx<R> psi[2][4];
     uint4 lv[2][MAXC];
@@ -74,10 +96,10 @@ __global__ void __launch_bounds__(32 * N) hop_colour_kernel(const HopParams prm)
         const int mu = k & 3;
         const bool fwd = k < 4;
         const R sp = fwd ? -sg : sg;
-        if (active) {
+        if (activeA) {
 #pragma unroll
             for (int r = 0; r < 2; r++)
-                hs[r][a][j] = psi[cur][r] + sp * ipow(ephase(mu, r), psi[cur][2 + eperm(mu, r)]);
+                hs[r][aA][jA] = psi[cur][r] + sp * ipow(ephase(mu, r), psi[cur][2 + eperm(mu, r)]);
         }
         if (k + 1 < 8) fetch(k + 1, psi[cur ^ 1], lv[cur ^ 1]);
         __syncthreads();
@@ -103,25 +125,33 @@ __global__ void __launch_bounds__(32 * N) hop_colour_kernel(const HopParams prm)
         }
         __syncthreads();
     }
+    // back to the spinor mapping for the epilogue and the coalesced stores
+    if (active)
+#pragma unroll
+        for (int s = 0; s < 4; s++) os[s][a][j] = acc[s];
+    __syncthreads();
     const R ca = (R)prm.a, cb = (R)prm.b;
     R n2 = 0;
-    if (active) {
+    if (activeA) {
+        cx<R> o[4];
+#pragma unroll
+        for (int s = 0; s < 4; s++) o[s] = os[s][aA][jA];
         if (prm.diag.data) {
             const char *dg = prm.diag.data + (size_t)rhs * prm.diag.rhs_stride;
 #pragma unroll
-            for (int s = 0; s < 4; s++) acc[s] = axpby(ca, acc[s], cb, comp(dg, i, s));
+            for (int s = 0; s < 4; s++) o[s] = axpby(ca, o[s], cb, comp(dg, iA, s));
         } else {
 #pragma unroll
-            for (int s = 0; s < 4; s++) acc[s] = ca * acc[s];
+            for (int s = 0; s < 4; s++) o[s] = ca * o[s];
         }
         char *out = prm.out.data + (size_t)rhs * prm.out.rhs_stride;
 #pragma unroll
         for (int s = 0; s < 4; s++) {
             C2 v;
-            v.x = acc[s].re;
-            v.y = acc[s].im;
-            *reinterpret_cast<C2 *>(out + ((size_t)i * 4 * N + (size_t)s * N + a) * sizeof(C2)) = v;
-            norm_acc(n2, acc[s]);
+            v.x = o[s].re;
+            v.y = o[s].im;
+            *reinterpret_cast<C2 *>(out + ((size_t)iA * NC + (size_t)s * N + aA) * sizeof(C2)) = v;
+            norm_acc(n2, o[s]);
         }
     }
     if constexpr (EPI == EPI_STORE_NORM) {
