@@ -290,6 +290,9 @@ typedef struct {
  * The gauge handle must hold F64 links, and the inner precision's links
  * when params->inner != HR_F64.  BLOCKS the calling thread until every
  * right-hand side has converged or failed.
+ * With a clover term (hr_gauge_set_clover) or for N >= 5 the solve runs on
+ * the multi-shift engine with the single shift 0 (same CG iterates; inner
+ * FP64 or FP32, x started from 0, FP64 residuals).
  * Errors: HR_ERR_NOT_CONVERGED (x holds the last iterate),
  *         HR_ERR_NONFINITE, HR_ERR_INVALID, HR_ERR_NOMEM, HR_ERR_CUDA. */
 hr_status hr_cg_solve(const hr_gauge *g, hr_parity sys, const void *b,
