@@ -430,6 +430,10 @@ hr_status hr_represent_gauge(const hr_lattice_desc *lat, const void *U_fund, uns
     if (!U_fund) { set_error("hr_represent_gauge: U_fund is NULL"); return HR_ERR_INVALID; }
     if (prec_mask == 0 || (prec_mask & ~0x1Fu)) { set_error("bad prec_mask 0x%x", prec_mask); return HR_ERR_INVALID; }
     if (link_modes == 0 || (link_modes & ~0x3u)) { set_error("bad link_modes 0x%x", link_modes); return HR_ERR_INVALID; }
+    if (lat->N >= 5 && link_modes != (1u << HR_LINKS_STORED)) {
+        set_error("SU(%d): the colour-parallel kernel reads stored links only (link_modes = STORED)", lat->N);
+        return HR_ERR_UNSUPPORTED;
+    }
     hr_gauge *g = new hr_gauge;
     memset(g, 0, sizeof *g);
     memset(g->tuned, -1, sizeof g->tuned);

@@ -70,9 +70,14 @@ def test_argument_errors_without_gpu(lib):
     d.N = 9
     assert lib.hr_represent_gauge(ctypes.byref(d), ctypes.c_void_p(16), 1, 1, None,
                                   ctypes.byref(out)) == -1
-    d.N = 5   # SU(5): the fundamental only
+    d.N = 5   # SU(5): the fundamental only, stored links only
     assert lib.hr_represent_gauge(ctypes.byref(d), ctypes.c_void_p(16), 1, 1, None,
                                   ctypes.byref(out)) == -7
+    d.rep = hr.FUND
+    assert lib.hr_represent_gauge(ctypes.byref(d), ctypes.c_void_p(16), 1, 2, None,
+                                  ctypes.byref(out)) == -7
+    assert b"stored links only" in lib.hr_last_error()
+    d.rep = hr.SYM
     d.N = 4
     d.rep = hr.ADJ   # SU(4) adjoint (D = 15) is not compiled
     assert lib.hr_represent_gauge(ctypes.byref(d), ctypes.c_void_p(16), 1, 1, None,
