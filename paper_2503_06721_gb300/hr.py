@@ -15,6 +15,7 @@ import ctypes
 from dataclasses import dataclass
 from pathlib import Path
 
+import numpy as np
 import torch
 
 _LIB_PATH = Path(__file__).resolve().parent / "_lib" / "libhr.so"
@@ -322,6 +323,29 @@ def hamiltonian(g, U_fund, pi, phi, beta: float, sys: int = EO_PRECOND, tol: flo
     """(H_pi, S_g, S_f) of Sec. 2.5 for the links g represents (= U_fund)."""
     Sf = fermion_action(g, sys, phi, tol, inner=inner, stream=stream) if phi is not None else 0.0
     return momenta_energy(g.lat, pi, stream), gauge_action(g.lat, U_fund, beta, stream), Sf
+
+
+def hmc_trajectory(g, U_fund, pi, eta, beta: float, tau: float, nsteps: int, u_accept: float,
+                   integrator: int = MD_OMELYAN2, sys: int = EO_PRECOND, tol: float = 1e-10,
+                   inner: int = F64, inner_tol: float = 1e-5, stream=None) -> dict:
+    """One HMC update (Sec. 2.5): pseudofermion heat bath phi = Dhat^dag eta
+    (D^dag eta for sys = FULL), H before, one MD trajectory, H after, and the
+    Metropolis test exp(-dH) > u_accept.  pi (heat-bath momenta, pi^a ~
+    N(0, 1/T_F)), eta (Gaussian) and u_accept (uniform in [0, 1)) are the
+    caller's random draws.  On acceptance U_fund holds the new links; on
+    rejection it is restored.  g represents U_fund on return."""
+    phi = g.apply(sys, F64, eta, dagger=True)
+    U0 = U_fund.clone()
+    H0 = hamiltonian(g, U_fund, pi, phi, beta, sys, tol=min(tol, 1e-11), inner=inner, stream=stream)
+    st = md_trajectory(g, U_fund, pi, phi, beta, tau, nsteps, integrator, sys, tol, inner, inner_tol,
+                       stream=stream)
+    H1 = hamiltonian(g, U_fund, pi, phi, beta, sys, tol=min(tol, 1e-11), inner=inner, stream=stream)
+    dH = sum(H1) - sum(H0)
+    accepted = bool(u_accept < min(1.0, float(np.exp(-dH))))
+    if not accepted:
+        U_fund.copy_(U0)
+        g.update(U_fund, stream=stream)
+    return dict(dH=dH, accepted=accepted, H0=H0, H1=H1, **st)
 
 
 def _prec_mask(precs) -> int:

@@ -119,3 +119,35 @@ def test_md_energy_violation_and_reversibility(hr, oracle_mod):
     U2, p2, _, _ = _gpu_traj(hr, lat, U1, -p1, phi, 0.5, 8, 1)
     assert np.abs(U2 - U).max() < 1e-9
     assert np.abs(p2 + pi).max() < 1e-8 * np.abs(pi).max()
+
+
+def test_hmc_update_matches_oracle(hr, oracle_mod):
+    """One HMC update (heat bath phi = Dhat^dag eta, H, trajectory, H,
+    Metropolis) against the oracle on the same random draws; a forced
+    rejection restores the links and their representation."""
+    lat, L, U, pi, _ = _hmc_case(hr, oracle_mod, False)
+    eta = H.spinor(lat.volume // 2, lat.D, 307)
+    UR = oracle_mod.represent_field(L, U)
+    phi = oracle_mod.dhat(L, UR, eta, dagger=True)
+    H0 = sum(oracle_mod.hamiltonian(L, U, pi, BETA, phi))
+    Uo, po = oracle_mod.md_trajectory(L, U, pi, BETA, 0.4, 4, phi, "omelyan")
+    dHo = sum(oracle_mod.hamiltonian(L, Uo, po, BETA, phi)) - H0
+    Ud = G.to_gpu(U)
+    g = hr.Gauge(lat, Ud, precs=("f64",))
+    try:
+        r = hr.hmc_trajectory(g, Ud, torch.as_tensor(pi).cuda().clone(), G.to_gpu(eta), BETA, 0.4, 4,
+                              u_accept=0.0, tol=1e-13)
+        assert r["accepted"] and abs(r["dH"] - dHo) < 1e-8 * max(1.0, abs(dHo)), (r["dH"], dHo)
+        np.testing.assert_allclose(Ud.cpu().numpy(), Uo, rtol=0, atol=1e-10)
+        # forced rejection: the links and the operator return to the start
+        U1 = Ud.clone()
+        r = hr.hmc_trajectory(g, Ud, torch.as_tensor(pi).cuda().clone(), G.to_gpu(eta), BETA, 0.4, 4,
+                              u_accept=2.0, tol=1e-13)
+        assert not r["accepted"]
+        assert torch.equal(Ud, U1)
+        psi = H.spinor(lat.volume // 2, lat.D, 311)
+        y = g.apply(hr.EVEN, hr.F64, G.to_gpu(psi)).cpu().numpy()
+        want = oracle_mod.hop_parity(L, oracle_mod.represent_field(L, U1.cpu().numpy()), 0, psi)
+        assert G.rel(y, want) <= 1e-13
+    finally:
+        g.close()
