@@ -22,8 +22,9 @@ r on [lo, hi].
 
 This is host-side set-up (numpy / scipy); nothing here runs on the GPU.  In
 double precision the evaluated error stops falling near 1e-13 (degree 20 and
-above on [1e-4, 1]); max_rel_err is measured on the evaluated partial
-fractions, so it reports that floor rather than the exact-arithmetic value.
+above on [1e-4, 1]); max_rel_err is the spread of the evaluated factored
+form over its sample points, so near that floor it reports the floor
+rather than the exact-arithmetic error.
 """
 from __future__ import annotations
 
