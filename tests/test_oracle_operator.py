@@ -102,7 +102,7 @@ def _dense(oracle_mod, L, UR, V, D, dagger=False):
     return M
 
 
-@pytest.mark.parametrize("N,rep", [(2, "ADJ"), (3, "SYM"), (3, "ADJ"), (4, "ASYM"), (5, "FUND")])
+@pytest.mark.parametrize("N,rep", [(2, "ADJ"), (3, "SYM"), (3, "ADJ"), (4, "ASYM"), (5, "FUND"), (8, "FUND")])
 def test_dense_2x2x2x2(oracle_mod, N, rep):
     dims = (2, 2, 2, 2)
     V = 16
