@@ -102,6 +102,8 @@ def _load():
             "or_num_threads": (I, []),
             "or_hop_sites": (None, [LP, P, I, P, P, ctypes.c_long, P, I]),
             "or_hop_local": (None, [LP, P, P, P, P, I]),
+            "or_hop_local_rep": (None, [LP, P, P, P, P, I]),
+            "or_represent_links": (None, [I, I, ctypes.c_long, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -213,20 +215,33 @@ def hop_sites(L: Lat, UF, out_parity: int, in_half, sites, dagger: bool = False)
     return out
 
 
-def hop_local(L: Lat, coords, Ulinks, psi, dagger: bool = False) -> np.ndarray:
+def hop_local(L: Lat, coords, Ulinks, psi, dagger: bool = False, represented: bool = False) -> np.ndarray:
     """Hopping term at output sites from gathered data: coords[n, 4] (t,x,y,z),
-    Ulinks[n, 8, N, N] fundamental links U(x,mu) / U(x-mu,mu), psi[n, 8, 4, D]
-    neighbour spinors.  Returns [n, 4, D]."""
+    Ulinks[n, 8, N, N] fundamental links U(x,mu) / U(x-mu,mu) (represented =
+    True: Ulinks[n, 8, D, D] = R of those links, without boundary signs),
+    psi[n, 8, 4, D] neighbour spinors.  Returns [n, 4, D]."""
     coords = np.ascontiguousarray(coords, dtype=np.int32)
     Ulinks, psi = _c(Ulinks), _c(psi)
     D = rep_dim(L.N, L.rep)
     n = coords.shape[0]
     out = np.zeros((n, 4, D), np.complex128)
-    f = _load().or_hop_local
+    f = _load().or_hop_local_rep if represented else _load().or_hop_local
     for k in range(n):
         f(ctypes.byref(L), coords[k].ctypes.data_as(ctypes.c_void_p), _p(Ulinks[k]), _p(psi[k]),
           out[k].ctypes.data_as(ctypes.c_void_p), int(dagger))
     return out
+
+
+def represent_links(N: int, rep, U) -> np.ndarray:
+    """R(U[k]) for a stack of N x N matrices U[..., N, N] (no boundary signs)."""
+    rep = REP_NAMES.get(rep, rep) if isinstance(rep, str) else rep
+    D = rep_dim(N, rep)
+    U = _c(U)
+    lead = U.shape[:-2]
+    n = int(np.prod(lead)) if lead else 1
+    R = np.zeros(lead + (D, D), np.complex128)
+    _load().or_represent_links(N, rep, n, _p(U), _p(R))
+    return R
 
 
 def _sum(name, a) -> float:

@@ -476,18 +476,18 @@ void or_hop_sites(const or_lat *L, const orc *UF, int out_parity,
     }
 }
 
-void or_hop_local(const or_lat *L, const int c[4], const orc *Ulinks,
-                  const orc *psi, orc *out, int dagger)
+void or_hop_local_rep(const or_lat *L, const int c[4], const orc *Rlinks,
+                      const orc *psi, orc *out, int dagger)
 {
-    int N = L->N, D = or_rep_dim(L->N, L->rep);
+    int D = or_rep_dim(L->N, L->rep);
     orc gam[4][16];
     load_gammas(gam);
     double sg = dagger ? -1.0 : 1.0;
-    orc R[OR_MAXD * OR_MAXD], chi[4 * OR_MAXD];
+    orc chi[4 * OR_MAXD];
     for (int q = 0; q < 4 * D; q++) out[q] = 0;
     for (int k = 0; k < 8; k++) {
         int mu = k & 3, dir = k < 4 ? +1 : -1;
-        or_represent_link(N, L->rep, Ulinks + (size_t)k * N * N, R);
+        const orc *R = Rlinks + (size_t)k * D * D;
         int cown = dir > 0 ? c[mu] : (c[mu] - 1 + L->dims[mu]) % L->dims[mu];
         double sign = (L->bc[mu] == -1 && cown == L->dims[mu] - 1) ? -1.0 : 1.0;
         const orc *p = psi + (size_t)k * 4 * D;
@@ -506,6 +506,24 @@ void or_hop_local(const or_lat *L, const int c[4], const orc *Ulinks,
                 out[s * D + r] += -0.5 * v;
             }
     }
+}
+
+void or_hop_local(const or_lat *L, const int c[4], const orc *Ulinks,
+                  const orc *psi, orc *out, int dagger)
+{
+    int N = L->N, D = or_rep_dim(L->N, L->rep);
+    orc R[8 * OR_MAXD * OR_MAXD];
+    for (int k = 0; k < 8; k++)
+        or_represent_link(N, L->rep, Ulinks + (size_t)k * N * N, R + (size_t)k * D * D);
+    or_hop_local_rep(L, c, R, psi, out, dagger);
+}
+
+void or_represent_links(int N, int rep, long n, const orc *U, orc *R)
+{
+    int D = or_rep_dim(N, rep);
+#pragma omp parallel for schedule(static)
+    for (long k = 0; k < n; k++)
+        or_represent_link(N, rep, U + (size_t)k * N * N, R + (size_t)k * D * D);
 }
 
 /* ------------------------------------------------------------------ */

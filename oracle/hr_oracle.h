@@ -97,6 +97,13 @@ void or_hop_sites(const or_lat *L, const orc *UF, int out_parity,
  * with the boundary signs of or_represent_field; lower signs for dagger. */
 void or_hop_local(const or_lat *L, const int c[4], const orc *Ulinks,
                   const orc *psi, orc *out, int dagger);
+/* The same from represented links: Rlinks[8][D][D] = R(U) of the 8 links
+ * above (without boundary signs; the sign is applied from the coordinates,
+ * as in or_hop_local), e.g. rounded copies of the stored links. */
+void or_hop_local_rep(const or_lat *L, const int c[4], const orc *Rlinks,
+                      const orc *psi, orc *out, int dagger);
+/* R[k] = or_represent_link(U[k]) for k < n. */
+void or_represent_links(int N, int rep, long n, const orc *U, orc *R);
 
 /* ---- reductions (Sec. 4.1.1, Algorithms FastTwoSum .. DoubleDoubleSum) ---- */
 void   or_fast_two_sum(double a, double b, double *s, double *c);

@@ -246,6 +246,12 @@ def test_hop_local_matches_full(oracle_mod):
             Ul[n, k] = UF[x if k < 4 else nb, mu]
             ps[n, k] = psi[nb]
     np.testing.assert_allclose(oracle_mod.hop_local(L, coords, Ul, ps), full[xs], atol=1e-14)
+    # the represented-link form, given R of the same links, is the same hopping term
+    Rl = oracle_mod.represent_links(N, rep, Ul)
+    np.testing.assert_allclose(oracle_mod.hop_local(L, coords, Rl, ps, represented=True), full[xs],
+                               atol=1e-14)
+    np.testing.assert_allclose(oracle_mod.hop_local(L, coords, Rl, ps, dagger=True, represented=True),
+                               (oracle_mod.dirac_full(L, UR, psi, True) - 4.0 * psi)[xs], atol=1e-14)
 
 
 def oracle_mod_neighbour(dims, lex, mu, d):
