@@ -213,8 +213,10 @@ hr_status hr_field_convert(const hr_lattice_desc *lat, hr_parity par,
                            hr_prec dst_prec, void *dst, int nrhs, void *stream);
 
 /* <a, b> = sum conj(a_i) b_i over each right-hand side, accumulated with
- * compensated (double-double) sums (Sec. 4.1.1).  out is a HOST array of
- * 2*nrhs doubles (re, im); the call synchronises the stream. */
+ * compensated (double-double) sums (Sec. 4.1.1).  par: HR_EVEN, HR_ODD or
+ * HR_EO_PRECOND (V/2 sites) or HR_FULL (V sites); other values give
+ * HR_ERR_INVALID.  out is a HOST array of 2*nrhs doubles (re, im); the call
+ * synchronises the stream. */
 hr_status hr_field_dot(const hr_lattice_desc *lat, hr_parity par, hr_prec prec,
                        const void *a, const void *b, int nrhs, double *out,
                        void *stream);
@@ -224,14 +226,18 @@ hr_status hr_field_dot(const hr_lattice_desc *lat, hr_parity par, hr_prec prec,
  * -- e.g. when another allocator owns the device memory, or on a path that
  * cannot take the implicit synchronisation of cudaMalloc/cudaFree -- while
  * hr_field_dot takes its reduction scratch from cudaMallocAsync.
- * Same arguments and result as hr_field_dot; additionally nrhs must be
- * 1..16 (HR_ERR_INVALID otherwise).  Its scratch is a fixed ~312 KB array in
- * device memory, present on every GPU that loads the library until the
- * process exits; every call shares it and it keeps the last call's contents
- * (each call zeroes the tickets it needs first).  Calls that overlap on the
- * GPU race on that array, so order them on one stream.  The first call on a
- * device looks up the array's device address with that device current; make
- * that first call before any stream capture on the device.
+ * Same arguments as hr_field_dot (every precision and representation it
+ * accepts); additionally nrhs must be 1..16 (HR_ERR_INVALID otherwise).  The
+ * result equals hr_field_dot's up to rounding: both sum in FP64 with
+ * compensated cross-block sums, but the summation order differs (a fixed
+ * number of blocks, each thread summing several sites with TwoSum).  Its
+ * scratch is a fixed ~312 KB array in device memory, present on every GPU
+ * that loads the library until the process exits; every call shares it and
+ * it keeps the last call's contents (each call zeroes the tickets it needs
+ * first).  Calls that overlap on the GPU race on that array, so order them
+ * on one stream.  The first call on a device looks up the array's device
+ * address with that device current; make that first call before any stream
+ * capture on the device.
  * Synchronises the stream. */
 hr_status hr_field_dot_static(const hr_lattice_desc *lat, hr_parity par,
                               hr_prec prec, const void *a, const void *b,

@@ -646,7 +646,7 @@ hr_status hr_field_dot(const hr_lattice_desc *lat, hr_parity par, hr_prec prec, 
 {
     hr_status st = check_lattice(lat);
     if (st != HR_OK) return st;
-    if (!a || !b || !out || nrhs < 1 || prec < HR_F64 || prec > HR_DF64) {
+    if (!a || !b || !out || nrhs < 1 || prec < HR_F64 || prec > HR_DF64 || par < HR_EVEN || par > HR_EO_PRECOND) {
         set_error("hr_field_dot: bad arguments");
         return HR_ERR_INVALID;
     }

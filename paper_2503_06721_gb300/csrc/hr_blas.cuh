@@ -49,4 +49,37 @@ hr_status blas_start_zero(int D, const BlasParams &bp, cudaStream_t st);
 
 constexpr int BLAS_THREADS = 256;
 
+// runtime dispatch on the representation dimension D and on a precision: BODY
+// is compiled once per case with the constant DD (and PN) set
+#define HR_FOR_D(D_, BODY)                     \
+    switch (D_) {                              \
+    case 2: { constexpr int DD = 2; BODY; } break; \
+    case 3: { constexpr int DD = 3; BODY; } break; \
+    case 4: { constexpr int DD = 4; BODY; } break; \
+    case 5: { constexpr int DD = 5; BODY; } break; \
+    case 6: { constexpr int DD = 6; BODY; } break; \
+    case 8: { constexpr int DD = 8; BODY; } break; \
+    default: set_error("representation dimension %d not compiled", D_); return HR_ERR_UNSUPPORTED; \
+    }
+
+#define HR_FOR_P(P_, PN, BODY)                              \
+    switch (P_) {                                           \
+    case HR_F64: { constexpr int PN = HR_F64; BODY; } break; \
+    case HR_F32: { constexpr int PN = HR_F32; BODY; } break; \
+    case HR_F16: { constexpr int PN = HR_F16; BODY; } break; \
+    case HR_BF16: { constexpr int PN = HR_BF16; BODY; } break; \
+    default: set_error("bad precision %d", P_); return HR_ERR_INVALID; \
+    }
+
+// the same with the float-float storage (conversions and dot products only)
+#define HR_FOR_PX(P_, PN, BODY)                              \
+    switch (P_) {                                           \
+    case HR_F64: { constexpr int PN = HR_F64; BODY; } break; \
+    case HR_F32: { constexpr int PN = HR_F32; BODY; } break; \
+    case HR_F16: { constexpr int PN = HR_F16; BODY; } break; \
+    case HR_BF16: { constexpr int PN = HR_BF16; BODY; } break; \
+    case HR_DF64: { constexpr int PN = HR_DF64; BODY; } break; \
+    default: set_error("bad precision %d", P_); return HR_ERR_INVALID; \
+    }
+
 }  // namespace hr

@@ -1,5 +1,10 @@
-// hr_static.cu -- hr_field_dot_static: the compensated field dot product of
-// hr_field_dot, for callers that must not allocate device memory.
+// hr_static.cu -- hr_field_dot_static: the field dot product <a, b> of
+// hr_field_dot, for callers that must not allocate device memory.  It
+// accepts every (representation dimension, precision) that hr_field_dot
+// accepts and returns the same value up to rounding: both sum in FP64 and
+// combine the per-block partials in double-double, but this kernel runs a
+// fixed number of blocks, so each thread first accumulates several sites
+// (compensated with TwoSum) and the summation order differs.
 //
 // Who needs it: code that runs where a device allocation is not allowed or
 // not acceptable -- for example a caller whose device memory is entirely
@@ -23,7 +28,10 @@ namespace hr {
 
 // limits of the fixed scratch: right-hand sides per call and reduction blocks
 constexpr int STATIC_DOT_MAX_RHS = 16;
-constexpr int STATIC_DOT_BLOCKS = 1216;   // 8 blocks of 256 threads per SM on 152 SMs
+// fixed upper bound on the blocks of one launch: it sizes the partials array;
+// lattices with more sites than blocks x threads are covered by each thread
+// taking several sites (grid-stride loop)
+constexpr int STATIC_DOT_BLOCKS = 1216;
 constexpr int STATIC_DOT_THREADS = 256;
 
 // [tickets: MAX_RHS unsigned (padded to 256 B)] [results: MAX_RHS x 2 doubles]
@@ -46,7 +54,10 @@ __global__ void __launch_bounds__(STATIC_DOT_THREADS) k_dot_static(long nsites, 
     double *results = reinterpret_cast<double *>(scr + STATIC_DOT_TICKETS);
     double *partials = reinterpret_cast<double *>(scr + STATIC_DOT_TICKETS + STATIC_DOT_RESULTS);
     using R = typename St<P>::R;
-    double v[2] = {0, 0};
+    // per-thread running sums kept as (hi, lo) pairs: TwoSum moves each
+    // addition's rounding error into lo, so a thread that takes many sites
+    // loses no more than one that takes one
+    double hi[2] = {0, 0}, lo[2] = {0, 0};
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < nsites; i += (long)gridDim.x * blockDim.x) {
         cx<R> x[4][D], y[4][D];
         SpinorIO<P, D>::load_rw(a, rhs, i, x);
@@ -56,12 +67,20 @@ __global__ void __launch_bounds__(STATIC_DOT_THREADS) k_dot_static(long nsites, 
         for (int s = 0; s < 4; s++)
 #pragma unroll
             for (int c = 0; c < D; c++) {
-                s0 += (double)x[s][c].re * y[s][c].re + (double)x[s][c].im * y[s][c].im;
-                s1 += (double)x[s][c].re * y[s][c].im - (double)x[s][c].im * y[s][c].re;
+                const double xr = (double)x[s][c].re, xi = (double)x[s][c].im;
+                const double yr = (double)y[s][c].re, yi = (double)y[s][c].im;
+                s0 += xr * yr + xi * yi;
+                s1 += xr * yi - xi * yr;
             }
-        v[0] += s0;
-        v[1] += s1;
+        double t, e;
+        two_sum(hi[0], s0, t, e);
+        hi[0] = t;
+        lo[0] += e;
+        two_sum(hi[1], s1, t, e);
+        hi[1] = t;
+        lo[1] += e;
     }
+    double v[2] = {hi[0] + lo[0], hi[1] + lo[1]};
     double tot[2];
     if (grid_reduce<2>(v, partials + (size_t)rhs * gridDim.x * 2, tickets + rhs, gridDim.x, blockIdx.x, tot)) {
         results[rhs * 2 + 0] = tot[0];
@@ -107,7 +126,7 @@ extern "C" hr_status hr_field_dot_static(const hr_lattice_desc *lat, hr_parity p
 {
     hr_status st = check_lattice(lat);
     if (st != HR_OK) return st;
-    if (!a || !b || !out || prec < HR_F64 || prec > HR_BF16) {
+    if (!a || !b || !out || prec < HR_F64 || prec > HR_DF64 || par < HR_EVEN || par > HR_EO_PRECOND) {
         set_error("hr_field_dot_static: bad arguments");
         return HR_ERR_INVALID;
     }
@@ -127,25 +146,8 @@ extern "C" hr_status hr_field_dot_static(const hr_lattice_desc *lat, hr_parity p
     FieldView va = make_view(const_cast<void *>(a), ns, D, prec), vb = make_view(const_cast<void *>(b), ns, D, prec);
     long blocks = (ns + STATIC_DOT_THREADS - 1) / STATIC_DOT_THREADS;
     if (blocks > STATIC_DOT_BLOCKS) blocks = STATIC_DOT_BLOCKS;
-    dim3 grid((unsigned)blocks, (unsigned)nrhs);
-#define HR_DOTS(DD)                                                                                      \
-    case DD:                                                                                             \
-        switch (prec) {                                                                                  \
-        case HR_F64: k_dot_static<DD, HR_F64><<<grid, STATIC_DOT_THREADS, 0, s>>>(ns, va, vb, scr); break;   \
-        case HR_F32: k_dot_static<DD, HR_F32><<<grid, STATIC_DOT_THREADS, 0, s>>>(ns, va, vb, scr); break;   \
-        case HR_F16: k_dot_static<DD, HR_F16><<<grid, STATIC_DOT_THREADS, 0, s>>>(ns, va, vb, scr); break;   \
-        case HR_BF16: k_dot_static<DD, HR_BF16><<<grid, STATIC_DOT_THREADS, 0, s>>>(ns, va, vb, scr); break; \
-        }                                                                                                \
-        break;
-    switch (D) {
-        HR_DOTS(2)
-        HR_DOTS(3)
-        HR_DOTS(4)
-        HR_DOTS(6)
-        HR_DOTS(8)
-    default: set_error("representation dimension %d not compiled", D); return HR_ERR_UNSUPPORTED;
-    }
-#undef HR_DOTS
+    const dim3 grid((unsigned)blocks, (unsigned)nrhs);
+    HR_FOR_D(D, HR_FOR_PX(prec, PN, (k_dot_static<DD, PN><<<grid, STATIC_DOT_THREADS, 0, s>>>(ns, va, vb, scr))));
     HR_LAUNCH_CHECK("k_dot_static");
     HR_CUDA_CHECK(cudaMemcpyAsync(out, scr + STATIC_DOT_TICKETS, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, s));
     HR_CUDA_CHECK(cudaStreamSynchronize(s));
