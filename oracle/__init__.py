@@ -32,8 +32,9 @@ _HDR = _HERE / "hr_oracle.h"
 _LIBDIR = _HERE / "_build"
 _LIB = _LIBDIR / "liboracle.so"
 
-FUND, ADJ, SYM, ASYM = 0, 1, 2, 3
-REP_NAMES = {"FUND": FUND, "ADJ": ADJ, "SYM": SYM, "ASYM": ASYM, "2AS": ASYM}
+FUND, ADJ, SYM, ASYM, ASYM_REAL = 0, 1, 2, 3, 4
+REP_NAMES = {"FUND": FUND, "ADJ": ADJ, "SYM": SYM, "ASYM": ASYM, "2AS": ASYM, "ASYM_REAL": ASYM_REAL,
+             "2AS_REAL": ASYM_REAL}
 
 
 def build(force: bool = False) -> Path:

@@ -64,6 +64,7 @@ int or_rep_dim(int N, int rep)
     case OR_ADJ:  return N * N - 1;
     case OR_SYM:  return N * (N + 1) / 2;
     case OR_ASYM: return N * (N - 1) / 2;
+    case OR_ASYM_REAL: return N == 4 ? 6 : -1;
     }
     return -1;
 }
@@ -140,6 +141,24 @@ int or_rep_basis(int N, int rep, orc *E)
         return N * N - 1;
     }
     if (rep == OR_FUND) return 0;
+    if (rep == OR_ASYM_REAL) {
+        if (N != 4) return 0;
+        /* pairs P with complement Q and the sign s of the permutation (P, Q) */
+        static const int P[3][2] = {{0, 1}, {0, 2}, {0, 3}}, Q[3][2] = {{2, 3}, {1, 3}, {1, 2}};
+        static const double sg[3] = {1.0, -1.0, 1.0};
+        for (int k = 0; k < 3; k++)
+            for (int im = 0; im < 2; im++) {
+                orc *B = E + (size_t)(2 * k + im) * 16;
+                memset(B, 0, 16 * sizeof(orc));
+                orc c = im ? 0.5 * I : 0.5;          /* 1/sqrt2 of f times 1/sqrt2 of e */
+                double q = im ? -sg[k] : sg[k];
+                B[P[k][0] * 4 + P[k][1]] += c;
+                B[P[k][1] * 4 + P[k][0]] -= c;
+                B[Q[k][0] * 4 + Q[k][1]] += q * c;
+                B[Q[k][1] * 4 + Q[k][0]] -= q * c;
+            }
+        return 6;
+    }
     int n = 0;
     double r2 = 1.0 / sqrt(2.0);
     for (int i = 0; i < N; i++)

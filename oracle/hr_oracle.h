@@ -26,11 +26,14 @@
 
 typedef double _Complex orc;
 
-enum { OR_FUND = 0, OR_ADJ = 1, OR_SYM = 2, OR_ASYM = 3 };
+/* OR_ASYM_REAL: the two-index antisymmetric representation of SU(4) (the 6,
+ * a real representation, Table 1) written in a basis in which R(U) is real
+ * orthogonal; only N = 4 */
+enum { OR_FUND = 0, OR_ADJ = 1, OR_SYM = 2, OR_ASYM = 3, OR_ASYM_REAL = 4 };
 
 typedef struct {
     int N;        /* gauge group SU(N) */
-    int rep;      /* OR_FUND / OR_ADJ / OR_SYM / OR_ASYM (Table 1) */
+    int rep;      /* OR_FUND / OR_ADJ / OR_SYM / OR_ASYM / OR_ASYM_REAL (Table 1) */
     int dims[4];  /* T, X, Y, Z */
     int bc[4];    /* +1 periodic, -1 antiperiodic (Sec. 5.3.1) */
     double m0;    /* bare mass m in D_m = D + m (Eq. D_m) */
@@ -45,7 +48,14 @@ void or_gamma(int mu, orc *g);
 void or_generators(int N, orc *T);
 /* orthonormal basis of the representation space: for ADJ the T^a (with the
  * coordinate map v_a = 2 Tr(T^a X)); for SYM/ASYM the matrices e_n with
- * Tr(e_n^dag e_m) = delta; returns the number of basis matrices */
+ * Tr(e_n^dag e_m) = delta; for ASYM_REAL (N = 4) the antisymmetric matrices
+ *   f = (e_P + s e_Q)/sqrt2,  f' = i (e_P - s e_Q)/sqrt2
+ * for the index pairs (P, Q; s) = ((01),(23);+1), ((02),(13);-1),
+ * ((03),(12);+1), each pair P with its complement Q, s the sign of the
+ * permutation (P, Q): every such f is fixed by A -> *conj(A) with
+ * (*A)_ij = 1/2 eps_ijkl A_kl, a map that commutes with A -> U A U^T for
+ * det U = 1, so R(U) is real in this basis.  Returns the number of basis
+ * matrices */
 int  or_rep_basis(int N, int rep, orc *E);
 /* represented link R(U) (D x D, row-major).  returns D */
 int  or_represent_link(int N, int rep, const orc *U, orc *R);

@@ -66,7 +66,9 @@ def test_rep_dims_table1(oracle_mod, row):
 
 
 REPS = [(N, rep) for N in (2, 3, 4) for rep in ("FUND", "ADJ", "SYM", "ASYM")
-        if not (N == 2 and rep == "ASYM")]
+        if not (N == 2 and rep == "ASYM")] + [(4, "ASYM_REAL")]
+# the real basis of the SU(4) 2AS is the same representation (Table 1's 2AS row)
+TABLE_REP = {"ASYM_REAL": "ASYM"}
 
 
 @pytest.mark.parametrize("N,rep", REPS)
@@ -81,8 +83,9 @@ def test_represent_homomorphism_unitarity(oracle_mod, N, rep):
         np.testing.assert_allclose(RU @ RU.conj().T, np.eye(D), atol=1e-13)
         RUd = oracle_mod.represent_link(N, rep, U[i].conj().T)
         np.testing.assert_allclose(RUd, RU.conj().T, atol=1e-13)
-        if rep == "ADJ":  # real representation (stored real, Sec. 3.1.2)
+        if rep in ("ADJ", "ASYM_REAL"):  # real representations (stored real, Sec. 3.1.2)
             assert np.abs(RU.imag).max() < 1e-14
+            assert abs(np.linalg.det(RU.real) - 1) < 1e-12
         np.testing.assert_allclose(oracle_mod.represent_link(N, rep, np.eye(N)), np.eye(D),
                                    atol=1e-15)
 
@@ -95,7 +98,7 @@ def test_characters(oracle_mod, N, rep):
         tr2 = np.trace(U @ U)
         chi = np.trace(oracle_mod.represent_link(N, rep, U))
         want = {"FUND": tr, "ADJ": abs(tr) ** 2 - 1, "SYM": (tr * tr + tr2) / 2,
-                "ASYM": (tr * tr - tr2) / 2}[rep]
+                "ASYM": (tr * tr - tr2) / 2, "ASYM_REAL": (tr * tr - tr2) / 2}[rep]
         assert abs(chi - want) < 1e-13
         if N == 3 and rep == "ASYM":  # 2AS of SU(3) is the anti-fundamental
             assert abs(chi - np.conj(tr)) < 1e-13
@@ -117,7 +120,10 @@ def test_rep_generators(oracle_mod, N, rep):
         fd = -1j * (Rp - Rm) / (2 * eps)
         np.testing.assert_allclose(TR[a], fd, atol=1e-9)
         np.testing.assert_allclose(TR[a], TR[a].conj().T, atol=1e-14)
-    row = [r for r in H.table1() if r["rep"] == rep and r["N"] == N][0]
+    row = [r for r in H.table1() if r["rep"] == TABLE_REP.get(rep, rep) and r["N"] == N][0]
+    if rep == "ASYM_REAL":   # generators of a real orthogonal representation: i x real antisymmetric
+        assert np.abs(TR.real).max() < 1e-14
+        np.testing.assert_allclose(TR.imag, -np.swapaxes(TR.imag, 1, 2), atol=1e-14)
     np.testing.assert_allclose(np.einsum("aij,bji->ab", TR, TR),
                                float(row["T"]) * np.eye(N * N - 1), atol=1e-13)
     np.testing.assert_allclose(np.einsum("aij,ajk->ik", TR, TR), float(row["C2"]) * np.eye(D),
@@ -127,6 +133,27 @@ def test_rep_generators(oracle_mod, N, rep):
     lhs = np.einsum("aij,bjk->abik", TR, TR) - np.einsum("bij,ajk->abik", TR, TR)
     rhs = 1j * np.einsum("abc,cik->abik", f, TR)
     np.testing.assert_allclose(lhs, rhs, atol=1e-13)
+
+
+def test_asym_real_basis_is_equivalent_to_asym(oracle_mod):
+    """The real basis of the SU(4) 2AS is the complex basis rotated by one
+    fixed unitary W (W_mn = Tr(e_m^dag f_n)): R_real(U) = W^dag R_2AS(U) W for
+    every U, and W maps the real basis onto matrices fixed by A -> *conj(A)."""
+    E = oracle_mod.rep_basis(4, "ASYM")
+    F = oracle_mod.rep_basis(4, "ASYM_REAL")
+    assert F.shape == (6, 4, 4)
+    np.testing.assert_allclose(np.einsum("nij,mij->nm", F.conj(), F), np.eye(6), atol=1e-15)
+    np.testing.assert_allclose(F, -np.swapaxes(F, 1, 2), atol=0)
+    eps = np.zeros((4, 4, 4, 4))
+    for p in itertools.permutations(range(4)):
+        eps[p] = np.linalg.det(np.eye(4)[list(p)])
+    for f in F:   # fixed by the antilinear Hodge map
+        np.testing.assert_allclose(0.5 * np.einsum("ijkl,kl->ij", eps, f.conj()), f, atol=1e-15)
+    W = np.einsum("mij,nij->mn", E.conj(), F)
+    np.testing.assert_allclose(W.conj().T @ W, np.eye(6), atol=1e-15)
+    for U in H.su_n(5, 4, seed=97):
+        np.testing.assert_allclose(oracle_mod.represent_link(4, "ASYM_REAL", U),
+                                   W.conj().T @ oracle_mod.represent_link(4, "ASYM", U) @ W, atol=1e-14)
 
 
 def test_table1_reading_is_consistent():

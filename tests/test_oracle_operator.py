@@ -9,7 +9,8 @@ import pytest
 
 from tests import _helpers as H
 
-CASES = [(2, "ADJ"), (3, "SYM"), (3, "ADJ"), (4, "FUND"), (4, "ASYM"), (3, "FUND"), (5, "FUND"), (8, "FUND")]
+CASES = [(2, "ADJ"), (3, "SYM"), (3, "ADJ"), (4, "FUND"), (4, "ASYM"), (3, "FUND"), (5, "FUND"), (8, "FUND"),
+         (4, "ASYM_REAL")]
 
 
 def _gam(oracle_mod):
@@ -102,7 +103,8 @@ def _dense(oracle_mod, L, UR, V, D, dagger=False):
     return M
 
 
-@pytest.mark.parametrize("N,rep", [(2, "ADJ"), (3, "SYM"), (3, "ADJ"), (4, "ASYM"), (5, "FUND"), (8, "FUND")])
+@pytest.mark.parametrize("N,rep", [(2, "ADJ"), (3, "SYM"), (3, "ADJ"), (4, "ASYM"), (5, "FUND"), (8, "FUND"),
+                                   (4, "ASYM_REAL")])
 def test_dense_2x2x2x2(oracle_mod, N, rep):
     dims = (2, 2, 2, 2)
     V = 16
@@ -258,3 +260,27 @@ def oracle_mod_neighbour(dims, lex, mu, d):
     c = list(np.unravel_index(lex, dims))
     c[mu] = (c[mu] + d) % dims[mu]
     return int(np.ravel_multi_index(c, dims))
+
+
+def test_asym_real_operator_and_force_equivalence(oracle_mod):
+    """The Wilson-Dirac operator with SU(4) 2AS links in the real basis is the
+    2AS operator in rotated colour coordinates: D_real (W^dag psi) =
+    W^dag (D_2AS psi), W the fixed basis change; the force, a function of
+    basis-independent bilinears, is the same for X, Y and W^dag X, W^dag Y."""
+    dims = (4, 2, 2, 4)
+    L = oracle_mod.lat(4, "ASYM", dims, (-1, 1, 1, 1), -0.1)
+    Lr = oracle_mod.lat(4, "ASYM_REAL", dims, (-1, 1, 1, 1), -0.1)
+    W = np.einsum("mij,nij->mn", oracle_mod.rep_basis(4, "ASYM").conj(), oracle_mod.rep_basis(4, "ASYM_REAL"))
+    V = int(np.prod(dims))
+    UF = H.links(dims, 4, 0.6, seed=301)
+    UR = oracle_mod.represent_field(L, UF)
+    URr = oracle_mod.represent_field(Lr, UF)
+    assert np.abs(URr.imag).max() < 1e-14
+    psi = H.spinor(V, 6, 303)
+    rot = lambda x: x @ W.conj()   # colour coordinates in the real basis: W^dag x per spin
+    for dag in (False, True):
+        np.testing.assert_allclose(oracle_mod.dirac_full(Lr, URr, rot(psi), dag),
+                                   rot(oracle_mod.dirac_full(L, UR, psi, dag)), atol=1e-13)
+    X, Y = H.spinor(V, 6, 305), H.spinor(V, 6, 307)
+    np.testing.assert_allclose(oracle_mod.force(Lr, URr, rot(X), rot(Y)), oracle_mod.force(L, UR, X, Y),
+                               atol=1e-12)
