@@ -44,10 +44,11 @@ if ROOT not in sys.path:
 WORKLOAD = "su3_sym_64x32x32x32"
 WORKLOAD_TEXT = "SU(3) sextet (SYM, D_R=6) 32^3x64, m0=-0.3, even/odd, mixed FP32/FP64 CG to 1e-10 + force"
 # DRAM bytes (read + write) of one FP32 D_eo launch of the direct hopping
-# kernel on this workload: 1.380 GB measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum) on the 32^4 sextet lattice, times 2 for the 32^3x64
-# site count.  Reported only while the tuner picks that kernel.
-DEO_TRAFFIC_DIRECT = 2 * 1.380e9
+# kernel on this workload (32^3 x 64 sextet, stored links), measured by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum = 2.624 + 0.167 GB) against
+# 2.819 GB of compulsory bytes.  Reported only while the tuner picks that
+# kernel.
+DEO_TRAFFIC_DIRECT = 2.790e9
 METRIC = "D_eo apply GB/s (% of HBM peak); mixed/batched vs FP64 CG time to residual 1e-10"
 UNIT = "GB/s"
 TOL = 1e-10
@@ -70,6 +71,20 @@ def hop_bytes(D: int, real_links: bool, prec: int, vh: int, spinor_reads: int = 
     lp = D * D * (cb // 2 if real_links else cb)
     sp = 4 * D * cb + (4 if prec >= 2 else 0)
     return vh * (8 * lp + (1 + spinor_reads) * sp)
+
+
+def link_bytes(N: int, D: int, rep: str, prec: int, rebuild: bool) -> int:
+    """bytes of one link as a launch reads it: D_R^2 complex (D_R^2 real for
+    the adjoint), or N^2 complex when rebuilt in the kernel from U_F"""
+    cb = [16, 8, 4, 4, 16][prec]
+    if rebuild:
+        return N * N * cb
+    return D * D * (cb // 2 if rep == "ADJ" else cb)
+
+
+def spinor_bytes(D: int, prec: int) -> int:
+    cb = [16, 8, 4, 4, 16][prec]
+    return 4 * D * cb + (4 if prec in (2, 3) else 0)
 
 
 def job_throughput(step_bytes_local: float, ms_local: float, steps: int, dist=None, device=None):
@@ -201,7 +216,7 @@ def run_ours(args, rank, world, local_rank):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.deo_per_step)]
     n_deo = args.deo_per_step
     deo_ms = []
-    work = {"bytes": 0}
+    work = {"bytes": 0, "actual": 0}
 
     pev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     phases = {"represent": 0.0, "deo": 0.0, "cg_force": 0.0}
@@ -240,6 +255,15 @@ def run_ours(args, rank, world, local_rank):
         # x = 0, is b itself), plus 4 for the FP64 confirmation of a DF64 one
         h64 = 1 + 4 * (r["outer_iters"] + (res_prec == hr.DF64))
         work["bytes"] += h32 * hop_bytes(D, real, hr.F32, vh) + h64 * hop_bytes(D, real, hr.F64, vh)
+        # the same launches at the bytes they move: the D_eo launches read
+        # stored links, the solver's launches use its tuned link mode
+        sp32, sp64 = spinor_bytes(D, hr.F32), spinor_bytes(D, hr.F64)
+        lp32 = link_bytes(wl.N, D, wl.rep, hr.F32, solver_links["f32"] == "rebuild")
+        lp64 = link_bytes(wl.N, D, wl.rep, hr.F64, solver_links["f64"] == "rebuild")
+        work["actual"] += (n_deo * vh * (8 * link_bytes(wl.N, D, wl.rep, hr.F32, False) + 2 * sp32)
+                           + vh * (8 * link_bytes(wl.N, D, wl.rep, hr.F64, False) + 2 * sp64)
+                           + 4 * r["iters"] * vh * (8 * lp32 + 2 * sp32)
+                           + (h64 - 1) * vh * (8 * lp64 + 2 * sp64))
         work["res"] = r
         return x, F
 
@@ -247,6 +271,7 @@ def run_ours(args, rank, world, local_rank):
         step(phi, U)
     torch.cuda.synchronize()
     work["bytes"] = 0
+    work["actual"] = 0
     for k in phases:
         phases[k] = 0.0
     clocks = Clocks(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
@@ -272,8 +297,10 @@ def run_ours(args, rank, world, local_rank):
     ck = clocks.stop()
     ms = t0.elapsed_time(t1)
     step_bytes = work["bytes"] / args.steps
+    actual_bytes = work["actual"] / args.steps
     res = work["res"]
     value, ms_per_step = job_throughput(step_bytes, ms, args.steps, dist, dev)
+    actual_value, _ = job_throughput(actual_bytes, ms, args.steps, dist, dev)
     phase_ms = {k: round(v / args.steps, 2) for k, v in phases.items()}
     deo_ms_avg = sum(deo_times) / len(deo_times)
     deo_bytes = hop_bytes(D, real, hr.F32, vh)
@@ -386,6 +413,11 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.empty_cache()
         batched = batched_compare(hr, synth, dev, stream)
 
+    by_rep = None
+    if rank == 0 and not args.no_deo_by_rep:
+        torch.cuda.empty_cache()
+        by_rep = deo_by_rep(hr, synth, dev, stream)
+
     largen = None
     if rank == 0 and not args.no_largen:
         torch.cuda.empty_cache()
@@ -416,6 +448,10 @@ def run_ours(args, rank, world, local_rank):
                          "bytes_per_launch": deo_bytes,
                          "effective_GBs": round(hop_bytes(D, real, hr.F32, vh, 8) / (deo_ms_avg * 1e-3) / 1e9, 1),
                          "frac_of_nominal_7900": round(achieved / 7900.0, 4)},
+            "step_actual_bytes": {"GBs": round(actual_value, 1), "bytes_per_step": int(actual_bytes),
+                                  "note": "the step's hopping launches at the bytes they move (solver "
+                                          "launches in their tuned link mode); value charges every "
+                                          "launch at stored-link bytes (D_eo-equivalent work)"},
             "hop_variants_f32": variants,
             "solver_links": solver_links,
             "solver_hop_variants_f32": solver_variants,
@@ -428,6 +464,7 @@ def run_ours(args, rank, world, local_rank):
             "multishift": multishift,
             "hmc": hmc,
             "clover": clover,
+            "deo_by_rep": by_rep,
             "large_n_fund_f32_deo": largen,
             "cpu_baseline": cpu,
         }
@@ -530,6 +567,113 @@ def largen_sweep(hr, synth, dev, stream, dims=(48, 24, 24, 24)):
         g.close()
         del x, y
         torch.cuda.empty_cache()
+    return out
+
+
+DEO_CASES = [
+    # (name, N, rep, dims, m0, eps, precisions, link modes)
+    ("su2_adj_8x8x8x8", 2, "ADJ", (8, 8, 8, 8), -0.2, 0.3, ("f32", "f16", "bf16"), ("stored",)),
+    ("su3_sym_64x32x32x32", 3, "SYM", (64, 32, 32, 32), -0.3, 0.4, ("f32", "f16", "bf16"),
+     ("stored", "rebuild")),
+    ("su3_adj_32x32x32x32", 3, "ADJ", (32, 32, 32, 32), -0.35, 0.5, ("f32", "f16", "bf16"), ("stored", "rebuild")),
+    ("su3_adj_128x64x64x64", 3, "ADJ", (128, 64, 64, 64), -0.35, 0.5, ("f32", "f16", "bf16"),
+     ("stored", "rebuild")),
+    ("su4_fund_48x24x24x24", 4, "FUND", (48, 24, 24, 24), -0.25, 0.4, ("f32", "f16", "bf16"), ("stored",)),
+    ("su4_asym_48x24x24x24", 4, "ASYM", (48, 24, 24, 24), -0.25, 0.4, ("f32", "f16", "bf16"),
+     ("stored", "rebuild")),
+]
+
+
+def fp64_peak(dev, stream, n=4096, reps=6):
+    """FP64 arithmetic peak of this GPU as a cuBLAS DGEMM measures it
+    (2 n^3 flop per product, best of reps, CUDA events)."""
+    import torch
+    a = torch.randn((n, n), dtype=torch.float64, device=dev)
+    b = torch.randn((n, n), dtype=torch.float64, device=dev)
+    c = a @ b
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = None
+    for _ in range(reps):
+        e0.record(stream)
+        torch.matmul(a, b, out=c)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None else min(best, t)
+    del a, b, c
+    torch.cuda.empty_cache()
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
+def deo_by_rep(hr, synth, dev, stream, reps=20):
+    """D_eo (even output, one right-hand side) for every representation and
+    storage precision, stored links and, where listed, links rebuilt in the
+    kernel from the fundamental ones; each with the tuned kernel variant.
+    GB/s of compulsory bytes V/2 (8 L_p + 2 S_p) at the bytes the launch
+    reads (L_p of the link mode), and the fraction of the measured HBM copy
+    bandwidth.  Plus the FP64 sextet D_eo, whose 0.92 flop per byte makes it
+    bound by the FP64 units: GFLOP/s (128 D^2 + 56 D flop per site) against
+    the FP64 peak a DGEMM measures on this GPU."""
+    import torch
+    peak, _ = _peaks()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {"unit": "GB/s of compulsory bytes", "peak_GBs": peak, "reps": reps}
+    for name, N, rep, dims, m0, eps, precs, modes in DEO_CASES:
+        lat = hr.Lattice(N, rep, dims, (-1, 1, 1, 1), m0)
+        vh, D = lat.volume // 2, lat.D
+        U = synth.random_links(lat.volume, N, eps, 2503067210 + 60, device=dev)
+        x64 = synth.gaussian_spinor(vh, D, 3, device=dev)
+        row = {"dims": list(dims), "D_R": D}
+        for p in precs:
+            # one handle per precision: the 64^3 x 128 adjoint's FP32 links alone take 69 GB
+            prec = hr.PRECS[p]
+            g = hr.Gauge(lat, U, precs=(p,), stored="stored" in modes, rebuild="rebuild" in modes)
+            x = x64.to(torch.complex64) if prec == hr.F32 else hr.field_convert(lat, hr.EVEN, x64, hr.F64, prec)
+            y = g.apply(hr.EVEN, prec, x)
+            for mode in modes:
+                g.set_link_mode(hr.LINKS_STORED if mode == "stored" else hr.LINKS_REBUILD)
+                g.tune(prec)
+                ms = timed(lambda: g.apply(hr.EVEN, prec, x, out=y))
+                byts = vh * (8 * link_bytes(N, D, rep, prec, mode == "rebuild") + 2 * spinor_bytes(D, prec))
+                gbs = byts / (ms * 1e-3) / 1e9
+                row[f"{p}_{mode}"] = {"ms": round(ms, 4), "GBs": round(gbs, 1), "frac": round(gbs / peak, 4),
+                                      "variant": g.hop_variant(prec, hr.EPI_STORE, 1)}
+            g.close()
+            del x, y
+            torch.cuda.empty_cache()
+        del U, x64
+        torch.cuda.empty_cache()
+        out[name] = row
+    # FP64 sextet D_eo against the FP64 units
+    fpk = fp64_peak(dev, stream)
+    lat = hr.Lattice(3, "SYM", (64, 32, 32, 32), (-1, 1, 1, 1), -0.3)
+    vh, D = lat.volume // 2, lat.D
+    g = hr.Gauge(lat, synth.random_links(lat.volume, 3, 0.4, 2503067210 + 61, device=dev), precs=("f64",))
+    x = synth.gaussian_spinor(vh, D, 3, device=dev)
+    y = g.apply(hr.EVEN, hr.F64, x)
+    ms = timed(lambda: g.apply(hr.EVEN, hr.F64, x, out=y))
+    flops = vh * (128 * D * D + 56 * D)
+    byts = vh * (8 * link_bytes(3, D, "SYM", hr.F64, False) + 2 * spinor_bytes(D, hr.F64))
+    out["su3_sym_64x32x32x32_f64"] = {
+        "ms": round(ms, 4), "GFLOPs": round(flops / (ms * 1e-3) / 1e9, 1),
+        "fp64_peak_dgemm_TFLOPs": round(fpk, 3), "flop_frac": round(flops / (ms * 1e-3) / 1e12 / fpk, 4),
+        "GBs": round(byts / (ms * 1e-3) / 1e9, 1), "frac_of_hbm": round(byts / (ms * 1e-3) / 1e9 / peak, 4),
+        "bound": "fp64 alu"}
+    g.close()
+    del x, y
+    torch.cuda.empty_cache()
     return out
 
 
@@ -855,6 +999,8 @@ def main():
     ap.add_argument("--no-hmc", action="store_true", help="skip the HMC trajectory measurement")
     ap.add_argument("--no-clover", action="store_true", help="skip the clover-operator measurement")
     ap.add_argument("--no-largen", action="store_true", help="skip the large-N fundamental D_eo sweep")
+    ap.add_argument("--no-deo-by-rep", action="store_true",
+                    help="skip the D_eo sweep over representations and precisions")
     ap.add_argument("--no-multishift", action="store_true",
                     help="skip the multi-shift-vs-sequential shifted solve comparison")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

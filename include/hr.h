@@ -44,8 +44,16 @@
 extern "C" {
 #endif
 
-/* Supported representations, Table 1 (Sec. 2.3). HR_ASYM is "2AS". */
-typedef enum { HR_FUND = 0, HR_ADJ = 1, HR_SYM = 2, HR_ASYM = 3 } hr_rep;
+/* Supported representations, Table 1 (Sec. 2.3). HR_ASYM is "2AS".
+ * HR_ASYM_REAL is the 2AS of SU(4) (the 6, a real representation) in a
+ * basis where R(U) is real orthogonal, so its links are stored as reals
+ * (Sec. 3.1.2): the orthonormal antisymmetric matrices
+ *   f_2k = (e_P + s e_Q)/sqrt2,  f_2k+1 = i (e_P - s e_Q)/sqrt2,
+ *   (P, Q; s) = ((0,1),(2,3);+1), ((0,2),(1,3);-1), ((0,3),(1,2);+1) for k = 0,1,2,
+ * with e_(ij) = (E_ij - E_ji)/sqrt2 the HR_ASYM basis.  Colour components of
+ * spinors are coordinates in this basis: psi_real = W^dag psi_2AS with
+ * W_mn = Tr(e_m^dag f_n). */
+typedef enum { HR_FUND = 0, HR_ADJ = 1, HR_SYM = 2, HR_ASYM = 3, HR_ASYM_REAL = 4 } hr_rep;
 
 /* Storage precision of fields and links.  F64 computes in double, F32/F16/BF16
  * in float; F16/BF16 spinors carry one float scale per site.  DF64 holds every
@@ -82,7 +90,8 @@ typedef enum { HR_LINKS_STORED = 0, HR_LINKS_REBUILD = 1, HR_LINKS_AUTO = 2 } hr
 
 typedef struct {
     int N;          /* SU(N): N = 2, 3, 4 with the representations FUND,
-                       ADJ, SYM (N = 2, 3), ASYM (N = 3, 4); N = 5, 6, 8 with
+                       ADJ, SYM (N = 2, 3), ASYM (N = 3, 4), ASYM_REAL
+                       (N = 4); N = 5, 6, 8 with
                        FUND only, run by the colour-parallel hopping kernel
                        (Sec. 8.2): FP64 / FP32 stored links, solves on the
                        multi-shift engine, no batched or fused solve + force */

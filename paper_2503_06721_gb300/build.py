@@ -26,7 +26,7 @@ NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "--expt-relaxed-constexpr", "-Xc
 
 PRECS = ["HR_F64", "HR_F32", "HR_F16", "HR_BF16", "HR_DF64"]
 PAIRS = [(2, "HR_FUND"), (2, "HR_ADJ"), (2, "HR_SYM"), (3, "HR_FUND"), (3, "HR_ADJ"), (3, "HR_SYM"),
-         (3, "HR_ASYM"), (4, "HR_FUND"), (4, "HR_ASYM")]
+         (3, "HR_ASYM"), (4, "HR_FUND"), (4, "HR_ASYM"), (4, "HR_ASYM_REAL")]
 # large-N fundamental pairs: colour-parallel hopping kernel, FP64 and FP32
 LARGE_PAIRS = [(5, "HR_FUND"), (6, "HR_FUND"), (8, "HR_FUND")]
 

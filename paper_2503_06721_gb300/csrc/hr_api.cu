@@ -35,7 +35,7 @@ long long launch_counter() { return g_launches.load(); }
 
 // --------------------------- dispatch --------------------------------------
 #define HR_PAIRS(X) X(2, HR_FUND) X(2, HR_ADJ) X(2, HR_SYM) X(3, HR_FUND) X(3, HR_ADJ) X(3, HR_SYM) \
-    X(3, HR_ASYM) X(4, HR_FUND) X(4, HR_ASYM)
+    X(3, HR_ASYM) X(4, HR_FUND) X(4, HR_ASYM) X(4, HR_ASYM_REAL)
 
 #define HR_DECL(N_, R_)                                                                                    \
     extern template hr_status launch_hop<N_, R_, HR_F64>(const HopParams &, bool, int, int, cudaStream_t);     \
@@ -126,7 +126,7 @@ hr_status check_lattice(const hr_lattice_desc *lat)
 {
     if (!lat) { set_error("null lattice descriptor"); return HR_ERR_INVALID; }
     if (lat->N < 2 || lat->N > HR_MAX_N) { set_error("N = %d outside 2..%d", lat->N, HR_MAX_N); return HR_ERR_INVALID; }
-    if (lat->rep < HR_FUND || lat->rep > HR_ASYM) { set_error("bad representation %d", (int)lat->rep); return HR_ERR_INVALID; }
+    if (lat->rep < HR_FUND || lat->rep > HR_ASYM_REAL) { set_error("bad representation %d", (int)lat->rep); return HR_ERR_INVALID; }
     for (int mu = 0; mu < 4; mu++) {
         if (lat->dims[mu] < 2 || (lat->dims[mu] & 1)) {
             set_error("dims[%d] = %d must be even and >= 2", mu, lat->dims[mu]);
@@ -390,7 +390,7 @@ unsigned long long hr_launch_count(void) { return (unsigned long long)g_launches
 
 int hr_rep_dim(int N, hr_rep rep)
 {
-    if (N < 2 || N > HR_MAX_N || rep < HR_FUND || rep > HR_ASYM) return -1;
+    if (N < 2 || N > HR_MAX_N || rep < HR_FUND || rep > HR_ASYM_REAL || (rep == HR_ASYM_REAL && N != 4)) return -1;
     return rep_dim(N, rep);
 }
 
@@ -789,6 +789,20 @@ void rep_generator_table(int N, int rep, double *out)
                             v = v + 2.0 * ((be * ga) * d);
                         }
                     }
+                } else if (rep == HR_ASYM_REAL) {
+                    // R_nm = conj(c_n) c_m sum w v U_ik U_jl -> the same with
+                    // [T_ik delta_jl + delta_ik T_jl]
+                    for (int e1 = 0; e1 < 4; e1++) {
+                        int i = rb_row(n, e1), j = rb_col(n, e1);
+                        for (int e2 = 0; e2 < 4; e2++) {
+                            int k = rb_row(m, e2), l = rb_col(m, e2);
+                            cx<double> d = {0, 0};
+                            if (j == l) d = d + Ta[i * N + k];
+                            if (i == k) d = d + Ta[j * N + l];
+                            v = v + (rb_val(n, e1) * rb_val(m, e2)) * d;
+                        }
+                    }
+                    v = rb_cc(n, rb_c(m, v));
                 } else {
                     for (int e1 = 0; e1 < sb_nent(N, rep, n); e1++) {
                         int i = sb_row(N, rep, n, e1), j = sb_col(N, rep, n, e1);

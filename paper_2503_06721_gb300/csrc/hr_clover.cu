@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(CL_APPLY_THREADS) k_clover_apply(const CloverA
 }
 
 #define HR_CL_PAIRS(X) X(2, HR_FUND) X(2, HR_ADJ) X(2, HR_SYM) X(3, HR_FUND) X(3, HR_ADJ) X(3, HR_SYM) \
-    X(3, HR_ASYM) X(4, HR_FUND) X(4, HR_ASYM)
+    X(3, HR_ASYM) X(4, HR_FUND) X(4, HR_ASYM) X(4, HR_ASYM_REAL)
 
 }  // namespace
 

@@ -144,6 +144,7 @@ hr_status represent_launch(const hr_gauge &gg, const double2 *UF, cudaStream_t s
 // D_R^2 products of K itself.
 
 // M = sum_n x_n e_n (SYM/2AS) or sum_a x_a T^a (ADJ); conj_x: use conj(x_n)
+// (for the complex real-basis matrices f_n of the SU(4) 2AS: conj(sum x_n f_n))
 template <int N, int REP, bool CONJ_X>
 __device__ __forceinline__ void rep_matrix(const cx<double> (&x)[rep_dim(N, REP)], cx<double> (&M)[N][N])
 {
@@ -159,6 +160,17 @@ __device__ __forceinline__ void rep_matrix(const cx<double> (&x)[rep_dim(N, REP)
                 constexpr int e = decltype(EE)::value;
                 cx<double> &m = M[gen_row(N, a, e)][gen_col(N, a, e)];
                 cmac(m, gen_val<double>(N, a, e), xa);
+            });
+        });
+    } else if constexpr (REP == HR_ASYM_REAL) {
+        // sum_n x_n f_n, f_n = c_n S_n; with CONJ_X its complex conjugate
+        static_for<0, rep_dim(N, REP)>([&](auto NN) {
+            constexpr int n = decltype(NN)::value;
+            const cx<double> t = rb_c(n, x[n]);
+            const cx<double> xn = CONJ_X ? conj(t) : t;
+            static_for<0, 4>([&](auto EE) {
+                constexpr int e = decltype(EE)::value;
+                rmac(M[rb_row(n, e)][rb_col(n, e)], rb_val(n, e), xn);
             });
         });
     } else {

@@ -6,8 +6,8 @@
 //             slot k = 0..3 : U_R(x, mu=k)            (forward hop)
 //             slot k = 4..7 : U_R(x - mu, mu)^dag     (backward hop, mu = k-4)
 //           stored as AoSoA tiles of 32 sites:  [tile][slot][component][lane]
-//           (component = complex entry r*D+c, or real entry for the real ADJ
-//           representation).  One warp streams one tile with fully coalesced
+//           (component = complex entry r*D+c, or real entry for the real
+//           representations: ADJ and the real-basis SU(4) 2AS).  One warp streams one tile with fully coalesced
 //           loads; each link is stored twice (once per endpoint parity), which
 //           HBM capacity allows and which turns every link read into a
 //           contiguous stream.
@@ -172,7 +172,8 @@ __host__ __device__ constexpr int rep_dim(int N, int rep)
 {
     return rep == HR_FUND ? N : rep == HR_ADJ ? N * N - 1 : rep == HR_SYM ? N * (N + 1) / 2 : N * (N - 1) / 2;
 }
-__host__ __device__ constexpr bool rep_real(int rep) { return rep == HR_ADJ; }
+// representations whose links are real in the library's basis (stored as reals)
+__host__ __device__ constexpr bool rep_real(int rep) { return rep == HR_ADJ || rep == HR_ASYM_REAL; }
 
 // the p-th pair (j,k), j<k, in lexicographic order
 __host__ __device__ constexpr int pair_j(int N, int p)

@@ -61,6 +61,34 @@ __host__ __device__ inline double sb_val(int N, int rep, int n, int e)
     return (rep == HR_ASYM && e == 1) ? -HR_RSQRT2 : HR_RSQRT2;
 }
 
+// --- the real basis of the SU(4) 2AS (HR_ASYM_REAL): f_n = c_n S_n with
+// c_n = 1 (n even) or i (n odd) and S_n real antisymmetric, entries +-1/2 at
+// (P0,P1), (P1,P0), (Q0,Q1), (Q1,Q0) for the k-th pair P with complement Q:
+//   f_2k = (e_P + s_k e_Q)/sqrt2,  f_2k+1 = i (e_P - s_k e_Q)/sqrt2,
+//   (P, Q, s) = ((0,1),(2,3),+1), ((0,2),(1,3),-1), ((0,3),(1,2),+1).
+// Each f_n is fixed by A -> *conj(A), (*A)_ij = eps_ijkl A_kl / 2, which
+// commutes with A -> U A U^T when det U = 1, so R(U) is real in this basis.
+__host__ __device__ constexpr int rb_p(int k, int j) { return j == 0 ? 0 : k + 1; }
+__host__ __device__ constexpr int rb_q(int k, int j) { return k == 0 ? 2 + j : k == 1 ? 1 + 2 * j : 1 + j; }
+__host__ __device__ constexpr int rb_row(int n, int e)
+{
+    return e == 0 ? rb_p(n / 2, 0) : e == 1 ? rb_p(n / 2, 1) : e == 2 ? rb_q(n / 2, 0) : rb_q(n / 2, 1);
+}
+__host__ __device__ constexpr int rb_col(int n, int e)
+{
+    return e == 0 ? rb_p(n / 2, 1) : e == 1 ? rb_p(n / 2, 0) : e == 2 ? rb_q(n / 2, 1) : rb_q(n / 2, 0);
+}
+// entry e of S_n
+__host__ __device__ constexpr double rb_val(int n, int e)
+{
+    return (e & 1 ? -0.5 : 0.5) * (e < 2 ? 1.0 : ((n & 1) ? -1.0 : 1.0) * (n / 2 == 1 ? -1.0 : 1.0));
+}
+// c_n v for the coordinate v of f_n (i v for odd n), and conj(c_n) v
+template <class R>
+__host__ __device__ __forceinline__ cx<R> rb_c(int n, cx<R> v) { return (n & 1) ? cx<R>{-v.im, v.re} : v; }
+template <class R>
+__host__ __device__ __forceinline__ cx<R> rb_cc(int n, cx<R> v) { return (n & 1) ? cx<R>{v.im, -v.re} : v; }
+
 // --- R(U) as a dense D x D matrix (FP64), U given as N x N ---
 template <int N, int REP>
 __host__ __device__ inline void represent(const cx<double> (&U)[N][N], cx<double> (&Rm)[rep_dim(N, REP)][rep_dim(N, REP)])
@@ -84,6 +112,21 @@ __host__ __device__ inline void represent(const cx<double> (&U)[N][N], cx<double
                     }
                 }
                 Rm[a][b] = {2.0 * s.re, 0.0};
+            }
+    } else if constexpr (REP == HR_ASYM_REAL) {
+        // R_nm = Tr(f_n^dag U f_m U^T) = conj(c_n) c_m sum_{S_n} sum_{S_m} w v U_ik U_jl
+        for (int n = 0; n < D; n++)
+            for (int m = 0; m < D; m++) {
+                cx<double> s = {0, 0};
+                for (int e1 = 0; e1 < 4; e1++) {
+                    const int i = rb_row(n, e1), j = rb_col(n, e1);
+                    const double w = rb_val(n, e1);
+                    for (int e2 = 0; e2 < 4; e2++) {
+                        const int k = rb_row(m, e2), l = rb_col(m, e2);
+                        s = s + (w * rb_val(m, e2)) * (U[i][k] * U[j][l]);
+                    }
+                }
+                Rm[n][m] = rb_cc(n, rb_c(m, s));
             }
     } else {
         // R_nm = sum_{(i,j,w) in e_n} sum_{(k,l,v) in e_m} w v U_ik U_jl
@@ -144,6 +187,15 @@ __device__ __forceinline__ void rep_act(const cx<R> (&F)[N][N], const cx<R> (&v)
                     cmac(X[gen_row(N, a, e)][gen_col(N, a, e)], gen_val<R>(N, a, e), v[a]);
                 });
             });
+        } else if constexpr (REP == HR_ASYM_REAL) {
+            static_for<0, D>([&](auto NN) {
+                constexpr int n = decltype(NN)::value;
+                const cx<R> cv = rb_c(n, v[n]);
+                static_for<0, 4>([&](auto EE) {
+                    constexpr int e = decltype(EE)::value;
+                    rmac(X[rb_row(n, e)][rb_col(n, e)], (R)rb_val(n, e), cv);
+                });
+            });
         } else {
             static_for<0, D>([&](auto NN) {
                 constexpr int n = decltype(NN)::value;
@@ -178,6 +230,21 @@ __device__ __forceinline__ void rep_act(const cx<R> (&F)[N][N], const cx<R> (&v)
                     cmac(s, gen_val<R>(N, a, e), y);
                 });
                 out[a] = (R)2 * s;
+            });
+        } else if constexpr (REP == HR_ASYM_REAL) {
+            // v'_n = Tr(f_n^dag Y) = conj(c_n) sum_{(i,j,w) in S_n} w Y_ij,  Y = Z F^T
+            static_for<0, D>([&](auto NN) {
+                constexpr int n = decltype(NN)::value;
+                cx<R> s = {0, 0};
+                static_for<0, 4>([&](auto EE) {
+                    constexpr int e = decltype(EE)::value;
+                    constexpr int i = rb_row(n, e), j = rb_col(n, e);
+                    cx<R> y = {0, 0};
+#pragma unroll
+                    for (int k = 0; k < N; k++) cmac(y, Z[i][k], F[j][k]);
+                    rmac(s, (R)rb_val(n, e), y);
+                });
+                out[n] = rb_cc(n, s);
             });
         } else {
             // v'_n = sum_{(i,j,w) in e_n} w Y_ij,  Y = Z F^T: Y_ij = sum_k Z_ik F_jk

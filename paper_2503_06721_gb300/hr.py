@@ -20,8 +20,9 @@ import torch
 
 _LIB_PATH = Path(__file__).resolve().parent / "_lib" / "libhr.so"
 
-FUND, ADJ, SYM, ASYM = 0, 1, 2, 3
-REPS = {"FUND": FUND, "ADJ": ADJ, "SYM": SYM, "ASYM": ASYM, "2AS": ASYM}
+FUND, ADJ, SYM, ASYM, ASYM_REAL = 0, 1, 2, 3, 4
+REPS = {"FUND": FUND, "ADJ": ADJ, "SYM": SYM, "ASYM": ASYM, "2AS": ASYM, "ASYM_REAL": ASYM_REAL,
+        "2AS_REAL": ASYM_REAL}
 F64, F32, F16, BF16, DF64 = 0, 1, 2, 3, 4
 PRECS = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16, "df64": DF64}
 EVEN, ODD, FULL, EO_PRECOND = 0, 1, 2, 3

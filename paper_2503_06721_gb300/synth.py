@@ -220,7 +220,7 @@ def gaussian_spinor(nsites: int, D: int, seed: int, stream: int = STREAM_SPINOR,
 class Workload:
     name: str
     N: int
-    rep: str            # FUND / ADJ / SYM / ASYM
+    rep: str            # FUND / ADJ / SYM / ASYM / ASYM_REAL
     dims: tuple         # (T, X, Y, Z)
     m0: float
     eps: float          # link width: U = exp(i eps H)
@@ -256,6 +256,9 @@ WORKLOADS = {
                                      -0.25, 0.4, seed=2503067213),
     "su4_asym_48x24x24x24": Workload("su4_asym_48x24x24x24", 4, "ASYM", (48, 24, 24, 24),
                                      -0.25, 0.4, seed=2503067213),
+    # the same SU(4) 2AS workload with the links in the real basis (stored real)
+    "su4_asym_real_48x24x24x24": Workload("su4_asym_real_48x24x24x24", 4, "ASYM_REAL", (48, 24, 24, 24),
+                                          -0.25, 0.4, seed=2503067213),
     # SU(8) fundamental 24^3 x 48: the colour-parallel (large-N) kernel
     "su8_fund_48x24x24x24": Workload("su8_fund_48x24x24x24", 8, "FUND", (48, 24, 24, 24),
                                      -0.1, 0.4, seed=2503067218),

@@ -14,7 +14,9 @@ from oracle import storage as OS
 from tests import _helpers as H
 
 PAIRS = [(2, "FUND"), (2, "ADJ"), (2, "SYM"), (3, "FUND"), (3, "ADJ"), (3, "SYM"), (3, "ASYM"),
-         (4, "FUND"), (4, "ASYM")]
+         (4, "FUND"), (4, "ASYM"), (4, "ASYM_REAL")]
+# representations whose links the library stores as reals
+REAL_REPS = ("ADJ", "ASYM_REAL")
 
 # per-site relative tolerance (max_x |d(x)| / rms_x |ref(x)|):
 #   FP64 and FP32: the stated parity bar (1e-13 / 1e-5);

@@ -37,6 +37,8 @@ def test_pure_host_calls(lib):
     assert lib.hr_rep_dim(3, hr.SYM) == 6
     assert lib.hr_rep_dim(3, hr.ADJ) == 8
     assert lib.hr_rep_dim(4, hr.ASYM) == 6
+    assert lib.hr_rep_dim(4, hr.ASYM_REAL) == 6
+    assert lib.hr_rep_dim(3, hr.ASYM_REAL) == -1
     assert lib.hr_rep_dim(9, hr.FUND) == -1
     assert lib.hr_rep_dim(8, hr.FUND) == 8
     assert b"HR_ERR_INVALID" in lib.hr_status_string(-1)

@@ -37,3 +37,16 @@ def test_hop_byte_model():
     assert bench.hop_bytes(8, True, 1, vh) == vh * (8 * 256 + 2 * 256)
     # F16 spinors carry a 4-byte scale
     assert bench.hop_bytes(6, False, 2, vh) == vh * (8 * 144 + 2 * (96 + 4))
+
+
+def test_link_and_spinor_bytes():
+    """bytes a launch reads per link and per spinor, by link mode and precision"""
+    import bench
+    # rebuilt links read the N x N fundamental link: SU(3) FP32 72 B, FP64 144 B
+    assert bench.link_bytes(3, 6, "SYM", 1, True) == 72
+    assert bench.link_bytes(3, 8, "ADJ", 0, True) == 144
+    # stored: D_R^2 complex, or D_R^2 real for the adjoint
+    assert bench.link_bytes(3, 6, "SYM", 1, False) == 288
+    assert bench.link_bytes(3, 8, "ADJ", 2, False) == 128
+    assert bench.spinor_bytes(6, 3) == 4 * 6 * 4 + 4
+    assert bench.spinor_bytes(8, 0) == 4 * 8 * 16

@@ -81,7 +81,7 @@ def test_batched_equals_separate(hr, oracle_mod):
         assert G.rel(x.cpu().numpy().reshape(-1, 4, g.lat.D), xs1.cpu().numpy().reshape(-1, 4, g.lat.D)) < 1e-9
 
 
-@pytest.mark.parametrize("rep", ["FUND", "ASYM"])
+@pytest.mark.parametrize("rep", ["FUND", "ASYM", "ASYM_REAL"])
 def test_batched_full_size_su4(hr, oracle_mod, rep):
     """SU(4) 24^3 x 48 with 12 point sources, plus 8^4, 12^4, 16^3 x 32 instances at
     m0 = -0.1, -0.25, -0.4, one batched FP32-inner / FP64-refined solve to 1e-10."""

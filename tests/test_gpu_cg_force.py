@@ -120,7 +120,7 @@ def test_cg_not_converged_and_nonfinite(hr, oracle_mod, cfg1):
     assert st == -5
 
 
-@pytest.mark.parametrize("N,rep", [(3, "SYM"), (2, "ADJ"), (4, "ASYM"), (3, "FUND")])
+@pytest.mark.parametrize("N,rep", [(3, "SYM"), (2, "ADJ"), (4, "ASYM"), (3, "FUND"), (4, "ASYM_REAL")])
 def test_force_parity(hr, oracle_mod, N, rep):
     dims = (4, 4, 2, 6)
     lat = hr.Lattice(N, rep, dims, (-1, 1, 1, 1), -0.1)

@@ -37,7 +37,7 @@ def _case(hr, oracle_mod, N, rep, dims=(4, 4, 2, 6), m0=-0.1, eps=0.6, seed=223,
 
 
 @pytest.mark.parametrize("mode", [1, 2], ids=["clover", "expclover"])
-@pytest.mark.parametrize("N,rep", [(2, "ADJ"), (3, "SYM"), (3, "FUND"), (4, "ASYM"), (2, "FUND")])
+@pytest.mark.parametrize("N,rep", [(2, "ADJ"), (3, "SYM"), (3, "FUND"), (4, "ASYM"), (2, "FUND"), (4, "ASYM_REAL")])
 def test_clover_operator_parity(hr, oracle_mod, N, rep, mode):
     lat, L, U, UR, C, g, Ud = _case(hr, oracle_mod, N, rep, mode=mode)
     V, D = lat.volume, lat.D

@@ -49,7 +49,7 @@ def _kernel_links(oracle_mod, L, UF, UR, rep, prec, mode):
     real adjoint); rebuild mode rounds U_F and the kernel represents that."""
     from oracle import storage as OS
     if mode == 0:
-        return OS.round_links(UR, prec, real=(rep == "ADJ"))
+        return OS.round_links(UR, prec, real=(rep in G.REAL_REPS))
     return oracle_mod.represent_field(L, OS.round_links(UF, prec))
 
 
@@ -119,6 +119,34 @@ def test_field_convert_equals_host_storage(hr, oracle_mod, prec, D_pair):
     back = G.back_to_f64(hr, lat, hr.EVEN, dev, prec, nrhs).cpu().numpy()
     want = OS.round_complex(OS.dequantize(codes, scales), "f32")
     np.testing.assert_array_equal(back, want)
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["stored", "rebuild"])
+def test_asym_real_equivalent_to_asym(hr, oracle_mod, mode):
+    """The library's SU(4) 2AS operator in the real basis (real links, 144 B per
+    FP32 link) is the complex-basis one in rotated colour coordinates:
+    D_real (W^dag psi) = W^dag (D_2AS psi) with the fixed unitary W, for every
+    block and the adjoint, FP64 and FP32."""
+    W = np.einsum("mij,nij->mn", oracle_mod.rep_basis(4, "ASYM").conj(),
+                  oracle_mod.rep_basis(4, "ASYM_REAL"))
+    dims, bc, m0 = DIMS, (-1, 1, 1, -1), -0.23
+    UF = H.links(dims, 4, 0.7, seed=5)
+    lat_c, lat_r = hr.Lattice(4, "ASYM", dims, bc, m0), hr.Lattice(4, "ASYM_REAL", dims, bc, m0)
+    g_c = hr.Gauge(lat_c, G.to_gpu(UF), precs=("f64", "f32"), stored=True, rebuild=True)
+    g_r = hr.Gauge(lat_r, G.to_gpu(UF), precs=("f64", "f32"), stored=True, rebuild=True)
+    g_c.set_link_mode(mode)
+    g_r.set_link_mode(mode)
+    psi = H.spinor(lat_c.volume, 6, 31)
+    rot = lambda x: x @ W.conj()
+    for prec, dt in ((hr.F64, torch.complex128), (hr.F32, torch.complex64)):
+        for par in (hr.EVEN, hr.ODD, hr.FULL, hr.EO_PRECOND):
+            x = psi if par == hr.FULL else psi[: lat_c.volume // 2]
+            for dagger in (False, True):
+                yc = g_c.apply(par, prec, G.to_gpu(x, dt), dagger=dagger).to(torch.complex128).cpu().numpy()
+                yr = g_r.apply(par, prec, G.to_gpu(rot(x), dt), dagger=dagger).to(torch.complex128).cpu().numpy()
+                assert G.rel(yr, rot(yc)) <= 2 * G.TOL[prec], (prec, par, dagger)
+    g_c.close()
+    g_r.close()
 
 
 def test_rebuild_equals_stored_f64(hr, oracle_mod):

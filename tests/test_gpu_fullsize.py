@@ -70,7 +70,7 @@ def _sampled_check(hr, oracle_mod, wl, U, x_in, y_out, parity, dagger, tol, seed
     if link_prec:
         from oracle import storage as OS
         R = oracle_mod.represent_links(wl.N, wl.rep, Ul.cpu().numpy())
-        R = OS.round_links(R, link_prec, real=(wl.rep == "ADJ"))
+        R = OS.round_links(R, link_prec, real=(wl.rep in G.REAL_REPS))
         ref = oracle_mod.hop_local(L, c.cpu().numpy(), R, ps.cpu().numpy(), dagger, represented=True)
     else:
         ref = oracle_mod.hop_local(L, c.cpu().numpy(), Ul.cpu().numpy(), ps.cpu().numpy(), dagger)
