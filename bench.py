@@ -73,13 +73,17 @@ def hop_bytes(D: int, real_links: bool, prec: int, vh: int, spinor_reads: int = 
     return vh * (8 * lp + (1 + spinor_reads) * sp)
 
 
+# representations whose links are stored as reals
+REAL_REPS = ("ADJ", "ASYM_REAL")
+
+
 def link_bytes(N: int, D: int, rep: str, prec: int, rebuild: bool) -> int:
     """bytes of one link as a launch reads it: D_R^2 complex (D_R^2 real for
     the adjoint), or N^2 complex when rebuilt in the kernel from U_F"""
     cb = [16, 8, 4, 4, 16][prec]
     if rebuild:
         return N * N * cb
-    return D * D * (cb // 2 if rep == "ADJ" else cb)
+    return D * D * (cb // 2 if rep in REAL_REPS else cb)
 
 
 def spinor_bytes(D: int, prec: int) -> int:
@@ -183,7 +187,7 @@ def run_ours(args, rank, world, local_rank):
     wl = synth.WORKLOADS[args.workload]
     lat = hr.Lattice(wl.N, wl.rep, wl.dims, wl.bc, wl.m0)
     vh, D = lat.volume // 2, lat.D
-    real = wl.rep == "ADJ"
+    real = wl.rep in REAL_REPS
     # replicas: every rank draws its own field
     import dataclasses
     wl_r = dataclasses.replace(wl, seed=wl.seed + 1000 * rank)
@@ -411,7 +415,12 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_batched:
         g.close()
         torch.cuda.empty_cache()
-        batched = batched_compare(hr, synth, dev, stream)
+        # SU(4) 24^3 x 48 + uneven instances: the 2AS in the real basis (real
+        # links) and the fundamental with every comparison, the 2AS in the
+        # complex basis with the batched mixed solve only
+        batched = {"ASYM_REAL": batched_compare(hr, synth, dev, stream, rep="ASYM_REAL"),
+                   "FUND": batched_compare(hr, synth, dev, stream, rep="FUND"),
+                   "ASYM": batched_compare(hr, synth, dev, stream, rep="ASYM", mixed_only=True)}
 
     by_rep = None
     if rank == 0 and not args.no_deo_by_rep:
@@ -478,8 +487,9 @@ def run_ours(args, rank, world, local_rank):
 
 def multishift_compare(hr, g, phi, stream, m0):
     """The RHMC's multi-shift inversion (Sec. 4.3.2) on the bench lattice:
-    (A + b_k) x_k = phi for the 10 poles b_k of the Zolotarev approximation of
-    x^(-1/2) on [0.1, ((4+m)^2 + 16)^2] (relative error 1e-7; the upper end
+    (A + b_k) x_k = phi for the 10 poles b_k of the best relative
+    approximation of x^(-1/2) on [0.1, ((4+m)^2 + 16)^2] (hr_rational_approx,
+    relative error 1e-7; the upper end
     bounds the spectrum of A = Dhat^dag Dhat), each to a true residual of
     1e-10: multi-shift CG in FP64 and with FP32 iterations + FP64 correction,
     against plain FP64 shifted CG solving one pole after another (the
@@ -489,10 +499,10 @@ def multishift_compare(hr, g, phi, stream, m0):
 
     from paper_2503_06721_gb300 import rational
     m4 = 4.0 + m0
-    ra = rational.zolotarev_inv_sqrt(10, 0.1, (m4 * m4 + 16.0) ** 2)
+    ra = rational.approx(0.5, 10, 0.1, (m4 * m4 + 16.0) ** 2)
     MS_SHIFTS = list(ra.poles)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    out = {"approx": f"Zolotarev x^-1/2, degree 10, [0.1, {ra.hi:.1f}], rel. error {ra.max_rel_err:.2e}",
+    out = {"approx": f"best x^-1/2 (Remez), degree 10, [0.1, {ra.hi:.1f}], rel. error {ra.max_rel_err:.2e}",
            "shifts": [float(f"{s:.6g}") for s in MS_SHIFTS]}
     for name, inner in (("multishift_fp64", hr.F64), ("multishift_mixed_fp32", hr.F32)):
         g.cg_solve_multishift(hr.EO_PRECOND, phi, MS_SHIFTS, tol=1e-3, inner=inner, check=False)
@@ -580,6 +590,8 @@ DEO_CASES = [
      ("stored", "rebuild")),
     ("su4_fund_48x24x24x24", 4, "FUND", (48, 24, 24, 24), -0.25, 0.4, ("f32", "f16", "bf16"), ("stored",)),
     ("su4_asym_48x24x24x24", 4, "ASYM", (48, 24, 24, 24), -0.25, 0.4, ("f32", "f16", "bf16"),
+     ("stored", "rebuild")),
+    ("su4_asym_real_48x24x24x24", 4, "ASYM_REAL", (48, 24, 24, 24), -0.25, 0.4, ("f32", "f16", "bf16"),
      ("stored", "rebuild")),
 ]
 
@@ -756,7 +768,7 @@ def hmc_measure(hr, lat, U, dev, stream, beta=5.5, tau=0.5, nsteps=4):
             "H0": [round(h, 4) for h in H0], "dH": round(sum(H1) - sum(H0), 6)}
 
 
-def batched_compare(hr, synth, dev, stream, rep="ASYM"):
+def batched_compare(hr, synth, dev, stream, rep="ASYM", mixed_only=False):
     """SU(4) 24^3 x 48 with 12 point sources (4 spins x 3 colour subsets) plus
     8^4, 12^4, 16^3 x 32 instances (4 Gaussian rhs each, m0 = -0.1, -0.25, -0.4):
     one batched FP32-inner / FP64-refined solve to 1e-10 against plain FP64 CG
@@ -784,8 +796,9 @@ def batched_compare(hr, synth, dev, stream, rep="ASYM"):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = {"workload": f"SU(4) {rep} 24^3x48 (12 point sources) + 8^4, 12^4, 16^3x32 (4 rhs each)",
            "rhs_total": sum(nr)}
-    for name, inner, resid in (("batched_mixed_fp32", hr.F32, hr.F64), ("batched_mixed_fp32_df64res", hr.F32, hr.DF64),
-                               ("batched_fp64", hr.F64, hr.F64)):
+    runs = (("batched_mixed_fp32", hr.F32, hr.F64), ("batched_mixed_fp32_df64res", hr.F32, hr.DF64),
+            ("batched_fp64", hr.F64, hr.F64))
+    for name, inner, resid in runs[:1] if mixed_only else runs:
         xs = [torch.zeros_like(b) for b in bs]
         hr.cg_solve_batched(gauges, hr.EO_PRECOND, bs, xs, nr, tol=1e-3, inner=inner, residual=resid,
                             check=False)
@@ -799,6 +812,25 @@ def batched_compare(hr, synth, dev, stream, rep="ASYM"):
         out[name] = {"ms": round(e0.elapsed_time(e1), 2), "status": hr.STATUS.get(st, st),
                      "max_true_rel_residual": max(r["true_rel_residual"] for r in res),
                      "max_iters": max(r["iters"] for r in res)}
+    # the same mixed solves instance by instance (each instance's right-hand
+    # sides together): the gain of batching over per-instance mixed solves
+    for g, b, n in zip(gauges, bs, nr):
+        g.cg_solve(hr.EO_PRECOND, b, nrhs=n, tol=1e-3, inner=hr.F32, check=False)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    worst = 0.0
+    for g, b, n in zip(gauges, bs, nr):
+        x, r, st = g.cg_solve(hr.EO_PRECOND, b, nrhs=n, tol=TOL, inner=hr.F32, inner_tol=1e-5, check=False)
+        worst = max([worst] + [q["true_rel_residual"] for q in r])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["per_instance_mixed_fp32"] = {"ms": round(e0.elapsed_time(e1), 2), "max_true_rel_residual": worst}
+    out["speedup_batched_vs_per_instance_mixed"] = round(
+        out["per_instance_mixed_fp32"]["ms"] / out["batched_mixed_fp32"]["ms"], 2)
+    if mixed_only:
+        for g in gauges:
+            g.close()
+        return out
     # plain FP64 CG, one right-hand side at a time
     torch.cuda.synchronize()
     e0.record(stream)
@@ -845,7 +877,7 @@ def cpu_baseline(wl, budget_s=15.0, dims=(32, 16, 16, 16)):
         el = time.perf_counter() - t0
         if el >= budget_s or (n >= 1 and el * (n + 1) / n > 2 * budget_s):
             break
-    byts = hop_bytes(D, wl.rep == "ADJ", 0, V // 2)
+    byts = hop_bytes(D, wl.rep in REAL_REPS, 0, V // 2)
     return {"value": round(n * byts / el / 1e9, 3), "unit": UNIT, "cores": oracle.num_threads(),
             "kind": "oracle",
             "sample": f"FP64 oracle D_eo on a {dims[3]}^3x{dims[0]} sub-lattice of the workload, "
@@ -878,7 +910,7 @@ def run_reference(args, rank, world):
         Xp = oracle.merge(L, x, oracle.hop_parity(L, UR, 1, x))
         Yp = oracle.merge(L, Y, oracle.hop_parity(L, UR, 1, Y, dagger=True))
         oracle.force(L, UR, Xp, Yp)
-        byts["b"] += (4 * (it + 2) + 2 + 2) * hop_bytes(D, wl.rep == "ADJ", 0, V // 2)
+        byts["b"] += (4 * (it + 2) + 2 + 2) * hop_bytes(D, wl.rep in REAL_REPS, 0, V // 2)
 
     for _ in range(args.warmup):
         step()
@@ -942,10 +974,7 @@ def run_deo(args, local_rank):
     ms = e0.elapsed_time(e1) / args.steps
     cb = [16, 8, 4, 4, 16][prec]
     sp = 4 * lat.D * cb + (4 if prec in (hr.F16, hr.BF16) else 0)
-    if args.rebuild:
-        lp = wl.N * wl.N * cb
-    else:
-        lp = lat.D * lat.D * (cb // 2 if wl.rep == "ADJ" else cb)
+    lp = link_bytes(wl.N, lat.D, wl.rep, prec, args.rebuild)
     # compulsory bytes: every link once, every input and output spinor once
     byts = vh * (8 * lp + 2 * n * sp)
     print(json.dumps({"mode": "deo", "workload": args.workload, "prec": args.prec, "nrhs": n,

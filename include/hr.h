@@ -384,6 +384,30 @@ hr_status hr_field_lincomb(const hr_lattice_desc *lat, hr_parity par,
                            const double *a, const void *x, void *y, int nrhs,
                            void *stream);
 
+/* RHMC rational approximation (Sec. 4.3.2: the rational functions of Q^2
+ * whose poles become the multi-shift CG's shifts, with coefficients from the
+ * Remez algorithm): the best relative approximation of degree (n, n),
+ *     r(x) = a0 + sum_k res[k] / (x + poles[k])  ~  x^(-alpha)  on [lo, hi],
+ * i.e. the one minimising max |r(x) x^alpha - 1|, found by a Remez exchange
+ * (the error levelled on 2n + 2 alternating reference points by Newton's
+ * method on the factored form, then the reference moved to the error's
+ * extrema, with continuation in the degree).  Powers: alpha = 1/2 for the
+ * one-flavour action and force ((Q^2)^(-1/2)), alpha = -1/4 for its heat
+ * bath ((Q^2)^(1/4)), and any other 0 < |alpha| < 1.
+ *   n          1..64
+ *   0 < lo < hi  the interval (it must contain the spectrum of A)
+ *   a0, max_rel_err  HOST doubles; res, poles  HOST arrays of n doubles,
+ *              poles ascending and positive (pass them as the shifts of
+ *              hr_cg_solve_multishift, then a0 and res to hr_field_lincomb)
+ *   max_rel_err  max |r(x) x^alpha - 1| over [lo, hi] (evaluated in FP64;
+ *              near 1e-13 the evaluation's rounding floor)
+ * Host computation only (no GPU work, no stream).
+ * Errors: HR_ERR_INVALID; HR_ERR_NOT_CONVERGED if the exchange cannot level
+ * the error (a degree beyond what FP64 resolves on [lo, hi]). */
+hr_status hr_rational_approx(double alpha, int n, double lo, double hi,
+                             double *a0, double *res, double *poles,
+                             double *max_rel_err);
+
 /* ------------------------------------------------------------------ */
 /* HMC building blocks (Sec. 2.4, Sec. 2.5, Sec. 4.2)                    */
 /* ------------------------------------------------------------------ */
@@ -445,6 +469,33 @@ typedef struct {
 hr_status hr_md_trajectory(hr_gauge *g, void *U_fund, double *pi,
                            const void *phi, const hr_md_params *p,
                            hr_md_stats *stats, void *stream);
+
+typedef struct {
+    double H0[3], H1[3];   /* (H_pi, S_g, S_f) before and after the trajectory */
+    double dH;             /* sum(H1) - sum(H0) */
+    int accepted;          /* 1 if u_accept < exp(-dH) */
+    hr_md_stats md;        /* the trajectory's statistics */
+} hr_hmc_result;
+
+/* One HMC update (Sec. 2.5): the pseudofermion heat bath phi = Dhat^dag eta
+ * (D^dag eta for sys = HR_FULL), H = H_pi + S_g + S_f before, one MD
+ * trajectory (hr_md_trajectory), H after, and the Metropolis test: the new
+ * links are kept if u_accept < exp(-dH), otherwise U_fund is restored.  The
+ * random draws are the caller's:
+ *   pi        DEVICE heat-bath momenta pi^a ~ N(0, 1/T_F) (FP64 [V][4][N*N-1]);
+ *             on return the trajectory's final momenta
+ *   eta       DEVICE complex Gaussian field of p->sys (FP64, Re and Im each
+ *             N(0, 1/2)); NULL for the pure gauge theory
+ *   u_accept  uniform draw in [0, 1) (any finite value >= 1 rejects: a
+ *             forced rejection)
+ * S_f = phi^dag A^-1 phi is formed by a solve (p->cg with the tolerance
+ * min(p->cg.tol_rel, 1e-11)) and hr_field_dot, before and after.  g
+ * represents U_fund on return, accepted or not.  Takes device scratch for a
+ * copy of U_fund and two fields (cudaMallocAsync on stream).  BLOCKS.
+ * Errors: those of the calls it makes; HR_ERR_INVALID for bad arguments. */
+hr_status hr_hmc_update(hr_gauge *g, void *U_fund, double *pi, const void *eta,
+                        double u_accept, const hr_md_params *p,
+                        hr_hmc_result *res, void *stream);
 
 /* ------------------------------------------------------------------ */
 /* Fermion force (Sec. 2.5)                                              */

@@ -33,7 +33,8 @@ LARGE_PAIRS = [(5, "HR_FUND"), (6, "HR_FUND"), (8, "HR_FUND")]
 
 def _units():
     units = []
-    for src in ("hr_api.cu", "hr_cg.cu", "hr_mscg.cu", "hr_hmc.cu", "hr_clover.cu", "hr_blas.cu", "hr_static.cu", "hr_tune.cu"):
+    for src in ("hr_api.cu", "hr_cg.cu", "hr_mscg.cu", "hr_hmc.cu", "hr_clover.cu", "hr_blas.cu", "hr_static.cu", "hr_tune.cu",
+                "hr_rational.cu"):
         units.append((CSRC / src, OBJDIR / (Path(src).stem + ".o"), []))
     for n, rep in PAIRS:
         tag = f"{n}_{rep.lower()[3:]}"

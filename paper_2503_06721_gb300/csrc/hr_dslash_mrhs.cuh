@@ -175,8 +175,8 @@ __global__ void __launch_bounds__(128, MINB) hop_mrhs_kernel(const HopParams prm
                     cx<R> up = rec_comp<P>(rec, r * D + c);
                     cx<R> dn = rec_comp<P>(rec, (2 + eperm(mu, r)) * D + c);
                     if constexpr (S::scaled) {
-                        up = sc * up;
-                        dn = sc * dn;
+                        up = scale_rn(sc, up);
+                        dn = scale_rn(sc, dn);
                     }
                     h[r][c] = up + sp * ipow(ephase(mu, r), dn);
                 }
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(128, MINB) hop_mrhs_kernel(const HopParams prm
 #pragma unroll
             for (int c = 0; c < D; c++) {
                 cx<R> d = rec_comp<P>(own(8), s * D + c);
-                if constexpr (S::scaled) d = dsc * d;
+                if constexpr (S::scaled) d = scale_rn(dsc, d);
                 acc[s][c] = axpby(a, acc[s][c], b, d);
             }
     } else {
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(128, MINB) hop_mrhs_kernel(const HopParams prm
                 const int n = j * CPC + q;
                 cx<RC> xx = rec_comp<PC>(&v, q);
                 cx<R> pp = rec_comp<P>(own(8), n);
-                if constexpr (S::scaled) pp = psc * pp;
+                if constexpr (S::scaled) pp = scale_rn(psc, pp);
                 rmac(xx, alpha, pp);
                 if constexpr (PC == HR_F64) {
                     v = make_uint4((unsigned)__double2loint(xx.re), (unsigned)__double2hiint(xx.re),

@@ -70,7 +70,7 @@ struct SpinorIO {
 #pragma unroll
             for (int c = 0; c < D; c++) {
                 cx<R> v = comp(raw, s * D + c);
-                if constexpr (S::scaled) v = sc * v;
+                if constexpr (S::scaled) v = scale_rn(sc, v);
                 psi[s][c] = v;
             }
     }
@@ -88,7 +88,7 @@ struct SpinorIO {
 #pragma unroll
             for (int c = 0; c < D; c++) {
                 cx<R> v = comp(raw, s * D + c);
-                if constexpr (S::scaled) v = sc * v;
+                if constexpr (S::scaled) v = scale_rn(sc, v);
                 psi[s][c] = v;
             }
     }
@@ -110,7 +110,7 @@ struct SpinorIO {
                 const float2 d = *reinterpret_cast<const float2 *>(b + 8 * c);
                 v[c] = {d.x, d.y};
             } else {
-                v[c] = sc * S::ld(*reinterpret_cast<const typename S::C *>(b + 4 * c));
+                v[c] = scale_rn(sc, S::ld(*reinterpret_cast<const typename S::C *>(b + 4 * c)));
             }
         }
     }

@@ -513,4 +513,72 @@ hr_status hr_md_trajectory(hr_gauge *g, void *U_fund, double *pi, const void *ph
     return st;
 }
 
+// H = (H_pi, S_g, S_f) for the links g represents (= U_fund); S_f =
+// phi^dag A^-1 phi by one solve (to min(tol, 1e-11)) and one dot product
+static hr_status hamiltonian(hr_gauge *g, const void *U_fund, const double *pi, const void *phi, void *x,
+                             const hr_md_params *p, double H[3], void *stream)
+{
+    hr_status st = hr_momenta_energy(&g->lat, pi, &H[0], stream);
+    if (st == HR_OK) st = hr_gauge_action(&g->lat, U_fund, p->beta, &H[1], stream);
+    H[2] = 0;
+    if (st != HR_OK || !phi) return st;
+    hr_cg_params cg = p->cg;
+    cg.tol_rel = std::min(cg.tol_rel, 1e-11);
+    cg.use_initial_guess = 0;
+    hr_cg_result r;
+    st = hr_cg_solve(g, p->sys, phi, x, 1, &cg, &r, stream);
+    if (st != HR_OK) return st;
+    double d[2];
+    st = hr_field_dot(&g->lat, p->sys == HR_FULL ? HR_FULL : HR_EVEN, HR_F64, phi, x, 1, d, stream);
+    H[2] = d[0];
+    return st;
+}
+
+hr_status hr_hmc_update(hr_gauge *g, void *U_fund, double *pi, const void *eta, double u_accept,
+                        const hr_md_params *p, hr_hmc_result *res, void *stream)
+{
+    if (!g || !U_fund || !pi || !p || !res || !(u_accept >= 0.0) || !std::isfinite(u_accept) ||
+        (eta && p->sys != HR_EO_PRECOND && p->sys != HR_FULL)) {
+        set_error("hr_hmc_update: bad arguments");
+        return HR_ERR_INVALID;
+    }
+    hr_status st = check_gauge_lat(&g->lat);
+    if (st != HR_OK) return st;
+    memset(res, 0, sizeof *res);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const hr_lattice_desc &lat = g->lat;
+    const long V = lat_volume(lat);
+    const long ns = p->sys == HR_FULL ? V : V / 2;
+    const size_t fb = eta ? field_rhs_bytes(ns, g->D, HR_F64) : 0;
+    const size_t ub = (size_t)V * 4 * lat.N * lat.N * 16;
+    // [U_fund before the trajectory][phi][x]
+    char *buf = nullptr;
+    HR_CUDA_CHECK(cudaMallocAsync((void **)&buf, ub + 2 * fb, s));
+    struct Free {
+        char *p;
+        cudaStream_t s;
+        ~Free()
+        {
+            if (p) cudaFreeAsync(p, s);
+        }
+    } fbuf{buf, s};
+    void *U0 = buf, *phi = eta ? buf + ub : nullptr, *x = eta ? buf + ub + fb : nullptr;
+    if ((st = kernel_copy(U0, U_fund, ub, s)) != HR_OK) return st;
+    // pseudofermion heat bath: phi = Dhat^dag eta (D^dag eta), so that
+    // phi^dag (Dhat^dag Dhat)^-1 phi = eta^dag eta
+    if (eta && (st = hr_dirac_dagger(g, p->sys, HR_F64, eta, phi, 1, stream)) != HR_OK) return st;
+    if ((st = hamiltonian(g, U_fund, pi, phi, x, p, res->H0, stream)) != HR_OK) return st;
+    if ((st = hr_md_trajectory(g, U_fund, pi, phi, p, &res->md, stream)) != HR_OK) return st;
+    if ((st = hamiltonian(g, U_fund, pi, phi, x, p, res->H1, stream)) != HR_OK) return st;
+    res->dH = (res->H1[0] + res->H1[1] + res->H1[2]) - (res->H0[0] + res->H0[1] + res->H0[2]);
+    // Metropolis: accept with probability min(1, exp(-dH))
+    res->accepted = std::isfinite(res->dH) && u_accept < std::exp(-res->dH);
+    if (!res->accepted) {
+        if ((st = kernel_copy(U_fund, U0, ub, s)) != HR_OK) return st;
+        if ((st = hr_gauge_update(g, U_fund, stream)) != HR_OK) return st;
+    }
+    HR_CUDA_CHECK(cudaStreamSynchronize(s));
+    return HR_OK;
+}
+
 }  // extern "C"

@@ -92,6 +92,12 @@ __host__ __device__ __forceinline__ void norm_acc(R &n2, cx<R> v)
     n2 = fma(v.re, v.re, n2);
     n2 = fma(v.im, v.im, n2);
 }
+// s * v with each part rounded once and never fused into a following add:
+// the dequantisation of per-site scaled (F16/BF16) values.  Left as a plain
+// product, the compiler may contract it into the next addition in one kernel
+// variant and not in another; written this way every variant rounds it alike.
+__device__ __forceinline__ cx<float> scale_rn(float s, cx<float> v) { return {__fmul_rn(s, v.re), __fmul_rn(s, v.im)}; }
+
 // multiply by i^k, k known at compile time after unrolling
 template <class R>
 __host__ __device__ __forceinline__ cx<R> ipow(int k, cx<R> a)

@@ -40,8 +40,8 @@ EXPORTS = ["hr_represent_gauge", "hr_gauge_update", "hr_gauge_set_link_mode", "h
            "hr_field_bytes", "hr_field_convert", "hr_field_dot", "hr_field_dot_static",
            "hr_dirac_apply", "hr_dirac_dagger",
            "hr_cg_solve", "hr_cg_solve_batched", "hr_cg_solve_force", "hr_cg_solve_multishift",
-           "hr_field_lincomb", "hr_dirac_force", "hr_gauge_action", "hr_gauge_force", "hr_link_update",
-           "hr_momenta_energy", "hr_md_trajectory", "hr_gauge_set_clover", "hr_rep_dim", "hr_generators",
+           "hr_field_lincomb", "hr_rational_approx", "hr_dirac_force", "hr_gauge_action", "hr_gauge_force", "hr_link_update",
+           "hr_momenta_energy", "hr_md_trajectory", "hr_hmc_update", "hr_gauge_set_clover", "hr_rep_dim", "hr_generators",
            "hr_status_string", "hr_last_error", "hr_launch_count"]
 
 
@@ -75,6 +75,11 @@ class MdParams(ctypes.Structure):
 class MdStats(ctypes.Structure):
     _fields_ = [("force_evals", ctypes.c_int), ("cg_iters", ctypes.c_int),
                 ("max_true_rel_residual", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+class HmcResult(ctypes.Structure):
+    _fields_ = [("H0", ctypes.c_double * 3), ("H1", ctypes.c_double * 3), ("dH", ctypes.c_double),
+                ("accepted", ctypes.c_int), ("md", MdStats)]
 
 
 MD_LEAPFROG, MD_OMELYAN2 = 0, 1
@@ -122,11 +127,14 @@ def load():
         "hr_cg_solve_multishift": (I, [P, I, P, P, I, ctypes.POINTER(D), I, ctypes.POINTER(CgParams),
                                        ctypes.POINTER(CgResult), P]),
         "hr_field_lincomb": (I, [LP, I, D, P, I, ctypes.POINTER(D), P, P, I, P]),
+        "hr_rational_approx": (I, [D, I, D, D, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D),
+                                   ctypes.POINTER(D)]),
         "hr_gauge_action": (I, [LP, P, D, ctypes.POINTER(D), P]),
         "hr_gauge_force": (I, [LP, P, D, D, P, P]),
         "hr_link_update": (I, [LP, P, P, D, P]),
         "hr_momenta_energy": (I, [LP, P, ctypes.POINTER(D), P]),
         "hr_md_trajectory": (I, [P, P, P, P, ctypes.POINTER(MdParams), ctypes.POINTER(MdStats), P]),
+        "hr_hmc_update": (I, [P, P, P, P, D, ctypes.POINTER(MdParams), ctypes.POINTER(HmcResult), P]),
         "hr_gauge_set_clover": (I, [P, P, D, I, P]),
         "hr_cg_solve_force": (I, [P, I, P, P, ctypes.POINTER(CgParams), ctypes.POINTER(CgResult), P, D, P, P]),
         "hr_rep_dim": (I, [I, I]),
@@ -251,6 +259,16 @@ def field_lincomb(lat: Lattice, parity: int, a0: float, b, coeffs, x, y=None, nr
     return y
 
 
+def rational_approx(alpha: float, n: int, lo: float, hi: float):
+    """(a0, residues, poles, max_rel_err) of the best degree-(n, n) relative
+    approximation of x^(-alpha) on [lo, hi] (hr_rational_approx)."""
+    a0, err = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    res, poles = (ctypes.c_double * n)(), (ctypes.c_double * n)()
+    _check(load().hr_rational_approx(float(alpha), int(n), float(lo), float(hi), ctypes.byref(a0), res, poles,
+                                     ctypes.byref(err)))
+    return a0.value, tuple(res), tuple(poles), err.value
+
+
 def rational_apply(g, sys: int, b, approx, nrhs: int = 1, tol: float = 1e-10, inner: int = F64,
                    inner_tol: float = 1e-5, stream=None):
     """r(A) b = a0 b + sum_k a_k (A + b_k)^-1 b for a RationalApprox (the RHMC's
@@ -329,24 +347,21 @@ def hamiltonian(g, U_fund, pi, phi, beta: float, sys: int = EO_PRECOND, tol: flo
 def hmc_trajectory(g, U_fund, pi, eta, beta: float, tau: float, nsteps: int, u_accept: float,
                    integrator: int = MD_OMELYAN2, sys: int = EO_PRECOND, tol: float = 1e-10,
                    inner: int = F64, inner_tol: float = 1e-5, stream=None) -> dict:
-    """One HMC update (Sec. 2.5): pseudofermion heat bath phi = Dhat^dag eta
-    (D^dag eta for sys = FULL), H before, one MD trajectory, H after, and the
-    Metropolis test exp(-dH) > u_accept.  pi (heat-bath momenta, pi^a ~
-    N(0, 1/T_F)), eta (Gaussian) and u_accept (uniform in [0, 1)) are the
-    caller's random draws.  On acceptance U_fund holds the new links; on
-    rejection it is restored.  g represents U_fund on return."""
-    phi = g.apply(sys, F64, eta, dagger=True)
-    U0 = U_fund.clone()
-    H0 = hamiltonian(g, U_fund, pi, phi, beta, sys, tol=min(tol, 1e-11), inner=inner, stream=stream)
-    st = md_trajectory(g, U_fund, pi, phi, beta, tau, nsteps, integrator, sys, tol, inner, inner_tol,
-                       stream=stream)
-    H1 = hamiltonian(g, U_fund, pi, phi, beta, sys, tol=min(tol, 1e-11), inner=inner, stream=stream)
-    dH = sum(H1) - sum(H0)
-    accepted = bool(u_accept < min(1.0, float(np.exp(-dH))))
-    if not accepted:
-        U_fund.copy_(U0)
-        g.update(U_fund, stream=stream)
-    return dict(dH=dH, accepted=accepted, H0=H0, H1=H1, **st)
+    """One HMC update (Sec. 2.5, hr_hmc_update): pseudofermion heat bath phi =
+    Dhat^dag eta (D^dag eta for sys = FULL), H before, one MD trajectory, H
+    after, and the Metropolis test exp(-dH) > u_accept.  pi (heat-bath
+    momenta, pi^a ~ N(0, 1/T_F)), eta (Gaussian, or None for the pure gauge
+    theory) and u_accept (uniform in [0, 1)) are the caller's random draws.
+    On acceptance U_fund holds the new links; on rejection it is restored.  g
+    represents U_fund on return."""
+    p = MdParams(float(beta), float(tau), int(nsteps), int(integrator), int(sys),
+                 CgParams(tol, 100000, inner, inner_tol, 0, F64))
+    r = HmcResult()
+    _check(load().hr_hmc_update(g.handle, _ptr(U_fund), _ptr(pi), _ptr(eta), float(u_accept), ctypes.byref(p),
+                                ctypes.byref(r), _stream(stream)))
+    return dict(dH=r.dH, accepted=bool(r.accepted), H0=tuple(r.H0), H1=tuple(r.H1),
+                force_evals=r.md.force_evals, cg_iters=r.md.cg_iters,
+                max_true_rel_residual=r.md.max_true_rel_residual)
 
 
 def _prec_mask(precs) -> int:

@@ -48,5 +48,6 @@ def test_link_and_spinor_bytes():
     # stored: D_R^2 complex, or D_R^2 real for the adjoint
     assert bench.link_bytes(3, 6, "SYM", 1, False) == 288
     assert bench.link_bytes(3, 8, "ADJ", 2, False) == 128
+    assert bench.link_bytes(4, 6, "ASYM_REAL", 1, False) == 144
     assert bench.spinor_bytes(6, 3) == 4 * 6 * 4 + 4
     assert bench.spinor_bytes(8, 0) == 4 * 8 * 16

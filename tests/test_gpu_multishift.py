@@ -170,7 +170,7 @@ def test_rational_apply(hr, oracle_mod, case, inner):
     from paper_2503_06721_gb300 import rational
     lat, L, UR, g = case
     m4 = 4 + L.m0
-    ra = rational.zolotarev_inv_sqrt(8, 1e-3, (m4 * m4 + 16) ** 2)
+    ra = rational.approx(0.5, 8, 1e-3, (m4 * m4 + 16) ** 2)
     b = H.spinor(lat.nsites(hr.EVEN), lat.D, 101)
     y, x, res = hr.rational_apply(g, hr.EO_PRECOND, G.to_gpu(b), ra, tol=1e-11, inner=inner)
     assert all(r[0]["status"] == "HR_OK" for r in res)
@@ -200,3 +200,43 @@ def test_solver_counters_left_clean(hr, oracle_mod, case):
         true_rel = np.linalg.norm(r) / np.linalg.norm(b)
         assert true_rel <= 1e-10 * 1.001, (k, true_rel)
         assert abs(res[k][0]["true_rel_residual"] - true_rel) <= 0.05 * true_rel + 1e-15, (k, res[k][0])
+
+
+@pytest.mark.parametrize("inner", [0, 1], ids=["f64", "f32"])
+def test_rhmc_heat_bath_against_dense_powers(hr, oracle_mod, inner):
+    """One-flavour RHMC on the GPU (Sec. 4.3.2): the heat bath phi =
+    r_{-1/4}(A) eta and the action phi^dag r_{1/2}(A) phi, each a multi-shift
+    solve plus hr_field_lincomb with hr_rational_approx's coefficients, against
+    A^(1/4) eta and eta^dag eta from the oracle's dense 2^4 matrix
+    (A = Dhat^dag Dhat, eigendecomposition): both within the approximations'
+    relative errors (plus the solves' 1e-12 tolerance)."""
+    from paper_2503_06721_gb300 import rational
+    N, rep, dims, m0 = 2, "ADJ", (2, 2, 2, 2), -0.2
+    L = oracle_mod.lat(N, rep, dims, (-1, 1, 1, 1), m0)
+    lat = hr.Lattice(N, rep, dims, (-1, 1, 1, 1), m0)
+    UF = H.links(dims, N, 1.0, seed=79)
+    UR = oracle_mod.represent_field(L, UF)
+    D, V = lat.D, lat.volume
+    nh = V // 2 * 4 * D
+    B = np.zeros((nh, nh), np.complex128)
+    e = np.zeros(nh, np.complex128)
+    for j in range(nh):
+        e[:] = 0
+        e[j] = 1
+        B[:, j] = oracle_mod.dhat(L, UR, e.reshape(V // 2, 4, D)).ravel()
+    lam, Q = np.linalg.eigh(B.conj().T @ B)
+    lo, hi = 0.9 * lam[0], 1.1 * lam[-1]
+    hb = rational.approx(-0.25, 4, lo, hi)
+    ac = rational.approx(0.5, 4, lo, hi)
+    g = hr.Gauge(lat, G.to_gpu(UF), precs=("f64", "f32"))
+    eta = H.spinor(V // 2, D, 89)
+    phi, _, res = hr.rational_apply(g, hr.EO_PRECOND, G.to_gpu(eta), hb, tol=1e-12, inner=inner)
+    assert all(r[0]["status"] == "HR_OK" for r in res)
+    exact = (Q @ ((Q.conj().T @ eta.ravel()) * lam ** 0.25)).reshape(eta.shape)
+    err = np.linalg.norm(phi.cpu().numpy() - exact) / np.linalg.norm(exact)
+    assert err <= hb.max_rel_err * 1.001 + 1e-10, (err, hb.max_rel_err)
+    y, _, res = hr.rational_apply(g, hr.EO_PRECOND, phi, ac, tol=1e-12, inner=inner)
+    S = hr.field_dot(lat, hr.EVEN, hr.F64, phi, y)[0].real
+    ee = float(np.vdot(eta.ravel(), eta.ravel()).real)
+    assert abs(S / ee - 1) <= 2 * hb.max_rel_err + ac.max_rel_err + 1e-10, S / ee - 1
+    g.close()
