@@ -593,6 +593,9 @@ DEO_CASES = [
      ("stored", "rebuild")),
     ("su4_asym_real_48x24x24x24", 4, "ASYM_REAL", (48, 24, 24, 24), -0.25, 0.4, ("f32", "f16", "bf16"),
      ("stored", "rebuild")),
+    # the colour-parallel kernel (Sec. 8.2's D_R-site-parallel form): D_R = 15 and 10
+    ("su4_adj_48x24x24x24", 4, "ADJ", (48, 24, 24, 24), -0.25, 0.4, ("f32",), ("stored",)),
+    ("su4_sym_48x24x24x24", 4, "SYM", (48, 24, 24, 24), -0.25, 0.4, ("f32",), ("stored",)),
 ]
 
 

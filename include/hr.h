@@ -91,9 +91,10 @@ typedef enum { HR_LINKS_STORED = 0, HR_LINKS_REBUILD = 1, HR_LINKS_AUTO = 2 } hr
 typedef struct {
     int N;          /* SU(N): N = 2, 3, 4 with the representations FUND,
                        ADJ, SYM (N = 2, 3), ASYM (N = 3, 4), ASYM_REAL
-                       (N = 4); N = 5, 6, 8 with
-                       FUND only, run by the colour-parallel hopping kernel
-                       (Sec. 8.2): FP64 / FP32 stored links, solves on the
+                       (N = 4); the colour-parallel pairs -- FUND for
+                       N = 5, 6, 8 and ADJ, SYM for N = 4 (D_R = 15, 10) --
+                       run on the colour-parallel hopping kernel (Sec.
+                       8.2): FP64 / FP32 stored links, solves on the
                        multi-shift engine, no batched or fused solve + force */
     hr_rep rep;
     int dims[4];    /* T, X, Y, Z (all even) */
@@ -305,7 +306,8 @@ typedef struct {
  * The gauge handle must hold F64 links, and the inner precision's links
  * when params->inner != HR_F64.  BLOCKS the calling thread until every
  * right-hand side has converged or failed.
- * With a clover term (hr_gauge_set_clover) or for N >= 5 the solve runs on
+ * With a clover term (hr_gauge_set_clover) or for a colour-parallel pair
+ * (N >= 5, SU(4) ADJ and SYM) the solve runs on
  * the multi-shift engine with the single shift 0 (same CG iterates; inner
  * FP64 or FP32, x started from 0, FP64 residuals).
  * Errors: HR_ERR_NOT_CONVERGED (x holds the last iterate),

@@ -27,8 +27,9 @@ NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "--expt-relaxed-constexpr", "-Xc
 PRECS = ["HR_F64", "HR_F32", "HR_F16", "HR_BF16", "HR_DF64"]
 PAIRS = [(2, "HR_FUND"), (2, "HR_ADJ"), (2, "HR_SYM"), (3, "HR_FUND"), (3, "HR_ADJ"), (3, "HR_SYM"),
          (3, "HR_ASYM"), (4, "HR_FUND"), (4, "HR_ASYM"), (4, "HR_ASYM_REAL")]
-# large-N fundamental pairs: colour-parallel hopping kernel, FP64 and FP32
-LARGE_PAIRS = [(5, "HR_FUND"), (6, "HR_FUND"), (8, "HR_FUND")]
+# pairs run by the colour-parallel hopping kernel (FP64 and FP32): the
+# fundamental of large N and the SU(4) adjoint and symmetric representations
+LARGE_PAIRS = [(5, "HR_FUND"), (6, "HR_FUND"), (8, "HR_FUND"), (4, "HR_ADJ"), (4, "HR_SYM")]
 
 
 def _units():
@@ -49,8 +50,8 @@ def _units():
         units.append((CSRC / "hr_gauge_inst.cu", OBJDIR / f"hr_gauge_inst_{tag}.o",
                       [f"-DHR_INST_N={n}", f"-DHR_INST_REP={rep}"]))
         for prec in ("HR_F64", "HR_F32"):
-            units.append((CSRC / "hr_dslash_colour.cu", OBJDIR / f"hr_dslash_colour_{n}_{prec.lower()[3:]}.o",
-                          [f"-DHR_INST_N={n}", f"-DHR_INST_P={prec}"]))
+            units.append((CSRC / "hr_dslash_colour.cu", OBJDIR / f"hr_dslash_colour_{tag}_{prec.lower()[3:]}.o",
+                          [f"-DHR_INST_N={n}", f"-DHR_INST_REP={rep}", f"-DHR_INST_P={prec}"]))
     return units
 
 

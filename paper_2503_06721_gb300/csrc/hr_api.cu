@@ -47,12 +47,13 @@ long long launch_counter() { return g_launches.load(); }
     extern template hr_status force_launch<N_, R_>(const ForceParams &, cudaStream_t);
 HR_PAIRS(HR_DECL)
 
-// large-N fundamental pairs: represent and force as above, the hop by the
-// colour-parallel kernel (FP64 and FP32, stored links)
-#define HR_LARGE_PAIRS(X) X(5, HR_FUND) X(6, HR_FUND) X(8, HR_FUND)
+// large pairs (the fundamental of large N, and the SU(4) adjoint and
+// symmetric representations with D_R = 15 and 10): represent and force as
+// above, the hop by the colour-parallel kernel (FP64 and FP32, stored links)
+#define HR_LARGE_PAIRS(X) X(5, HR_FUND) X(6, HR_FUND) X(8, HR_FUND) X(4, HR_ADJ) X(4, HR_SYM)
 #define HR_DECL_LARGE(N_, R_)                                                                          \
-    extern template hr_status launch_colour<N_, HR_F64>(const HopParams &, int, cudaStream_t);         \
-    extern template hr_status launch_colour<N_, HR_F32>(const HopParams &, int, cudaStream_t);         \
+    extern template hr_status launch_colour<N_, R_, HR_F64>(const HopParams &, int, cudaStream_t);     \
+    extern template hr_status launch_colour<N_, R_, HR_F32>(const HopParams &, int, cudaStream_t);     \
     extern template hr_status represent_launch<N_, R_>(const hr_gauge &, const double2 *, cudaStream_t); \
     extern template hr_status force_launch<N_, R_>(const ForceParams &, cudaStream_t);
 HR_LARGE_PAIRS(HR_DECL_LARGE)
@@ -84,12 +85,12 @@ hr_status hop_dispatch(int N, int rep, int P, const HopParams &prm, bool rebuild
 #define HR_HOP_LARGE(N_, R_)                                                                          \
     if (N == N_ && rep == R_) {                                                                       \
         if (rebuild || (P != HR_F64 && P != HR_F32)) {                                                \
-            set_error("SU(%d): the colour-parallel kernel takes stored FP64 or FP32 links", N);       \
+            set_error("SU(%d) rep %d: the colour-parallel kernel takes stored FP64 or FP32 links", N, rep); \
             return HR_ERR_UNSUPPORTED;                                                                \
         }                                                                                             \
         (void)variant;                                                                                \
-        return P == HR_F64 ? launch_colour<N_, HR_F64>(prm, epi, stream)                              \
-                           : launch_colour<N_, HR_F32>(prm, epi, stream);                             \
+        return P == HR_F64 ? launch_colour<N_, R_, HR_F64>(prm, epi, stream)                          \
+                           : launch_colour<N_, R_, HR_F32>(prm, epi, stream);                         \
     }
     HR_LARGE_PAIRS(HR_HOP_LARGE)
 #undef HR_HOP_LARGE
@@ -430,7 +431,7 @@ hr_status hr_represent_gauge(const hr_lattice_desc *lat, const void *U_fund, uns
     if (!U_fund) { set_error("hr_represent_gauge: U_fund is NULL"); return HR_ERR_INVALID; }
     if (prec_mask == 0 || (prec_mask & ~0x1Fu)) { set_error("bad prec_mask 0x%x", prec_mask); return HR_ERR_INVALID; }
     if (link_modes == 0 || (link_modes & ~0x3u)) { set_error("bad link_modes 0x%x", link_modes); return HR_ERR_INVALID; }
-    if (lat->N >= 5 && link_modes != (1u << HR_LINKS_STORED)) {
+    if (colour_pair(lat->N, lat->rep) && link_modes != (1u << HR_LINKS_STORED)) {
         set_error("SU(%d): the colour-parallel kernel reads stored links only (link_modes = STORED)", lat->N);
         return HR_ERR_UNSUPPORTED;
     }
@@ -453,7 +454,7 @@ hr_status hr_represent_gauge(const hr_lattice_desc *lat, const void *U_fund, uns
     for (int P = 0; P < HR_NPREC; P++) {
         if (!(prec_mask & (1u << P))) continue;
         if (link_modes & (1u << HR_LINKS_STORED)) {
-            size_t b = link_record_bytes(g->geom, P, g->real, g->D * g->D);
+            size_t b = link_record_bytes(g->geom, P, g->real, g->D * link_row_stride(lat->N, lat->rep, P));
             g->rep_bytes[P] = b;
             for (int par = 0; par < 2; par++) {
                 cudaError_t e = cudaMalloc(&g->rep[P][par], b);

@@ -44,7 +44,8 @@ hr_status hop(const hr_gauge *g, int P, int out_parity, int dagger, const FieldV
 
 // the large-N fundamental pairs (N >= 5), run by the colour-parallel hopping
 // kernel without a fused CG-update epilogue
-inline bool large_n(const hr_gauge *g) { return g->lat.N >= 5; }
+// pairs run by the colour-parallel hopping kernel (no fused CG update)
+inline bool large_n(const hr_gauge *g) { return colour_pair(g->lat.N, g->lat.rep); }
 
 // whether operator launches in precision P read fundamental links (rebuild)
 bool rebuild_for(const hr_gauge *g, int P);

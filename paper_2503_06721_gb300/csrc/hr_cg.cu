@@ -692,7 +692,7 @@ extern "C" hr_status hr_cg_solve_force(const hr_gauge *g, hr_parity sys, const v
     }
     if (b == x) { set_error("hr_cg_solve_force: b and x must not overlap"); return HR_ERR_INVALID; }
     if (g->clover_mode || large_n(g)) {
-        set_error("hr_cg_solve_force: not provided with a clover term or for N >= 5 (use hr_cg_solve + "
+        set_error("hr_cg_solve_force: not provided with a clover term or for the colour-parallel pairs (use hr_cg_solve + "
                   "hr_dirac_force for the latter)");
         return HR_ERR_UNSUPPORTED;
     }
@@ -740,7 +740,7 @@ extern "C" hr_status hr_cg_solve_batched(int n_inst, const hr_gauge *const *g, h
             return HR_ERR_INVALID;
         }
         if (g[i]->clover_mode || large_n(g[i])) {
-            set_error("hr_cg_solve_batched: instance %d has a clover term or N >= 5 (use hr_cg_solve)", i);
+            set_error("hr_cg_solve_batched: instance %d has a clover term or is a colour-parallel pair (use hr_cg_solve)", i);
             return HR_ERR_UNSUPPORTED;
         }
         for (int j = 0; j < i; j++)

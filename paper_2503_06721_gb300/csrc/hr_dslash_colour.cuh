@@ -1,13 +1,16 @@
-// hr_dslash_colour.cuh -- the colour-parallel hopping kernel for large N.
+// hr_dslash_colour.cuh -- the colour-parallel ("D_R-site-parallel") hopping
+// kernel for large representations.
 //
 // Sec. 8.2 (single-GPU efficiency) reports that a kernel holding a whole site per
-// thread spills registers once the representation grows (N > 4 in the
-// fundamental), and that a kernel in which each thread computes one colour
+// thread spills registers once the representation grows (large N, or a large
+// D_R), and that a kernel in which each thread computes one colour
 // component of one output site keeps the per-thread state small: the local
 // work becomes D_R-length dot products of a link row with the projected
-// neighbour spinor instead of D_R x D_R matrix-vector products.
+// neighbour spinor instead of D_R x D_R matrix-vector products.  It serves
+// the fundamental of SU(5), SU(6), SU(8) and the SU(4) adjoint (D_R = 15, real
+// links) and symmetric (D_R = 10) representations.
 //
-// Here a thread block is one 32-site tile times N colour rows.  For the
+// Here a thread block is one 32-site tile times D_R colour rows.  For the
 // link rows the threads are (row a, site j), site fastest, so every link-row
 // load of a warp reads 32 consecutive lanes of the AoSoA link record; for
 // the site-major spinors they are (site, colour), colour fastest, so that
@@ -28,18 +31,23 @@
 namespace hr {
 
 // resident blocks per SM asked of the register allocator in FP32: the
-// largest count whose register cap does not make ptxas spill (N = 5: 4
-// blocks of 160 threads; N = 6: 4 of 192; N = 8: 3 of 256, all <= 80
-// registers per thread); FP64 unconstrained
-template <int N, int P>
-constexpr int colour_minb() { return P == HR_F64 ? 1 : (N <= 6 ? 4 : 3); }
+// largest count whose register cap does not make ptxas spill (D = 5: 4
+// blocks of 160 threads; D = 6: 4 of 192; D = 8: 3 of 256, all <= 80
+// registers per thread; D = 10: 2 of 320; D = 15: 1 of 480); FP64
+// unconstrained
+template <int D, int P>
+constexpr int colour_minb() { return P == HR_F64 ? 1 : (D <= 6 ? 4 : D <= 8 ? 3 : D <= 10 ? 2 : 1); }
 
-template <int N, int P, int EPI>
-__global__ void __launch_bounds__(32 * N, colour_minb<N, P>()) hop_colour_kernel(const HopParams prm)
+template <int N, int REP, int P, int EPI>
+__global__ void __launch_bounds__(32 * rep_dim(N, REP), colour_minb<rep_dim(N, REP), P>())
+    hop_colour_kernel(const HopParams prm)
 {
     using R = typename St<P>::R;
     using C2 = typename std::conditional<P == HR_F64, double2, float2>::type;
-    using LIO = LinkIO<P, false, N * N>;
+    constexpr int D = rep_dim(N, REP);
+    constexpr bool REAL = rep_real(REP);
+    constexpr int RS = link_row_stride(N, REP, P);   // padded to whole chunks
+    using LIO = LinkIO<P, REAL, D * RS>;
     const Geom &g = prm.g;
     const int rhs = blockIdx.y;
     if (prm.state && cg_idle(prm.state[rhs])) return;   // uniform per block
@@ -49,29 +57,32 @@ __global__ void __launch_bounds__(32 * N, colour_minb<N, P>()) hop_colour_kernel
     const int a = threadIdx.x >> 5;
     // spinor mapping (colour fastest): thread = (site jA, colour aA), so that
     // consecutive threads read and write consecutive numbers of one record
-    const int jA = threadIdx.x / N;
-    const int aA = threadIdx.x % N;
+    const int jA = threadIdx.x / D;
+    const int aA = threadIdx.x % D;
     const bool active = tile * HR_TILE + j < g.vh;
     const long iA = tile * HR_TILE + jA;
     const bool activeA = iA < g.vh;
     const R sg = prm.dagger ? (R)-1 : (R)1;
-    constexpr int NC = 4 * N;                                 // complex numbers per spinor record
-    constexpr int MAXC = (N + LIO::VPC - 1) / LIO::VPC + 1;   // chunks a row can touch
+    constexpr int NC = 4 * D;                                 // complex numbers per spinor record
+    constexpr int MAXC = (D + LIO::VPC - 1) / LIO::VPC;       // chunks a row takes
     // one padding column: the colour-fastest accesses of a warp (same site,
     // consecutive colours) then fall in different banks
-    __shared__ cx<R> hs[2][N][HR_TILE + 1];
-    __shared__ cx<R> os[4][N][HR_TILE + 1];
+    // the two half-spinor planes of the hop loop live in the first two planes
+    // of the output buffer, which is only written after the loop's last barrier
+    __shared__ cx<R> os[4][D][HR_TILE + 1];
+    auto &hs = os;
 
     cx<R> acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
     Site stA;
     if (activeA) stA = site_of(g, iA, prm.out_parity);
     const char *in = prm.in.data + (size_t)rhs * prm.in.rhs_stride;
     auto comp = [&](const char *base, long site, int s) -> cx<R> {
-        const C2 v = *reinterpret_cast<const C2 *>(base + ((size_t)site * NC + (size_t)s * N + aA) * sizeof(C2));
+        const C2 v = *reinterpret_cast<const C2 *>(base + ((size_t)site * NC + (size_t)s * D + aA) * sizeof(C2));
         return {(R)v.x, (R)v.y};
     };
-    // the row's elements e = a N .. a N + N - 1 lie in chunks c0 .. c0 + nch - 1
-    const int e0 = a * N, c0 = e0 / LIO::VPC, nch = (e0 + N - 1) / LIO::VPC - c0 + 1;
+    // the row's elements e = a RS .. a RS + D - 1 lie in chunks c0 .. c0 + nch - 1
+    // (RS a multiple of the chunk size: the row starts a chunk)
+    const int e0 = a * RS, c0 = e0 / LIO::VPC, nch = (e0 + D - 1) / LIO::VPC - c0 + 1;
     // the loads of hop k: colour aA of site jA's neighbour, link row a of site j
     auto fetch = [&](int k, cx<R> (&psi)[4], uint4 (&lv)[MAXC]) {
         if (activeA) {
@@ -111,10 +122,16 @@ __global__ void __launch_bounds__(32 * N, colour_minb<N, P>()) hop_colour_kernel
 #pragma unroll
                 for (int q = 0; q < LIO::VPC; q++) {
                     const int b = (c0 + cc) * LIO::VPC + q - e0;
-                    if (b < 0 || b >= N) continue;
-                    const cx<R> u = LIO::cunpack(lv[cur][cc], q);
-                    cmac(chi[0], u, hs[0][b][j]);
-                    cmac(chi[1], u, hs[1][b][j]);
+                    if (b < 0 || b >= D) continue;
+                    if constexpr (REAL) {
+                        const R u = LIO::runpack(lv[cur][cc], q);
+                        rmac(chi[0], u, hs[0][b][j]);
+                        rmac(chi[1], u, hs[1][b][j]);
+                    } else {
+                        const cx<R> u = LIO::cunpack(lv[cur][cc], q);
+                        cmac(chi[0], u, hs[0][b][j]);
+                        cmac(chi[1], u, hs[1][b][j]);
+                    }
                 }
             }
 #pragma unroll
@@ -150,7 +167,7 @@ __global__ void __launch_bounds__(32 * N, colour_minb<N, P>()) hop_colour_kernel
             C2 v;
             v.x = o[s].re;
             v.y = o[s].im;
-            *reinterpret_cast<C2 *>(out + ((size_t)iA * NC + (size_t)s * N + aA) * sizeof(C2)) = v;
+            *reinterpret_cast<C2 *>(out + ((size_t)iA * NC + (size_t)s * D + aA) * sizeof(C2)) = v;
             norm_acc(n2, o[s]);
         }
     }
@@ -162,13 +179,14 @@ __global__ void __launch_bounds__(32 * N, colour_minb<N, P>()) hop_colour_kernel
     }
 }
 
-template <int N, int P>
+template <int N, int REP, int P>
 hr_status launch_colour(const HopParams &prm, int epi, cudaStream_t stream)
 {
+    constexpr int D = rep_dim(N, REP);
     const dim3 grid((unsigned)prm.g.ntiles, (unsigned)prm.nrhs);
     switch (epi) {
-    case EPI_STORE: hop_colour_kernel<N, P, EPI_STORE><<<grid, 32 * N, 0, stream>>>(prm); break;
-    case EPI_STORE_NORM: hop_colour_kernel<N, P, EPI_STORE_NORM><<<grid, 32 * N, 0, stream>>>(prm); break;
+    case EPI_STORE: hop_colour_kernel<N, REP, P, EPI_STORE><<<grid, 32 * D, 0, stream>>>(prm); break;
+    case EPI_STORE_NORM: hop_colour_kernel<N, REP, P, EPI_STORE_NORM><<<grid, 32 * D, 0, stream>>>(prm); break;
     default:
         set_error("the colour-parallel hopping kernel has no fused CG-update epilogue");
         return HR_ERR_UNSUPPORTED;

@@ -188,6 +188,20 @@ __host__ __device__ constexpr int link_nchunk(int P, bool real, int ncomp)
 {
     return (ncomp + link_vpc(P, real) - 1) / link_vpc(P, real);
 }
+// Row stride (in components) of the stored D_R x D_R links: D_R, except for
+// the pairs run by the colour-parallel kernel, where each thread reads one
+// row: there the rows are padded to whole 16-byte chunks, so that a row
+// never straddles a chunk boundary and each thread loads exactly its row
+// (D_R = 5 complex FP32 rows take 3 chunks instead of up to 4, the real
+// D_R = 15 adjoint rows of SU(4) 4 instead of up to 5).  Component (a, b) of
+// a link is stored at a * stride + b; the padding is never read.
+__host__ __device__ constexpr int link_row_stride(int N, int rep, int P)
+{
+    return colour_pair(N, rep) ? (rep_dim(N, rep) + link_vpc(P, rep_real(rep)) - 1) / link_vpc(P, rep_real(rep)) *
+                                     link_vpc(P, rep_real(rep))
+                               : rep_dim(N, rep);
+}
+
 // byte offset of component c of (tile, slot, lane) in a record of ncomp components
 __host__ __device__ inline size_t link_offset(int P, bool real, int ncomp, long tile, int slot, int lane, int c)
 {

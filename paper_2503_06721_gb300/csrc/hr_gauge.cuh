@@ -68,8 +68,8 @@ struct ForceParams {
 template <int N, int REP>
 hr_status force_launch(const ForceParams &fp, cudaStream_t stream);
 
-// the colour-parallel hopping kernel of the large-N pairs (hr_dslash_colour.cuh)
-template <int N, int P>
+// the colour-parallel hopping kernel of the large pairs (hr_dslash_colour.cuh)
+template <int N, int REP, int P>
 hr_status launch_colour(const HopParams &prm, int epi, cudaStream_t stream);
 
 // precision dispatch of the hop kernel for a runtime (N, rep)

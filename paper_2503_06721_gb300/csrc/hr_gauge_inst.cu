@@ -83,9 +83,10 @@ __global__ void __launch_bounds__(128) represent_kernel(const double2 *__restric
                 const cx<double> v = sg * Rm[r][q];
                 for (int P = 0; P < HR_NPREC; P++) {
                     if (!of.rep[P]) continue;
-                    store_entry(P, REAL, reinterpret_cast<char *>(of.rep[P]) + link_offset(P, REAL, D * D, tile, mu, lane, r * D + q), v);
+                    const int RS = link_row_stride(N, REP, P);
+                    store_entry(P, REAL, reinterpret_cast<char *>(of.rep[P]) + link_offset(P, REAL, D * RS, tile, mu, lane, r * RS + q), v);
                     // the dagger: entry (q, r) of the backward slot
-                    store_entry(P, REAL, reinterpret_cast<char *>(ob.rep[P]) + link_offset(P, REAL, D * D, tb, 4 + mu, lb, q * D + r), conj(v));
+                    store_entry(P, REAL, reinterpret_cast<char *>(ob.rep[P]) + link_offset(P, REAL, D * RS, tb, 4 + mu, lb, q * RS + r), conj(v));
                 }
             }
     }
@@ -233,7 +234,8 @@ __global__ void __launch_bounds__(128) force_kernel(const ForceParams fp)
     constexpr int NG = N * N - 1;
     constexpr bool REAL = rep_real(REP);
     using SIO = SpinorIO<HR_F64, D>;
-    using LIO = LinkIO<HR_F64, REAL, D * D>;
+    constexpr int RS = link_row_stride(N, REP, HR_F64);
+    using LIO = LinkIO<HR_F64, REAL, D * RS>;
     const Geom &g = fp.g;
     // two threads per link (adjacent lanes): spin component r = 0, 1 of the projections
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(128) force_kernel(const ForceParams fp)
         for (int a = 0; a < D; a++) {
             cx<double> su = {0, 0}, sv = {0, 0};
             for (int b = 0; b < D; b++) {
-                const int cc = a * D + b;
+                const int cc = a * RS + b;
                 const uint4 ch = __ldg(lp + (size_t)(cc / LIO::VPC) * HR_TILE);
                 cx<double> uab;
                 if constexpr (REAL)

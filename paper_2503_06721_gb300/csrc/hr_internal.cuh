@@ -178,6 +178,13 @@ __host__ __device__ constexpr int rep_dim(int N, int rep)
 {
     return rep == HR_FUND ? N : rep == HR_ADJ ? N * N - 1 : rep == HR_SYM ? N * (N + 1) / 2 : N * (N - 1) / 2;
 }
+// (N, representation) pairs whose hop runs on the colour-parallel kernel:
+// the fundamental for N >= 5, the SU(4) adjoint (D_R = 15) and symmetric
+// (D_R = 10) representations
+__host__ __device__ constexpr bool colour_pair(int N, int rep)
+{
+    return N >= 5 || (N == 4 && (rep == HR_ADJ || rep == HR_SYM));
+}
 // representations whose links are real in the library's basis (stored as reals)
 __host__ __device__ constexpr bool rep_real(int rep) { return rep == HR_ADJ || rep == HR_ASYM_REAL; }
 

@@ -259,6 +259,11 @@ WORKLOADS = {
     # the same SU(4) 2AS workload with the links in the real basis (stored real)
     "su4_asym_real_48x24x24x24": Workload("su4_asym_real_48x24x24x24", 4, "ASYM_REAL", (48, 24, 24, 24),
                                           -0.25, 0.4, seed=2503067213),
+    # SU(4) adjoint (D_R = 15) and symmetric (D_R = 10) 24^3 x 48: the colour-parallel kernel
+    "su4_adj_48x24x24x24": Workload("su4_adj_48x24x24x24", 4, "ADJ", (48, 24, 24, 24), -0.25, 0.4,
+                                    seed=2503067216),
+    "su4_sym_48x24x24x24": Workload("su4_sym_48x24x24x24", 4, "SYM", (48, 24, 24, 24), -0.25, 0.4,
+                                    seed=2503067217),
     # SU(8) fundamental 24^3 x 48: the colour-parallel (large-N) kernel
     "su8_fund_48x24x24x24": Workload("su8_fund_48x24x24x24", 8, "FUND", (48, 24, 24, 24),
                                      -0.1, 0.4, seed=2503067218),

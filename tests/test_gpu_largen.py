@@ -1,5 +1,7 @@
-"""GPU parity of the large-N fundamental pairs SU(5), SU(6), SU(8), run by the
-colour-parallel hopping kernel (one thread per colour row of a site, Sec. 8.2),
+"""GPU parity of the pairs run by the colour-parallel hopping kernel (one
+thread per colour row of a site, Sec. 8.2): the fundamental of SU(5), SU(6),
+SU(8) and the SU(4) adjoint (D_R = 15, real links) and symmetric (D_R = 10)
+representations,
 with the oracle: every parity selector, plain and dagger, FP64 and FP32, on a
 lattice that spans several 32-site tiles and ends in a ragged tail; solves
 (which run on the multi-shift engine for these pairs); the fermion force; and
@@ -22,18 +24,21 @@ def hr():
     return hr
 
 
-def _case(hr, oracle_mod, N, dims=(4, 4, 2, 6), m0=-0.1, eps=0.6, seed=257, precs=("f64", "f32")):
-    lat = hr.Lattice(N, "FUND", dims, (-1, 1, 1, 1), m0)
-    L = oracle_mod.lat(N, "FUND", dims, (-1, 1, 1, 1), m0)
+COLOUR_PAIRS = [(5, "FUND"), (6, "FUND"), (8, "FUND"), (4, "ADJ"), (4, "SYM")]
+
+
+def _case(hr, oracle_mod, N, dims=(4, 4, 2, 6), m0=-0.1, eps=0.6, seed=257, precs=("f64", "f32"), rep="FUND"):
+    lat = hr.Lattice(N, rep, dims, (-1, 1, 1, 1), m0)
+    L = oracle_mod.lat(N, rep, dims, (-1, 1, 1, 1), m0)
     U = H.links(dims, N, eps, seed=seed)
     UR = oracle_mod.represent_field(L, U)
     g = hr.Gauge(lat, G.to_gpu(U), precs=precs)
     return lat, L, U, UR, g
 
 
-@pytest.mark.parametrize("N", [5, 6, 8])
-def test_largen_operator_parity(hr, oracle_mod, N):
-    lat, L, U, UR, g = _case(hr, oracle_mod, N)
+@pytest.mark.parametrize("N,rep", COLOUR_PAIRS)
+def test_largen_operator_parity(hr, oracle_mod, N, rep):
+    lat, L, U, UR, g = _case(hr, oracle_mod, N, rep=rep)
     V, D = lat.volume, lat.D
     psi = H.spinor(V, D, 263)
     half = H.spinor(V // 2, D, 269)
@@ -70,8 +75,9 @@ def test_largen_operator_parity(hr, oracle_mod, N):
 
 @pytest.mark.parametrize("sys", [3, 2], ids=["eo", "full"])
 @pytest.mark.parametrize("inner", [0, 1], ids=["f64", "f32"])
-def test_largen_solve(hr, oracle_mod, sys, inner):
-    lat, L, U, UR, g = _case(hr, oracle_mod, 5, dims=(8, 4, 4, 4), m0=0.1)
+@pytest.mark.parametrize("N,rep", [(5, "FUND"), (4, "ADJ")])
+def test_largen_solve(hr, oracle_mod, sys, inner, N, rep):
+    lat, L, U, UR, g = _case(hr, oracle_mod, N, dims=(8, 4, 4, 4), m0=0.1, rep=rep)
     ns = lat.nsites(sys if sys == hr.FULL else hr.EVEN)
     b = H.spinor(ns, lat.D, 277)
     tol = 1e-10
@@ -91,9 +97,9 @@ def test_largen_solve(hr, oracle_mod, sys, inner):
     g.close()
 
 
-@pytest.mark.parametrize("N", [5, 8])
-def test_largen_force(hr, oracle_mod, N):
-    lat, L, U, UR, g = _case(hr, oracle_mod, N, precs=("f64",))
+@pytest.mark.parametrize("N,rep", [(5, "FUND"), (8, "FUND"), (4, "ADJ"), (4, "SYM")])
+def test_largen_force(hr, oracle_mod, N, rep):
+    lat, L, U, UR, g = _case(hr, oracle_mod, N, precs=("f64",), rep=rep)
     V = lat.volume
     X = H.spinor(V, lat.D, 281)
     Y = H.spinor(V, lat.D, 283)

@@ -10,7 +10,7 @@ import pytest
 from tests import _helpers as H
 
 CASES = [(2, "ADJ"), (3, "SYM"), (3, "ADJ"), (4, "FUND"), (4, "ASYM"), (3, "FUND"), (5, "FUND"), (8, "FUND"),
-         (4, "ASYM_REAL")]
+         (4, "ASYM_REAL"), (4, "ADJ"), (4, "SYM")]
 
 
 def _gam(oracle_mod):
