@@ -117,8 +117,16 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const HopParams prm)
             const long nb = neighbour(g, st, mu, fwd ? +1 : -1);
             // projector (1 + sp gamma_mu): sp = -s forward, +s backward
             const R sp = fwd ? -sg : sg;
+            // F16/BF16: the codes are projected and multiplied as stored; the
+            // site scale sc enters once, in the accumulation below
             cx<R> psi[4][D];
-            SIO::load(prm.in, rhs, nb, psi);
+            R sc = 1;
+            if constexpr (S::scaled) {
+                SIO::load_codes(prm.in, rhs, nb, psi);
+                sc = (R)SIO::ld_scale(prm.in, rhs, nb);
+            } else {
+                SIO::load(prm.in, rhs, nb, psi);
+            }
             cx<R> h[2][D];
 #pragma unroll
             for (int r = 0; r < 2; r++)
@@ -181,8 +189,13 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const HopParams prm)
             for (int r = 0; r < 2; r++)
 #pragma unroll
                 for (int c = 0; c < D; c++) {
-                    acc[r][c] = acc[r][c] + chi[r][c];
-                    acc[2 + eperm(mu, r)][c] = acc[2 + eperm(mu, r)][c] + sp * ipow(4 - ephase(mu, r), chi[r][c]);
+                    if constexpr (S::scaled) {
+                        acc_scaled(acc[r][c], sc, chi[r][c]);
+                        acc_scaled(acc[2 + eperm(mu, r)][c], sc, sp * ipow(4 - ephase(mu, r), chi[r][c]));
+                    } else {
+                        acc[r][c] = acc[r][c] + chi[r][c];
+                        acc[2 + eperm(mu, r)][c] = acc[2 + eperm(mu, r)][c] + sp * ipow(4 - ephase(mu, r), chi[r][c]);
+                    }
                 }
         }
         // epilogue: out = a * H + b * diag

@@ -172,12 +172,9 @@ __global__ void __launch_bounds__(128, MINB) hop_mrhs_kernel(const HopParams prm
             for (int r = 0; r < 2; r++)
 #pragma unroll
                 for (int c = 0; c < D; c++) {
-                    cx<R> up = rec_comp<P>(rec, r * D + c);
-                    cx<R> dn = rec_comp<P>(rec, (2 + eperm(mu, r)) * D + c);
-                    if constexpr (S::scaled) {
-                        up = scale_rn(sc, up);
-                        dn = scale_rn(sc, dn);
-                    }
+                    // F16/BF16: codes as stored; the scale sc enters in the accumulation
+                    const cx<R> up = rec_comp<P>(rec, r * D + c);
+                    const cx<R> dn = rec_comp<P>(rec, (2 + eperm(mu, r)) * D + c);
                     h[r][c] = up + sp * ipow(ephase(mu, r), dn);
                 }
             cx<R> chi[2][D];
@@ -227,8 +224,13 @@ __global__ void __launch_bounds__(128, MINB) hop_mrhs_kernel(const HopParams prm
             for (int r = 0; r < 2; r++)
 #pragma unroll
                 for (int c = 0; c < D; c++) {
-                    acc[r][c] = acc[r][c] + chi[r][c];
-                    acc[2 + eperm(mu, r)][c] = acc[2 + eperm(mu, r)][c] + sp * ipow(4 - ephase(mu, r), chi[r][c]);
+                    if constexpr (S::scaled) {
+                        acc_scaled(acc[r][c], sc, chi[r][c]);
+                        acc_scaled(acc[2 + eperm(mu, r)][c], sc, sp * ipow(4 - ephase(mu, r), chi[r][c]));
+                    } else {
+                        acc[r][c] = acc[r][c] + chi[r][c];
+                        acc[2 + eperm(mu, r)][c] = acc[2 + eperm(mu, r)][c] + sp * ipow(4 - ephase(mu, r), chi[r][c]);
+                    }
                 }
         }
         __syncthreads();   // every warp is done with hop k's buffers before hop k+2 refills them

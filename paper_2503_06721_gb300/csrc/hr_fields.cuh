@@ -75,6 +75,19 @@ struct SpinorIO {
             }
     }
 
+    // the stored values without the site scale (the codes of F16/BF16 fields)
+    __device__ __forceinline__ static void load_codes(const FieldView &f, int rhs, long i, cx<R> (&psi)[4][D])
+    {
+        const uint4 *p = site_ptr(f, rhs, i);
+        uint4 raw[NV];
+#pragma unroll
+        for (int j = 0; j < NV; j++) raw[j] = __ldg(p + j);
+#pragma unroll
+        for (int s = 0; s < 4; s++)
+#pragma unroll
+            for (int c = 0; c < D; c++) psi[s][c] = comp(raw, s * D + c);
+    }
+
     // plain (non-caching-hint) load for fields this kernel may also write
     __device__ __forceinline__ static void load_rw(const FieldView &f, int rhs, long i, cx<R> (&psi)[4][D])
     {
@@ -272,15 +285,40 @@ struct LinkIO {
                 if (j * VPC + k < NCOMP) W[j * VPC + k] = cunpack(v, k);
         }
     }
-    __device__ __forceinline__ static void load(const uint4 *p, R (&W)[NCOMP], bool keep = false)
+    // the real components 2w, 2w+1 of a chunk of a 16-bit (F16/BF16) record:
+    // one paired conversion of the 32-bit word w (exact, like two single ones)
+    __device__ __forceinline__ static void runpack_pair(const uint4 &v, int w, R &lo, R &hi)
     {
+        const unsigned u = word(v, w);
+        typename S::C h;
+        memcpy(&h, &u, 4);
+        const cx<R> f = S::ld(h);
+        lo = f.re;
+        hi = f.im;
+    }
+    __device__ __forceinline__ static void unpack_real(const uint4 &v, int j, R (&W)[NCOMP])
+    {
+        if constexpr (S::scaled) {
 #pragma unroll
-        for (int j = 0; j < NCHUNK; j++) {
-            const uint4 v = ld(p + (size_t)j * HR_TILE, keep);
+            for (int w = 0; w < 4; w++) {
+                const int e = j * VPC + 2 * w;
+                if (e < NCOMP) {
+                    R lo, hi;
+                    runpack_pair(v, w, lo, hi);
+                    W[e] = lo;
+                    if (e + 1 < NCOMP) W[e + 1] = hi;
+                }
+            }
+        } else {
 #pragma unroll
             for (int k = 0; k < VPC; k++)
                 if (j * VPC + k < NCOMP) W[j * VPC + k] = runpack(v, k);
         }
+    }
+    __device__ __forceinline__ static void load(const uint4 *p, R (&W)[NCOMP], bool keep = false)
+    {
+#pragma unroll
+        for (int j = 0; j < NCHUNK; j++) unpack_real(ld(p + (size_t)j * HR_TILE, keep), j, W);
     }
     // the same from a copy of the warp's slot records in shared memory
     // (chunk j of lane l at p[j * 32], p = base + l)
@@ -297,12 +335,7 @@ struct LinkIO {
     __device__ __forceinline__ static void load_shared(const uint4 *p, R (&W)[NCOMP])
     {
 #pragma unroll
-        for (int j = 0; j < NCHUNK; j++) {
-            const uint4 v = p[j * HR_TILE];
-#pragma unroll
-            for (int k = 0; k < VPC; k++)
-                if (j * VPC + k < NCOMP) W[j * VPC + k] = runpack(v, k);
-        }
+        for (int j = 0; j < NCHUNK; j++) unpack_real(p[j * HR_TILE], j, W);
     }
 };
 

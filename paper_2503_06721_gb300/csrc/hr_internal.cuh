@@ -98,6 +98,16 @@ __host__ __device__ __forceinline__ void norm_acc(R &n2, cx<R> v)
 // variant and not in another; written this way every variant rounds it alike.
 __device__ __forceinline__ cx<float> scale_rn(float s, cx<float> v) { return {__fmul_rn(s, v.re), __fmul_rn(s, v.im)}; }
 
+// acc += s * v as two fmas (s real): the hop of a per-site scaled
+// (F16/BF16) field projects and multiplies the stored codes and applies the
+// neighbour's scale once, here, instead of to every component it loaded
+template <class R>
+__host__ __device__ __forceinline__ void acc_scaled(cx<R> &acc, R s, cx<R> v)
+{
+    acc.re = fma(s, v.re, acc.re);
+    acc.im = fma(s, v.im, acc.im);
+}
+
 // multiply by i^k, k known at compile time after unrolling
 template <class R>
 __host__ __device__ __forceinline__ cx<R> ipow(int k, cx<R> a)
