@@ -264,6 +264,9 @@ WORKLOADS = {
                                     seed=2503067216),
     "su4_sym_48x24x24x24": Workload("su4_sym_48x24x24x24", 4, "SYM", (48, 24, 24, 24), -0.25, 0.4,
                                     seed=2503067217),
+    # SU(5) fundamental 24^3 x 48: the colour-parallel kernel with an odd D_R
+    "su5_fund_48x24x24x24": Workload("su5_fund_48x24x24x24", 5, "FUND", (48, 24, 24, 24),
+                                     -0.1, 0.4, seed=2503067219),
     # SU(8) fundamental 24^3 x 48: the colour-parallel (large-N) kernel
     "su8_fund_48x24x24x24": Workload("su8_fund_48x24x24x24", 8, "FUND", (48, 24, 24, 24),
                                      -0.1, 0.4, seed=2503067218),
