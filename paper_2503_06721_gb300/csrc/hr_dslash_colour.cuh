@@ -31,12 +31,13 @@
 namespace hr {
 
 // resident blocks per SM asked of the register allocator in FP32: the
-// largest count whose register cap does not make ptxas spill (D = 5: 4
-// blocks of 160 threads; D = 6: 4 of 192; D = 8: 3 of 256, all <= 80
-// registers per thread; D = 10: 2 of 320; D = 15: 1 of 480); FP64
-// unconstrained
+// largest count whose register cap does not make ptxas spill (D = 5: 5
+// blocks of 160 threads at 72 registers; D = 6: 4 of 192; D = 8: 3 of 256,
+// <= 80 registers; D = 10: 2 of 320), except D = 15: 2 blocks of 480 at 64
+// registers with a small spill; FP64 unconstrained.  ncu on SU(5) at 4
+// blocks: 20 warps per SM, stalled on the gathers (long scoreboard)
 template <int D, int P>
-constexpr int colour_minb() { return P == HR_F64 ? 1 : (D <= 6 ? 4 : D <= 8 ? 3 : D <= 10 ? 2 : 1); }
+constexpr int colour_minb() { return P == HR_F64 ? 1 : (D <= 5 ? 5 : D <= 6 ? 4 : D <= 8 ? 3 : 2); }
 
 template <int N, int REP, int P, int EPI>
 __global__ void __launch_bounds__(32 * rep_dim(N, REP), colour_minb<rep_dim(N, REP), P>())

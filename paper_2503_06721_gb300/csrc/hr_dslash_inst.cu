@@ -6,6 +6,14 @@
 
 namespace hr {
 
+// register budget of the direct variant: F16/BF16 launches with D_R <= 4
+// are held to 4 blocks of 128 threads per SM (128 registers, which they fit
+// without spilling; ncu showed the unconstrained kernel at 168 registers and
+// 12 warps per SM, stalled on its gathers); larger D_R spill at that cap and
+// stay unconstrained, as do the other precisions
+template <int N, int REP, int P>
+constexpr int direct_minb() { return St<P>::scaled && rep_dim(N, REP) <= 4 ? 4 : 1; }
+
 // register budget (resident blocks of 128 threads per SM) of a staged variant
 template <int N, int REP>
 constexpr int staged_minb(int variant)
@@ -130,9 +138,13 @@ static hr_status launch_epi(const HopParams &prm, int epi, int variant, cudaStre
         if constexpr (!RB) hop_df64_kernel<N, REP><<<grid, block, 0, stream>>>(prm);
     } else {
         switch (epi) {
-        case EPI_STORE: hop_kernel<N, REP, P, RB, EPI_STORE><<<grid, block, 0, stream>>>(prm); break;
-        case EPI_STORE_NORM: hop_kernel<N, REP, P, RB, EPI_STORE_NORM><<<grid, block, 0, stream>>>(prm); break;
-        case EPI_CG_UPDATE: hop_kernel<N, REP, P, RB, EPI_CG_UPDATE><<<grid, block, 0, stream>>>(prm); break;
+        case EPI_STORE: hop_kernel<N, REP, P, RB, EPI_STORE, direct_minb<N, REP, P>()><<<grid, block, 0, stream>>>(prm); break;
+        case EPI_STORE_NORM:
+            hop_kernel<N, REP, P, RB, EPI_STORE_NORM, direct_minb<N, REP, P>()><<<grid, block, 0, stream>>>(prm);
+            break;
+        case EPI_CG_UPDATE:
+            hop_kernel<N, REP, P, RB, EPI_CG_UPDATE, direct_minb<N, REP, P>()><<<grid, block, 0, stream>>>(prm);
+            break;
         default: set_error("bad epilogue %d", epi); return HR_ERR_INVALID;
         }
     }
