@@ -79,7 +79,11 @@ static hr_status launch_mrhs(const HopParams &prm, cudaStream_t stream)
     constexpr int NCH = link_nchunk(P, rep_real(REP) && !RB, RB ? N * N : rep_dim(N, REP) * rep_dim(N, REP));
     constexpr size_t smem = MrhsShape<P, rep_dim(N, REP), EPI, NCH>::SMEM;
     constexpr int b = (int)((size_t)227 * 1024 / (smem + 8192));
-    constexpr int MINB = b < 1 ? 1 : b > 4 ? 4 : b;
+    // as many blocks as the shared memory allows (at most 4: 128 registers,
+    // small spills with stored links); the in-kernel rebuild needs more
+    // registers and keeps a budget of 2 blocks
+    constexpr int bm = RB ? 2 : 4;
+    constexpr int MINB = b < 1 ? 1 : b > bm ? bm : b;
     auto kern = hop_mrhs_kernel<N, REP, P, RB, EPI, MINB>;
     static const cudaError_t attr =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

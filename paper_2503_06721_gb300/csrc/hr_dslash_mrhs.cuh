@@ -8,7 +8,12 @@
 // and all four warps read them there, so the links cross L2 and HBM once per
 // 4 right-hand sides instead of once per right-hand side.  The neighbour
 // spinors and the output / CG-update records of each warp move through
-// shared memory as in hop_staged_kernel.  Consecutive blocks are the
+// shared memory as in hop_staged_kernel, but through one buffer per warp:
+// as soon as hop k's half-spinors are in registers the buffer takes the
+// gather of hop k+1, which then overlaps hop k's link products.  With one
+// spinor buffer a block takes 45 KB of shared memory (complex 2AS, FP32),
+// so 4 blocks (16 warps) fit an SM and the register budget is 128; with two
+// buffers 3 blocks did (ncu: 12 warps per SM, issue- and latency-bound).  Consecutive blocks are the
 // right-hand-side groups of one tile, so the other groups find the tile's
 // links in L2.  The arithmetic per site equals hop_kernel, bit for bit.
 //
@@ -29,7 +34,7 @@ struct MrhsShape {
     static constexpr int SU = SS::SU;
     static constexpr int BUF = SS::BUF;            // chunks per warp spinor buffer
     static constexpr int LBUF = LCH * 32;          // chunks per block link buffer
-    static constexpr size_t SMEM = ((size_t)MRHS_WARPS * 2 * BUF + 2 * LBUF) * 16;
+    static constexpr size_t SMEM = ((size_t)MRHS_WARPS * BUF + 2 * LBUF) * 16;
 };
 
 // warp-level grid reduction of one value per right-hand side over `nparts`
@@ -90,10 +95,9 @@ __global__ void __launch_bounds__(128, MINB) hop_mrhs_kernel(const HopParams prm
 
     extern __shared__ uint4 mrhs_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint4 *const wbuf = mrhs_smem + (size_t)warp * 2 * Sh::BUF;
-    uint4 *const lbase = mrhs_smem + (size_t)MRHS_WARPS * 2 * Sh::BUF;
-    auto buf = [&](int g) { return wbuf + (g % 2) * Sh::BUF; };
-    auto own = [&](int g) { return wbuf + (g % 2) * Sh::BUF + lane * SU; };
+    uint4 *const buf = mrhs_smem + (size_t)warp * Sh::BUF;   // the warp's record buffer
+    uint4 *const own = buf + lane * SU;                        // this lane's record in it
+    uint4 *const lbase = mrhs_smem + (size_t)MRHS_WARPS * Sh::BUF;
     auto lbuf = [&](int g) { return lbase + (g % 2) * Sh::LBUF; };
 
     const Geom &g = prm.g;
@@ -137,11 +141,16 @@ __global__ void __launch_bounds__(128, MINB) hop_mrhs_kernel(const HopParams prm
 #pragma unroll
         for (int c = 0; c < D; c++) acc[s][c] = {0, 0};
 
-    R scale_q[2];
+    // cp.async groups, per thread, in the order issued: [links 0 + gather 0],
+    // then per hop k: [links k+1] at the top, [gather k+1 (or the diagonal)]
+    // once hop k's half-spinors are in registers.  At the top of hop k the
+    // wait for all but the newest group therefore means: gather k and links k
+    // have landed.
+    R scale_cur;
     {
         const int site = gather_site(0);
-        scale_q[0] = (R)SIO::ld_scale(prm.in, rhs, site);
-        if (work) warp_gather<NC, SU>(buf(0), in_base, site, lane);
+        scale_cur = (R)SIO::ld_scale(prm.in, rhs, site);
+        if (work) warp_gather<NC, SU>(buf, in_base, site, lane);
         copy_links(0);
         cp_async_commit();
     }
@@ -149,34 +158,37 @@ __global__ void __launch_bounds__(128, MINB) hop_mrhs_kernel(const HopParams prm
     for (int k = 0; k < 8; k++) {
         const int mu = k & 3;
         const bool fwd = k < 4;
-        {
-            const int q = k + 1;
-            if (q < 8) {
-                const int site = gather_site(q);
-                scale_q[q % 2] = (R)SIO::ld_scale(prm.in, rhs, site);
-                if (work) warp_gather<NC, SU>(buf(q), in_base, site, lane);
-                copy_links(q);
-            } else if (diag_base && work) {
-                warp_gather<NC, SU>(buf(8), diag_base, (int)ie, lane);
-            }
-            cp_async_commit();
-            cp_async_wait<1>();
-        }
+        if (k + 1 < 8) copy_links(k + 1);   // into the buffer hop k-1 used (all warps are past it)
+        cp_async_commit();
+        cp_async_wait<1>();
         __syncthreads();   // hop k's links (copied by all warps) and spinors have landed
+        const R sc = scale_cur;
+        const R sp = fwd ? -sg : sg;
+        cx<R> h[2][D];
         if (work) {
-            const R sc = scale_q[k % 2];
-            const R sp = fwd ? -sg : sg;
-            cx<R> h[2][D];
-            const uint4 *rec = own(k);
 #pragma unroll
             for (int r = 0; r < 2; r++)
 #pragma unroll
                 for (int c = 0; c < D; c++) {
                     // F16/BF16: codes as stored; the scale sc enters in the accumulation
-                    const cx<R> up = rec_comp<P>(rec, r * D + c);
-                    const cx<R> dn = rec_comp<P>(rec, (2 + eperm(mu, r)) * D + c);
+                    const cx<R> up = rec_comp<P>(own, r * D + c);
+                    const cx<R> dn = rec_comp<P>(own, (2 + eperm(mu, r)) * D + c);
                     h[r][c] = up + sp * ipow(ephase(mu, r), dn);
                 }
+        }
+        __syncwarp();   // every lane has its half-spinors: the buffer takes the next gather
+        {
+            const int q = k + 1;
+            if (q < 8) {
+                const int site = gather_site(q);
+                scale_cur = (R)SIO::ld_scale(prm.in, rhs, site);
+                if (work) warp_gather<NC, SU>(buf, in_base, site, lane);
+            } else if (diag_base && work) {
+                warp_gather<NC, SU>(buf, diag_base, (int)ie, lane);
+            }
+            cp_async_commit();
+        }
+        if (work) {
             cx<R> chi[2][D];
             const uint4 *lp = lbuf(k) + lane;
             if constexpr (REBUILD) {
@@ -233,7 +245,7 @@ __global__ void __launch_bounds__(128, MINB) hop_mrhs_kernel(const HopParams prm
                     }
                 }
         }
-        __syncthreads();   // every warp is done with hop k's buffers before hop k+2 refills them
+        __syncthreads();   // every warp is done with hop k's links before hop k+2's refill them
     }
     cp_async_wait<0>();
     __syncwarp();
@@ -246,7 +258,7 @@ __global__ void __launch_bounds__(128, MINB) hop_mrhs_kernel(const HopParams prm
         for (int s = 0; s < 4; s++)
 #pragma unroll
             for (int c = 0; c < D; c++) {
-                cx<R> d = rec_comp<P>(own(8), s * D + c);
+                cx<R> d = rec_comp<P>(own, s * D + c);
                 if constexpr (S::scaled) d = scale_rn(dsc, d);
                 acc[s][c] = axpby(a, acc[s][c], b, d);
             }
@@ -270,9 +282,10 @@ __global__ void __launch_bounds__(128, MINB) hop_mrhs_kernel(const HopParams prm
             if (active) *(reinterpret_cast<float *>(prm.out.scale + (size_t)rhs * prm.out.rhs_stride) + i) = m;
             inv = m > 0 ? (R)1 / m : (R)0;
         }
-        rec_store<P, D>(own(7), acc, inv);
+        __syncwarp();   // every lane has read its diagonal record from the buffer
+        rec_store<P, D>(own, acc, inv);
         __syncwarp();
-        warp_scatter<NC, SU>(buf(7), prm.out.data + (size_t)rhs * prm.out.rhs_stride, wfirst, g.vh, lane);
+        warp_scatter<NC, SU>(buf, prm.out.data + (size_t)rhs * prm.out.rhs_stride, wfirst, g.vh, lane);
         if constexpr (EPI == EPI_STORE) return;
         R n2 = 0;
         if (active) {
@@ -290,17 +303,16 @@ __global__ void __launch_bounds__(128, MINB) hop_mrhs_kernel(const HopParams prm
         constexpr int CPC = 16 / (int)prec_cbytes(PC);
         char *r_base = prm.r.data + (size_t)rhs * prm.r.rhs_stride;
         char *x_base = prm.x.data + (size_t)rhs * prm.x.rhs_stride;
-        warp_gather<NCC, SU>(buf(8), r_base, (int)ie, lane);
-        cp_async_commit();
-        warp_gather<NCC, SU>(buf(7), x_base, (int)ie, lane);
+        // r, then p, then x through the warp's one buffer
+        warp_gather<NCC, SU>(buf, r_base, (int)ie, lane);
         cp_async_commit();
         const R alpha = (R)prm.state[rhs].alpha;
         R n2 = 0;
-        cp_async_wait<1>();
+        cp_async_wait<0>();
         __syncwarp();
 #pragma unroll
         for (int j = 0; j < NCC; j++) {
-            uint4 v = own(8)[j];
+            uint4 v = own[j];
 #pragma unroll
             for (int q = 0; q < CPC; q++) {
                 const int n = j * CPC + q;
@@ -318,26 +330,35 @@ __global__ void __launch_bounds__(128, MINB) hop_mrhs_kernel(const HopParams prm
                     v.w = __float_as_uint(rr.im);
                 }
             }
-            own(8)[j] = v;
+            own[j] = v;
         }
         __syncwarp();
-        warp_scatter<NCC, SU>(buf(8), r_base, wfirst, g.vh, lane);
+        warp_scatter<NCC, SU>(buf, r_base, wfirst, g.vh, lane);
         __syncwarp();
-        warp_gather<NC, SU>(buf(8), prm.p.data + (size_t)rhs * prm.p.rhs_stride, (int)ie, lane);
+        warp_gather<NC, SU>(buf, prm.p.data + (size_t)rhs * prm.p.rhs_stride, (int)ie, lane);
         cp_async_commit();
         const R psc = (R)SIO::ld_scale(prm.p, rhs, ie);
         cp_async_wait<0>();
         __syncwarp();
+        cx<R> pp[4 * D];
+#pragma unroll
+        for (int n = 0; n < 4 * D; n++) {
+            pp[n] = rec_comp<P>(own, n);
+            if constexpr (S::scaled) pp[n] = scale_rn(psc, pp[n]);
+        }
+        __syncwarp();
+        warp_gather<NCC, SU>(buf, x_base, (int)ie, lane);
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncwarp();
 #pragma unroll
         for (int j = 0; j < NCC; j++) {
-            uint4 v = own(7)[j];
+            uint4 v = own[j];
 #pragma unroll
             for (int q = 0; q < CPC; q++) {
                 const int n = j * CPC + q;
                 cx<RC> xx = rec_comp<PC>(&v, q);
-                cx<R> pp = rec_comp<P>(own(8), n);
-                if constexpr (S::scaled) pp = scale_rn(psc, pp);
-                rmac(xx, alpha, pp);
+                rmac(xx, alpha, pp[n]);
                 if constexpr (PC == HR_F64) {
                     v = make_uint4((unsigned)__double2loint(xx.re), (unsigned)__double2hiint(xx.re),
                                    (unsigned)__double2loint(xx.im), (unsigned)__double2hiint(xx.im));
@@ -349,10 +370,10 @@ __global__ void __launch_bounds__(128, MINB) hop_mrhs_kernel(const HopParams prm
                     v.w = __float_as_uint(xx.im);
                 }
             }
-            own(7)[j] = v;
+            own[j] = v;
         }
         __syncwarp();
-        warp_scatter<NCC, SU>(buf(7), x_base, wfirst, g.vh, lane);
+        warp_scatter<NCC, SU>(buf, x_base, wfirst, g.vh, lane);
         double tot;
         if (warp_grid_reduce(active ? (double)n2 : 0.0, part, prm.counters + rhs, g.ntiles, tile, tot))
             hop_finalize(prm, rhs, tot);
