@@ -5,12 +5,13 @@ by a random Haar gauge transform, antiperiodic in time.
 
 One step is one pass of the whole hot path over one batch of synthetic
 input, as an HMC force evaluation of the fermion monomial does it:
-  1. represent the fundamental gauge field (FP64 and FP32 stored links),
+  1. represent the fundamental gauge field (FP64, FP32 and float-float
+     stored links, FP64 and FP32 fundamental links for the in-kernel rebuild),
   2. D_eo applications in FP32 and FP64 (the metric's kernel, event-timed),
-  3. mixed-precision CG (FP32 inner, FP64 defect correction) on
-     Dhat^dag Dhat x = phi to a true relative residual of 1e-10
-     (--residual df64 forms the intermediate true residuals in float-float
-     and confirms the one that meets the tolerance in FP64),
+  3. mixed-precision CG (FP32 inner, defect correction) on
+     Dhat^dag Dhat x = phi to a true relative residual of 1e-10: the
+     intermediate true residuals in float-float, the one that meets the
+     tolerance in FP64 (--residual f64: every true residual in FP64),
   4. the fermion force of S = phi^dag (Dhat^dag Dhat)^-1 phi (fused with the
      solve: the force reuses the operator applications of its final residual).
 
@@ -988,7 +989,7 @@ def run_deo(args, local_rank):
 
 def run_force(args, local_rank):
     """Fermion force only (for profiler captures): Y = Dhat X, then W untimed
-    and K timed calls of the even/odd force in FP64."""
+    and K timed calls of the even/odd force (FP64 or float-float kernel)."""
     import torch
     from paper_2503_06721_gb300 import build, hr, synth
     dev = torch.device(f"cuda:{local_rank}")
@@ -996,22 +997,23 @@ def run_force(args, local_rank):
     build.build()
     wl = synth.WORKLOADS[args.workload]
     lat = hr.Lattice(wl.N, wl.rep, wl.dims, wl.bc, wl.m0)
-    g = hr.Gauge(lat, wl.links(device=dev), precs=("f64",))
+    arith = hr.PRECS[args.force_arith]
+    g = hr.Gauge(lat, wl.links(device=dev), precs=("f64",) + (("df64",) if arith == hr.DF64 else ()))
     X = synth.gaussian_spinor(lat.volume // 2, lat.D, 5, device=dev)
     Y = g.apply(hr.EO_PRECOND, hr.F64, X)
     F = torch.zeros((lat.volume, 4, wl.N ** 2 - 1), dtype=torch.float64, device=dev)
     for _ in range(max(args.warmup, 1)):
-        g.force(hr.EO_PRECOND, X, Y, F=F)
+        g.force(hr.EO_PRECOND, X, Y, F=F, arith=arith)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("hr_force")
     e0.record()
     for _ in range(args.steps):
-        g.force(hr.EO_PRECOND, X, Y, F=F)
+        g.force(hr.EO_PRECOND, X, Y, F=F, arith=arith)
     e1.record()
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
-    print(json.dumps({"mode": "force", "workload": args.workload,
+    print(json.dumps({"mode": "force", "workload": args.workload, "arith": args.force_arith,
                       "ms_per_call": round(e0.elapsed_time(e1) / args.steps, 4),
                       "note": "two force_kernel launches (one per parity) and two FP64 odd-half hops per call"}))
 
@@ -1039,9 +1041,11 @@ def main():
     ap.add_argument("--mode", choices=["step", "deo", "force"], default="step",
                     help="deo: only D_eo applications; force: only the fermion force (profiler captures)")
     ap.add_argument("--prec", choices=["f64", "f32", "f16", "bf16", "df64"], default="f32")
-    ap.add_argument("--residual", choices=["df64", "f64"], default="f64",
+    ap.add_argument("--residual", choices=["df64", "f64"], default="df64",
                     help="arithmetic of the defect-correction true residuals (df64: float-float, "
                          "confirmed once in FP64 when it meets the tolerance)")
+    ap.add_argument("--force-arith", choices=["f64", "df64"], default="f64",
+                    help="force mode: arithmetic of the force kernel")
     ap.add_argument("--rebuild", action="store_true", help="deo mode: rebuild links in-kernel")
     ap.add_argument("--nrhs", type=int, default=1, help="deo mode: right-hand sides per application")
     ap.add_argument("--variant", type=int, default=None, choices=[0, 1, 2, 3, 4],

@@ -153,7 +153,8 @@ hr_status hr_gauge_set_clover(hr_gauge *g, const void *U_fund, double csw,
 
 /* Chooses STORED, REBUILD or AUTO links for later operator calls on g.
  * HR_ERR_INVALID if that storage (both, for AUTO) was not requested at
- * creation.  The force always reads the stored FP64 links. */
+ * creation.  The force always reads stored links (FP64, or DF64 for the
+ * float-float force). */
 hr_status hr_gauge_set_link_mode(hr_gauge *g, hr_link_mode mode);
 
 /* The link mode operator calls in precision prec use now (STORED or
@@ -336,8 +337,11 @@ hr_status hr_cg_solve_batched(int n_inst, const hr_gauge *const *g,
  * even/odd system D_oe x and (D^dag)_oe Dhat x) are those of the solve's
  * final FP64 true residual, kept instead of recomputed.
  *   Y  optional DEVICE output of D x / Dhat x (NULL: not returned).
- * The handle needs stored FP64 links.  F is left unchanged if the solve
- * fails (its status is returned).  BLOCKS like hr_cg_solve. */
+ * The handle needs stored FP64 links.  With params->residual = HR_DF64
+ * the force kernel runs in float-float on the stored DF64 links
+ * (hr_dirac_force_prec with HR_DF64); otherwise in FP64.  F is left
+ * unchanged if the solve fails (its status is returned).  BLOCKS like
+ * hr_cg_solve. */
 hr_status hr_cg_solve_force(const hr_gauge *g, hr_parity sys, const void *b,
                             void *x, const hr_cg_params *params,
                             hr_cg_result *res, void *Y, double coeff,
@@ -512,6 +516,20 @@ hr_status hr_hmc_update(hr_gauge *g, void *U_fund, double *pi, const void *eta,
  * F is a device array of V*4*(N*N-1) doubles. */
 hr_status hr_dirac_force(const hr_gauge *g, hr_parity sys, const void *X,
                          const void *Y, double coeff, void *F, void *stream);
+
+/* hr_dirac_force with a choice of arithmetic for the force kernel:
+ *   arith = HR_F64   FP64 on the stored FP64 links (hr_dirac_force);
+ *   arith = HR_DF64  float-float (about 48 significant bits) on the stored
+ *                    DF64 links, which g must hold: the FP64 spinors are
+ *                    projected in FP64 and split into float-float pairs, the
+ *                    matrix products run on the FP32 units, and F (FP64) is
+ *                    accumulated in FP64.  Each component agrees with the
+ *                    FP64 force to about 1e-13 of max |F|.
+ * The hops that form D_oe X and (D^dag)_oe Y for sys = HR_EO_PRECOND are
+ * FP64 in both cases.  HR_ERR_INVALID for another arith or missing links. */
+hr_status hr_dirac_force_prec(const hr_gauge *g, hr_parity sys, const void *X,
+                              const void *Y, double coeff, void *F,
+                              hr_prec arith, void *stream);
 
 /* ------------------------------------------------------------------ */
 /* Introspection                                                         */

@@ -684,13 +684,27 @@ hr_status hr_field_dot(const hr_lattice_desc *lat, hr_parity par, hr_prec prec, 
 hr_status hr_dirac_force(const hr_gauge *g, hr_parity sys, const void *X, const void *Y, double coeff, void *F,
                          void *stream)
 {
+    return hr_dirac_force_prec(g, sys, X, Y, coeff, F, HR_F64, stream);
+}
+
+hr_status hr_dirac_force_prec(const hr_gauge *g, hr_parity sys, const void *X, const void *Y, double coeff, void *F,
+                              hr_prec arith, void *stream)
+{
     if (g && g->clover_mode) {
         set_error("hr_dirac_force: the clover term's force is not provided");
         return HR_ERR_UNSUPPORTED;
     }
     if (!g || !X || !Y || !F) { set_error("hr_dirac_force: NULL argument"); return HR_ERR_INVALID; }
+    if (arith != HR_F64 && arith != HR_DF64) {
+        set_error("hr_dirac_force: arithmetic must be HR_F64 or HR_DF64");
+        return HR_ERR_INVALID;
+    }
     if (!(g->prec_mask & (1u << HR_F64)) || !g->rep[HR_F64][0]) {
         set_error("hr_dirac_force needs FP64 stored represented links in the handle");
+        return HR_ERR_INVALID;
+    }
+    if (arith == HR_DF64 && !g->rep[HR_DF64][0]) {
+        set_error("hr_dirac_force: the float-float force needs DF64 stored represented links in the handle");
         return HR_ERR_INVALID;
     }
     if (sys != HR_FULL && sys != HR_EO_PRECOND) { set_error("hr_dirac_force: sys must be FULL or EO_PRECOND"); return HR_ERR_INVALID; }
@@ -724,14 +738,14 @@ hr_status hr_dirac_force(const hr_gauge *g, hr_parity sys, const void *X, const 
         if (st != HR_OK) return st;
         c = -coeff;
     }
-    return force_full(g, fx, fy, c, reinterpret_cast<double *>(F), s);
+    return force_full(g, fx, fy, c, reinterpret_cast<double *>(F), arith, s);
 }
 
 }  // extern "C"
 
 namespace hr {
 
-hr_status force_full(const hr_gauge *g, const FieldView &fx, const FieldView &fy, double c, double *F,
+hr_status force_full(const hr_gauge *g, const FieldView &fx, const FieldView &fy, double c, double *F, int arith,
                      cudaStream_t s)
 {
     const long vh = g->geom.vh;
@@ -740,7 +754,8 @@ hr_status force_full(const hr_gauge *g, const FieldView &fx, const FieldView &fy
         ForceParams fp;
         fp.g = g->geom;
         fp.parity = p;
-        fp.links = g->rep[HR_F64][p];
+        fp.arith = arith;
+        fp.links = g->rep[arith][p];
         fp.X_here = half_view(fx, p, vh, D, HR_F64);
         fp.Y_here = half_view(fy, p, vh, D, HR_F64);
         fp.X_nb = half_view(fx, 1 - p, vh, D, HR_F64);

@@ -59,8 +59,9 @@ int hop_variant(const hr_gauge *g, int P, bool rebuild, int epi, int nrhs);
 hr_status tune_hops(hr_gauge *g, int P, int nrhs, cudaStream_t stream);
 
 // F += c * (force of the full-operator action -2 Re <Y, D X>) for full FP64
-// fields X = fx, Y = fy, reading the stored FP64 links
-hr_status force_full(const hr_gauge *g, const FieldView &fx, const FieldView &fy, double c, double *F,
+// fields X = fx, Y = fy, in FP64 on the stored FP64 links (arith = HR_F64)
+// or in float-float on the stored DF64 links (HR_DF64)
+hr_status force_full(const hr_gauge *g, const FieldView &fx, const FieldView &fy, double c, double *F, int arith,
                      cudaStream_t s);
 
 // the clover diagonal (hr_clover.cu): build C and C^-1 from U_F for the

@@ -87,7 +87,11 @@ __global__ void __launch_bounds__(BLAS_THREADS) k_convert(const BlasParams bp)
 #pragma unroll
     for (int s = 0; s < 4; s++)
 #pragma unroll
-        for (int c = 0; c < D; c++) w[s][c] = {(RD)(f * (double)v[s][c].re), (RD)(f * (double)v[s][c].im)};
+        for (int c = 0; c < D; c++) {
+            const double re = to_f64(v[s][c].re), im = to_f64(v[s][c].im);
+            w[s][c] = f == 1.0 ? cx<RD>{from_f64<RD>(re), from_f64<RD>(im)}
+                               : cx<RD>{from_f64<RD>(f * re), from_f64<RD>(f * im)};
+        }
     SpinorIO<PD, D>::store(bp.a, rhs, i, w);
 }
 
@@ -214,7 +218,7 @@ __global__ void __launch_bounds__(BLAS_THREADS) k_inner_init(const BlasParams bp
         for (int s = 0; s < 4; s++)
 #pragma unroll
             for (int c = 0; c < D; c++) {
-                ri[s][c] = {(float)(f * r[s][c].re), (float)(f * r[s][c].im)};
+                ri[s][c] = {f32_rn(f * r[s][c].re), f32_rn(f * r[s][c].im)};
                 z[s][c] = {0.f, 0.f};
                 n2 += ri[s][c].re * ri[s][c].re + ri[s][c].im * ri[s][c].im;
             }
@@ -259,8 +263,8 @@ __global__ void __launch_bounds__(BLAS_THREADS) k_outer_update(const BlasParams 
     for (int s = 0; s < 4; s++)
 #pragma unroll
         for (int c = 0; c < D; c++) {
-            x[s][c].re = fma(f, (double)e[s][c].re, x[s][c].re);
-            x[s][c].im = fma(f, (double)e[s][c].im, x[s][c].im);
+            x[s][c].re = fma(f, f64_of(e[s][c].re), x[s][c].re);
+            x[s][c].im = fma(f, f64_of(e[s][c].im), x[s][c].im);
         }
     SpinorIO<HR_F64, D>::store(bp.a, rhs, i, x);
 }
@@ -280,8 +284,8 @@ __global__ void __launch_bounds__(BLAS_THREADS) k_dot(const BlasParams bp)
         for (int s = 0; s < 4; s++)
 #pragma unroll
             for (int c = 0; c < D; c++) {
-                const double ar = (double)a[s][c].re, ai = (double)a[s][c].im;
-                const double br = (double)b[s][c].re, bi = (double)b[s][c].im;
+                const double ar = to_f64(a[s][c].re), ai = to_f64(a[s][c].im);
+                const double br = to_f64(b[s][c].re), bi = to_f64(b[s][c].im);
                 v[0] += ar * br + ai * bi;
                 v[1] += ar * bi - ai * br;
             }

@@ -702,6 +702,10 @@ extern "C" hr_status hr_cg_solve_force(const hr_gauge *g, hr_parity sys, const v
         set_error("hr_cg_solve_force needs FP64 stored represented links in the handle");
         return HR_ERR_INVALID;
     }
+    if (params->residual == HR_DF64 && !g->rep[HR_DF64][0]) {
+        set_error("hr_cg_solve_force: the float-float force needs DF64 stored represented links in the handle");
+        return HR_ERR_INVALID;
+    }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     std::vector<Inst> ins(1);
     st = prepare(ins[0], g, sys, b, x, 1, params->inner, params->residual, res, s, true);
@@ -717,10 +721,13 @@ extern "C" hr_status hr_cg_solve_force(const hr_gauge *g, hr_parity sys, const v
     }
     const size_t fb = field_rhs_bytes(c.ns, c.D, HR_F64);
     if (Y && (st = kernel_copy(Y, in.q64.data, fb, s)) != HR_OK) return st;
-    if (sys == HR_FULL) return force_full(g, in.vx, in.q64, coeff, reinterpret_cast<double *>(F), s);
+    // the force in the residual's arithmetic: float-float when the caller
+    // chose float-float residuals (the handle then holds DF64 links)
+    const int arith = params->residual == HR_DF64 ? HR_DF64 : HR_F64;
+    if (sys == HR_FULL) return force_full(g, in.vx, in.q64, coeff, reinterpret_cast<double *>(F), arith, s);
     // even/odd: minus the full-operator force on X' = (x, D_oe x), Y' = (Dhat x, (D^dag)_oe Dhat x)
     if ((st = kernel_copy(in.fx.data, x, fb, s)) != HR_OK) return st;
-    return force_full(g, in.fx, in.fy, -coeff, reinterpret_cast<double *>(F), s);
+    return force_full(g, in.fx, in.fy, -coeff, reinterpret_cast<double *>(F), arith, s);
 }
 
 extern "C" hr_status hr_cg_solve_batched(int n_inst, const hr_gauge *const *g, hr_parity sys, const void *const *b,

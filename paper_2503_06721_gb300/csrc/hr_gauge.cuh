@@ -58,7 +58,8 @@ hr_status represent_launch(const hr_gauge &g, const double2 *UF, cudaStream_t st
 struct ForceParams {
     Geom g;
     int parity;             // sites of this parity own the links processed
-    const void *links;      // F64 stored records of this parity (U_R with signs)
+    int arith;              // HR_F64: FP64 arithmetic, HR_DF64: float-float
+    const void *links;      // stored records of this parity (U_R with signs), FP64 or DF64 as arith
     FieldView X_here, Y_here;   // FULL-field views of X, Y at sites of `parity`
     FieldView X_nb, Y_nb;       // views of the opposite parity
     const double *TR;

@@ -5,28 +5,56 @@
 
 namespace hr {
 
-// one link entry in precision P (real: the real part only)
-__device__ inline void store_entry(int P, bool real, char *dst, cx<double> v)
+// one link entry v in precision P at fw and its conjugate at bw (real: the
+// real part only); each part is rounded once and the conjugate's imaginary
+// part is the exact negation of the rounded one
+template <int P, bool REAL>
+__device__ __forceinline__ void store_pair(char *fw, char *bw, cx<double> v)
 {
-    if (P == HR_DF64) {
-        const df re(v.re), im(v.im);
-        if (real)
-            *reinterpret_cast<float2 *>(dst) = make_float2(re.hi, re.lo);
-        else
-            *reinterpret_cast<float4 *>(dst) = make_float4(re.hi, re.lo, im.hi, im.lo);
-        return;
-    }
-    if (real) {
-        if (P == HR_F64) *reinterpret_cast<double *>(dst) = v.re;
-        if (P == HR_F32) *reinterpret_cast<float *>(dst) = (float)v.re;
-        if (P == HR_F16) *reinterpret_cast<__half *>(dst) = __double2half(v.re);
-        if (P == HR_BF16) *reinterpret_cast<__nv_bfloat16 *>(dst) = __double2bfloat16(v.re);
+    if constexpr (P == HR_DF64) {
+        const df re(v.re);
+        if constexpr (REAL) {
+            *reinterpret_cast<float2 *>(fw) = make_float2(re.hi, re.lo);
+            *reinterpret_cast<float2 *>(bw) = make_float2(re.hi, re.lo);
+        } else {
+            const df im(v.im);
+            *reinterpret_cast<float4 *>(fw) = make_float4(re.hi, re.lo, im.hi, im.lo);
+            *reinterpret_cast<float4 *>(bw) = make_float4(re.hi, re.lo, -im.hi, -im.lo);
+        }
+    } else if constexpr (REAL) {
+        if constexpr (P == HR_F64) {
+            *reinterpret_cast<double *>(fw) = v.re;
+            *reinterpret_cast<double *>(bw) = v.re;
+        } else if constexpr (P == HR_F32) {
+            const float r = f32_rn(v.re);
+            *reinterpret_cast<float *>(fw) = r;
+            *reinterpret_cast<float *>(bw) = r;
+        } else if constexpr (P == HR_F16) {
+            const __half r = __double2half(v.re);
+            *reinterpret_cast<__half *>(fw) = r;
+            *reinterpret_cast<__half *>(bw) = r;
+        } else {
+            const __nv_bfloat16 r = __double2bfloat16(v.re);
+            *reinterpret_cast<__nv_bfloat16 *>(fw) = r;
+            *reinterpret_cast<__nv_bfloat16 *>(bw) = r;
+        }
     } else {
-        if (P == HR_F64) *reinterpret_cast<double2 *>(dst) = make_double2(v.re, v.im);
-        if (P == HR_F32) *reinterpret_cast<float2 *>(dst) = make_float2((float)v.re, (float)v.im);
-        if (P == HR_F16) *reinterpret_cast<__half2 *>(dst) = __halves2half2(__double2half(v.re), __double2half(v.im));
-        if (P == HR_BF16)
-            *reinterpret_cast<__nv_bfloat162 *>(dst) = __halves2bfloat162(__double2bfloat16(v.re), __double2bfloat16(v.im));
+        if constexpr (P == HR_F64) {
+            *reinterpret_cast<double2 *>(fw) = make_double2(v.re, v.im);
+            *reinterpret_cast<double2 *>(bw) = make_double2(v.re, -v.im);
+        } else if constexpr (P == HR_F32) {
+            const float r = f32_rn(v.re), i = f32_rn(v.im);
+            *reinterpret_cast<float2 *>(fw) = make_float2(r, i);
+            *reinterpret_cast<float2 *>(bw) = make_float2(r, -i);
+        } else if constexpr (P == HR_F16) {
+            const __half r = __double2half(v.re), i = __double2half(v.im);
+            *reinterpret_cast<__half2 *>(fw) = __halves2half2(r, i);
+            *reinterpret_cast<__half2 *>(bw) = __halves2half2(r, __hneg(i));
+        } else {
+            const __nv_bfloat16 r = __double2bfloat16(v.re), i = __double2bfloat16(v.im);
+            *reinterpret_cast<__nv_bfloat162 *>(fw) = __halves2bfloat162(r, i);
+            *reinterpret_cast<__nv_bfloat162 *>(bw) = __halves2bfloat162(r, __hneg(i));
+        }
     }
 }
 
@@ -62,41 +90,76 @@ __global__ void __launch_bounds__(128) represent_kernel(const double2 *__restric
     const int lb = (int)(ib % HR_TILE);
     const RepOut &of = parity == 0 ? o0 : o1;   // records of x's parity
     const RepOut &ob = parity == 0 ? o1 : o0;   // records of (x+mu)'s parity
-    const int L[4] = {g.T, g.X, g.Y, g.Z};
     const long lex = lex_of(g, s);
     const double2 *u = UF + ((size_t)lex * 4 + mu) * N * N;
-    cx<double> U[N][N];
-    for (int a = 0; a < N; a++)
-        for (int b = 0; b < N; b++) {
-            const double2 v = u[a * N + b];
-            U[a][b] = {v.x, v.y};
-        }
-    const bool neg = g.bc[mu] == -1 && s.c[mu] == L[mu] - 1;
-    bool any_rep = false;
-    for (int p = 0; p < HR_NPREC; p++) any_rep |= of.rep[p] != nullptr;
-    if (any_rep) {
-        cx<double> Rm[D][D];
-        represent<N, REP>(U, Rm);
-        const double sg = neg ? -1.0 : 1.0;
-        for (int r = 0; r < D; r++)
-            for (int q = 0; q < D; q++) {
-                const cx<double> v = sg * Rm[r][q];
-                for (int P = 0; P < HR_NPREC; P++) {
-                    if (!of.rep[P]) continue;
-                    const int RS = link_row_stride(N, REP, P);
-                    store_entry(P, REAL, reinterpret_cast<char *>(of.rep[P]) + link_offset(P, REAL, D * RS, tile, mu, lane, r * RS + q), v);
-                    // the dagger: entry (q, r) of the backward slot
-                    store_entry(P, REAL, reinterpret_cast<char *>(ob.rep[P]) + link_offset(P, REAL, D * RS, tb, 4 + mu, lb, q * RS + r), conj(v));
-                }
-            }
+    auto uld = [&](int a, int b) {
+        const double2 v = __ldg(u + a * N + b);
+        return cx<double>{v.x, v.y};
+    };
+    // the fundamental entries are copied one at a time (an 8 x 8 link would
+    // not fit in registers); a higher representation needs all of U at once
+    constexpr int NU = REP == HR_FUND ? 1 : N;
+    cx<double> U[NU][NU];
+    if constexpr (REP != HR_FUND) {
+#pragma unroll
+        for (int a = 0; a < N; a++)
+#pragma unroll
+            for (int b = 0; b < N; b++) U[a][b] = uld(a, b);
     }
-    for (int r = 0; r < N; r++)
-        for (int q = 0; q < N; q++)
-            for (int P = 0; P < HR_NPREC; P++) {
-                if (!of.fund[P]) continue;
-                store_entry(P, false, reinterpret_cast<char *>(of.fund[P]) + link_offset(P, false, N * N, tile, mu, lane, r * N + q), U[r][q]);
-                store_entry(P, false, reinterpret_cast<char *>(ob.fund[P]) + link_offset(P, false, N * N, tb, 4 + mu, lb, q * N + r), conj(U[r][q]));
+    const int Lmu = mu == 0 ? g.T : mu == 1 ? g.X : mu == 2 ? g.Y : g.Z;
+    const int xmu = mu == 0 ? s.c[0] : mu == 1 ? s.c[1] : mu == 2 ? s.c[2] : s.c[3];
+    const int bmu = mu == 0 ? g.bc[0] : mu == 1 ? g.bc[1] : mu == 2 ? g.bc[2] : g.bc[3];
+    // the boundary sign as a flip of the sign bits (no FP64 multiply)
+    const unsigned long long sgn = bmu == -1 && xmu == Lmu - 1 ? 0x8000000000000000ull : 0ull;
+    auto sg = [&](cx<double> e) {
+        return cx<double>{__longlong_as_double(__double_as_longlong(e.re) ^ (long long)sgn),
+                          __longlong_as_double(__double_as_longlong(e.im) ^ (long long)sgn)};
+    };
+    bool any_rep = false;
+    static_for<0, HR_NPREC>([&](auto PP) { any_rep |= of.rep[decltype(PP)::value] != nullptr; });
+    // every entry is formed once, in FP64, and written at once to the forward
+    // and backward records of each precision present; entry indices and
+    // precisions are compile-time constants, so nothing leaves the registers
+    static_for<0, D>([&](auto RR) {
+        constexpr int r = decltype(RR)::value;
+        static_for<0, D>([&](auto QQ) {
+            constexpr int q = decltype(QQ)::value;
+            if (!any_rep) return;
+            cx<double> v;
+            if constexpr (REP == HR_FUND)
+                v = sg(uld(r, q));
+            else
+                v = sg(rep_entry<N, REP, r, q>(U));
+            static_for<0, HR_NPREC>([&](auto PP) {
+                constexpr int P = decltype(PP)::value;
+                if (!of.rep[P]) return;
+                constexpr int RS = link_row_stride(N, REP, P);
+                // the dagger: entry (q, r) of the backward slot
+                store_pair<P, REAL>(reinterpret_cast<char *>(of.rep[P]) +
+                                        link_offset(P, REAL, D * RS, tile, mu, lane, r * RS + q),
+                                    reinterpret_cast<char *>(ob.rep[P]) +
+                                        link_offset(P, REAL, D * RS, tb, 4 + mu, lb, q * RS + r), v);
+            });
+        });
+    });
+    static_for<0, HR_NPREC>([&](auto PP) {
+        constexpr int P = decltype(PP)::value;
+        if (!of.fund[P]) return;
+#pragma unroll
+        for (int r = 0; r < N; r++)
+#pragma unroll
+            for (int q = 0; q < N; q++) {
+                cx<double> w;
+                if constexpr (REP == HR_FUND)
+                    w = uld(r, q);
+                else
+                    w = U[r][q];
+                store_pair<P, false>(reinterpret_cast<char *>(of.fund[P]) +
+                                         link_offset(P, false, N * N, tile, mu, lane, r * N + q),
+                                     reinterpret_cast<char *>(ob.fund[P]) +
+                                         link_offset(P, false, N * N, tb, 4 + mu, lb, q * N + r), w);
             }
+    });
 }
 
 template <int N, int REP>
@@ -128,7 +191,7 @@ hr_status represent_launch(const hr_gauge &gg, const double2 *UF, cudaStream_t s
 // matrix-vector products.  tr(T_R^a K) is pulled back to the fundamental,
 // tr(T_R^a K) = tr(T^a P) (below), so only the N x N matrix P meets the
 // generators.
-// One thread per (site of `parity`, mu); FP64 throughout.
+// One thread per (site of `parity`, mu); FP64 throughout, or float-float.
 // ---------------------------------------------------------------------------
 // The pullback tr(T_R^a K) = tr(T^a P) for K = x y^dag (x, y in the space of
 // R), written with the N x N matrices of the representation-space vectors:
@@ -145,58 +208,58 @@ hr_status represent_launch(const hr_gauge &gg, const double2 *UF, cudaStream_t s
 // D_R^2 products of K itself.
 
 // M = sum_n x_n e_n (SYM/2AS) or sum_a x_a T^a (ADJ); conj_x: use conj(x_n)
-// (for the complex real-basis matrices f_n of the SU(4) 2AS: conj(sum x_n f_n))
-template <int N, int REP, bool CONJ_X>
-__device__ __forceinline__ void rep_matrix(const cx<double> (&x)[rep_dim(N, REP)], cx<double> (&M)[N][N])
+// (for the complex real-basis matrices f_n of the SU(4) 2AS: conj(sum x_n f_n)).
+// R = double, or df for the float-float force.
+template <int N, int REP, bool CONJ_X, class R>
+__device__ __forceinline__ void rep_matrix(const cx<R> (&x)[rep_dim(N, REP)], cx<R> (&M)[N][N])
 {
 #pragma unroll
     for (int i = 0; i < N; i++)
 #pragma unroll
-        for (int j = 0; j < N; j++) M[i][j] = {0, 0};
+        for (int j = 0; j < N; j++) M[i][j] = {R(0), R(0)};
     if constexpr (REP == HR_ADJ) {
         static_for<0, N * N - 1>([&](auto AA) {
             constexpr int a = decltype(AA)::value;
-            const cx<double> xa = CONJ_X ? conj(x[a]) : x[a];
+            const cx<R> xa = CONJ_X ? conj(x[a]) : x[a];
             static_for<0, gen_nent(N, a)>([&](auto EE) {
                 constexpr int e = decltype(EE)::value;
-                cx<double> &m = M[gen_row(N, a, e)][gen_col(N, a, e)];
-                cmac(m, gen_val<double>(N, a, e), xa);
+                cx<R> &m = M[gen_row(N, a, e)][gen_col(N, a, e)];
+                cmac(m, gen_val<R>(N, a, e), xa);
             });
         });
     } else if constexpr (REP == HR_ASYM_REAL) {
         // sum_n x_n f_n, f_n = c_n S_n; with CONJ_X its complex conjugate
         static_for<0, rep_dim(N, REP)>([&](auto NN) {
             constexpr int n = decltype(NN)::value;
-            const cx<double> t = rb_c(n, x[n]);
-            const cx<double> xn = CONJ_X ? conj(t) : t;
+            const cx<R> t = rb_c(n, x[n]);
+            const cx<R> xn = CONJ_X ? conj(t) : t;
             static_for<0, 4>([&](auto EE) {
                 constexpr int e = decltype(EE)::value;
-                rmac(M[rb_row(n, e)][rb_col(n, e)], rb_val(n, e), xn);
+                rmac(M[rb_row(n, e)][rb_col(n, e)], R(rb_val(n, e)), xn);
             });
         });
     } else {
         static_for<0, rep_dim(N, REP)>([&](auto NN) {
             constexpr int n = decltype(NN)::value;
-            const cx<double> xn = CONJ_X ? conj(x[n]) : x[n];
+            const cx<R> xn = CONJ_X ? conj(x[n]) : x[n];
             static_for<0, sb_nent(N, REP, n)>([&](auto EE) {
                 constexpr int e = decltype(EE)::value;
-                cx<double> &m = M[sb_row(N, REP, n, e)][sb_col(N, REP, n, e)];
-                rmac(m, sb_val(N, REP, n, e), xn);
+                cx<R> &m = M[sb_row(N, REP, n, e)][sb_col(N, REP, n, e)];
+                rmac(m, R(sb_val(N, REP, n, e)), xn);
             });
         });
     }
 }
 
 // P += f (A B)
-template <int N>
-__device__ __forceinline__ void mat_mac(cx<double> (&P)[N][N], double f, const cx<double> (&A)[N][N],
-                                        const cx<double> (&B)[N][N])
+template <int N, class R>
+__device__ __forceinline__ void mat_mac(cx<R> (&P)[N][N], R f, const cx<R> (&A)[N][N], const cx<R> (&B)[N][N])
 {
 #pragma unroll
     for (int i = 0; i < N; i++)
 #pragma unroll
         for (int j = 0; j < N; j++) {
-            cx<double> s = {0, 0};
+            cx<R> s = {R(0), R(0)};
 #pragma unroll
             for (int k = 0; k < N; k++) cmac(s, A[i][k], B[k][j]);
             rmac(P[i][j], f, s);
@@ -204,38 +267,51 @@ __device__ __forceinline__ void mat_mac(cx<double> (&P)[N][N], double f, const c
 }
 
 // P += sgn * (pullback of x y^dag)
-template <int N, int REP>
-__device__ __forceinline__ void pullback_add(cx<double> (&P)[N][N], double sgn, const cx<double> (&x)[rep_dim(N, REP)],
-                                             const cx<double> (&y)[rep_dim(N, REP)])
+template <int N, int REP, class R>
+__device__ __forceinline__ void pullback_add(cx<R> (&P)[N][N], double sgn, const cx<R> (&x)[rep_dim(N, REP)],
+                                             const cx<R> (&y)[rep_dim(N, REP)])
 {
     if constexpr (REP == HR_FUND) {
 #pragma unroll
         for (int i = 0; i < N; i++)
 #pragma unroll
-            for (int j = 0; j < N; j++) rmac(P[i][j], sgn, x[i] * conj(y[j]));
+            for (int j = 0; j < N; j++) rmac(P[i][j], R(sgn), x[i] * conj(y[j]));
     } else if constexpr (REP == HR_ADJ) {
-        cx<double> X[N][N], Yd[N][N];
+        cx<R> X[N][N], Yd[N][N];
         rep_matrix<N, REP, false>(x, X);
         rep_matrix<N, REP, true>(y, Yd);   // Y^dag (T^a Hermitian)
-        mat_mac<N>(P, 2.0 * sgn, X, Yd);
-        mat_mac<N>(P, -2.0 * sgn, Yd, X);
+        mat_mac<N>(P, R(2.0 * sgn), X, Yd);
+        mat_mac<N>(P, R(-2.0 * sgn), Yd, X);
     } else {
-        cx<double> X[N][N], Yc[N][N];
+        cx<R> X[N][N], Yc[N][N];
         rep_matrix<N, REP, false>(x, X);
         rep_matrix<N, REP, true>(y, Yc);   // conj(Y)
-        mat_mac<N>(P, (REP == HR_SYM ? 2.0 : -2.0) * sgn, X, Yc);
+        mat_mac<N>(P, R((REP == HR_SYM ? 2.0 : -2.0) * sgn), X, Yc);
     }
 }
 
-template <int N, int REP>
+// the sum of a value over the two lanes of a pair
+__device__ __forceinline__ double pair_sum(double v) { return v + __shfl_xor_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ df pair_sum(df v)
+{
+    return v + df(__shfl_xor_sync(0xffffffffu, v.hi, 1), __shfl_xor_sync(0xffffffffu, v.lo, 1));
+}
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(df v) { return (double)v; }
+
+// LP = HR_F64: FP64 arithmetic on the FP64 links; LP = HR_DF64: float-float
+// arithmetic on the DF64 links (the FP64 spinors are projected in FP64 and
+// split into float-float pairs once; the FP32 units do the rest).
+template <int N, int REP, int LP>
 __global__ void __launch_bounds__(128) force_kernel(const ForceParams fp)
 {
     constexpr int D = rep_dim(N, REP);
     constexpr int NG = N * N - 1;
     constexpr bool REAL = rep_real(REP);
+    using R = typename St<LP>::R;
     using SIO = SpinorIO<HR_F64, D>;
-    constexpr int RS = link_row_stride(N, REP, HR_F64);
-    using LIO = LinkIO<HR_F64, REAL, D * RS>;
+    constexpr int RS = link_row_stride(N, REP, LP);
+    using LIO = LinkIO<LP, REAL, D * RS>;
     const Geom &g = fp.g;
     // two threads per link (adjacent lanes): spin component r = 0, 1 of the projections
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -244,7 +320,11 @@ __global__ void __launch_bounds__(128) force_kernel(const ForceParams fp)
     const long i = link >> 2;
     const int mu = (int)(link & 3);
     const bool active = i < g.vh;   // both lanes of a pair agree
-    cx<double> P[N][N];
+    cx<R> P[N][N];
+#pragma unroll
+    for (int a = 0; a < N; a++)
+#pragma unroll
+        for (int b = 0; b < N; b++) P[a][b] = {R(0), R(0)};
     if (active) {
         Site s = site_of(g, i, fp.parity);
         const long nb = neighbour(g, s, mu, +1);
@@ -253,27 +333,31 @@ __global__ void __launch_bounds__(128) force_kernel(const ForceParams fp)
             const uint4 v = __ldg(SIO::site_ptr(f, 0, site) + (sp * D + c));
             return cx<double>{__hiloint2double((int)v.y, (int)v.x), __hiloint2double((int)v.w, (int)v.z)};
         };
+        auto cv = [](cx<double> v) { return cx<R>{R(v.re), R(v.im)}; };
         // upper component r of (1 -+ g_mu) psi: psi_r -+ i^{ph} psi_q
-        cx<double> hX[D], hY[D], z[D], w[D];
+        cx<R> hX[D], hY[D], z[D], w[D];
+#pragma unroll
         for (int c = 0; c < D; c++) {
-            hX[c] = ld(fp.X_nb, nb, r, c) + (-1.0) * ipow(ph, ld(fp.X_nb, nb, q, c));
-            hY[c] = ld(fp.Y_nb, nb, r, c) + ipow(ph, ld(fp.Y_nb, nb, q, c));
-            z[c] = ld(fp.Y_here, i, r, c) + (-1.0) * ipow(ph, ld(fp.Y_here, i, q, c));
-            w[c] = ld(fp.X_here, i, r, c) + ipow(ph, ld(fp.X_here, i, q, c));
+            hX[c] = cv(ld(fp.X_nb, nb, r, c) + (-1.0) * ipow(ph, ld(fp.X_nb, nb, q, c)));
+            hY[c] = cv(ld(fp.Y_nb, nb, r, c) + ipow(ph, ld(fp.Y_nb, nb, q, c)));
+            z[c] = cv(ld(fp.Y_here, i, r, c) + (-1.0) * ipow(ph, ld(fp.Y_here, i, q, c)));
+            w[c] = cv(ld(fp.X_here, i, r, c) + ipow(ph, ld(fp.X_here, i, q, c)));
         }
         // u = U hX, v = U hY with U_R(x, mu) (slot mu, boundary sign included), row by row
         const long tile = i / HR_TILE;
         const int lane = (int)(i % HR_TILE);
         const uint4 *lp = LIO::slot_ptr(fp.links, tile, mu, lane);
-        cx<double> u[D], v[D];
+        cx<R> u[D], v[D];
+#pragma unroll
         for (int a = 0; a < D; a++) {
-            cx<double> su = {0, 0}, sv = {0, 0};
+            cx<R> su = {R(0), R(0)}, sv = {R(0), R(0)};
+#pragma unroll
             for (int b = 0; b < D; b++) {
                 const int cc = a * RS + b;
                 const uint4 ch = __ldg(lp + (size_t)(cc / LIO::VPC) * HR_TILE);
-                cx<double> uab;
+                cx<R> uab;
                 if constexpr (REAL)
-                    uab = {LIO::runpack(ch, cc % LIO::VPC), 0.0};
+                    uab = {LIO::runpack(ch, cc % LIO::VPC), R(0)};
                 else
                     uab = LIO::cunpack(ch, 0);
                 cmac(su, uab, hX[b]);
@@ -283,25 +367,16 @@ __global__ void __launch_bounds__(128) force_kernel(const ForceParams fp)
             v[a] = sv;
         }
         // K_r = u z^dag - w v^dag, pulled back to the fundamental
-#pragma unroll
-        for (int a = 0; a < N; a++)
-#pragma unroll
-            for (int b = 0; b < N; b++) P[a][b] = {0, 0};
         pullback_add<N, REP>(P, 1.0, u, z);
         pullback_add<N, REP>(P, -1.0, w, v);
-    } else {
-#pragma unroll
-        for (int a = 0; a < N; a++)
-#pragma unroll
-            for (int b = 0; b < N; b++) P[a][b] = {0, 0};
     }
     // combine the two spin components of the link
 #pragma unroll
     for (int a = 0; a < N; a++)
 #pragma unroll
         for (int b = 0; b < N; b++) {
-            P[a][b].re += __shfl_xor_sync(0xffffffffu, P[a][b].re, 1);
-            P[a][b].im += __shfl_xor_sync(0xffffffffu, P[a][b].im, 1);
+            P[a][b].re = pair_sum(P[a][b].re);
+            P[a][b].im = pair_sum(P[a][b].im);
         }
     if (!active || r != 0) return;
     const long lex = lex_of(g, site_of(g, i, fp.parity));
@@ -309,12 +384,12 @@ __global__ void __launch_bounds__(128) force_kernel(const ForceParams fp)
     // F^a += -coeff Im tr(T^a P) = -coeff Im sum_{(i,j,al) in T^a} al P_ji
     static_for<0, NG>([&](auto AA) {
         constexpr int a = decltype(AA)::value;
-        cx<double> tr = {0, 0};
+        cx<R> tr = {R(0), R(0)};
         static_for<0, gen_nent(N, a)>([&](auto EE) {
             constexpr int e = decltype(EE)::value;
-            cmac(tr, gen_val<double>(N, a, e), P[gen_col(N, a, e)][gen_row(N, a, e)]);
+            cmac(tr, gen_val<R>(N, a, e), P[gen_col(N, a, e)][gen_row(N, a, e)]);
         });
-        Fo[a] += -fp.coeff * tr.im;
+        Fo[a] += -fp.coeff * to_double(tr.im);
     });
 }
 
@@ -322,7 +397,11 @@ template <int N, int REP>
 hr_status force_launch(const ForceParams &fp, cudaStream_t stream)
 {
     const long threads = fp.g.vh * 8;   // two threads per link
-    force_kernel<N, REP><<<(unsigned)((threads + 127) / 128), 128, 0, stream>>>(fp);
+    const unsigned blocks = (unsigned)((threads + 127) / 128);
+    if (fp.arith == HR_DF64)
+        force_kernel<N, REP, HR_DF64><<<blocks, 128, 0, stream>>>(fp);
+    else
+        force_kernel<N, REP, HR_F64><<<blocks, 128, 0, stream>>>(fp);
     HR_LAUNCH_CHECK("force_kernel");
     return HR_OK;
 }

@@ -19,6 +19,7 @@
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "hr.h"
 
@@ -131,15 +132,140 @@ __host__ __device__ __forceinline__ cx<R> ipow(int k, cx<R> a)
 using ::fma;
 using ::isfinite;
 
+// ---------------------------------------------------------------------------
+// FP64 <-> FP32 conversions from the IEEE 754 bit patterns.  GB300 executes
+// F2F conversions to and from 64-bit types at its FP64 rate (measured: about
+// 1.8 per clock per SM, like a DFMA, against 109 FP32 FMAs), so the hot paths
+// convert with integer and FP32 operations instead.  Each function returns
+// exactly what the hardware conversion returns -- binary64 -> binary32 with
+// round to nearest, ties to even; binary32 -> binary64 exactly -- handling
+// zeros by their bits and handing the cases it does not treat (subnormal
+// inputs or results, overflow, Inf, NaN) to the hardware conversion.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ unsigned long long bits_of(double v)
+{
+#ifdef __CUDA_ARCH__
+    return (unsigned long long)__double_as_longlong(v);
+#else
+    unsigned long long u;
+    memcpy(&u, &v, 8);
+    return u;
+#endif
+}
+__host__ __device__ __forceinline__ double double_of(unsigned long long u)
+{
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)u);
+#else
+    double v;
+    memcpy(&v, &u, 8);
+    return v;
+#endif
+}
+__host__ __device__ __forceinline__ float float_of(unsigned u)
+{
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+#endif
+}
+__host__ __device__ __forceinline__ unsigned fbits_of(float f)
+{
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(f);
+#else
+    unsigned u;
+    memcpy(&u, &f, 4);
+    return u;
+#endif
+}
+
+// binary64 -> binary32, round to nearest even.  The 52-bit significand keeps
+// its top 23 bits; the 29 dropped bits decide the rounding (above half, or
+// exactly half with an odd last kept bit, rounds up, and the carry runs into
+// the exponent field, up to Inf).  Biased exponents e = 897 .. 1150 give
+// normal results; every other e goes to the hardware.
+__host__ __device__ __forceinline__ float f32_rn(double v)
+{
+    const unsigned long long u = bits_of(v);
+    const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
+    const unsigned e = (hw >> 20) & 0x7FFu;
+    if (e - 897u > 253u) {
+        if ((u << 1) == 0) return float_of(hw & 0x80000000u);   // +-0
+        return (float)v;
+    }
+    const unsigned m = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+    const unsigned rest = lw & 0x1FFFFFFFu;
+    const unsigned up = (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    return float_of((hw & 0x80000000u) | (((e - 896u) << 23) + m + up));
+}
+
+// binary32 -> binary64 (exact): rebias the exponent, shift the significand
+__host__ __device__ __forceinline__ double f64_of(float f)
+{
+    const unsigned u = fbits_of(f);
+    const unsigned e = (u >> 23) & 0xFFu;
+    if (e - 1u > 253u) {
+        if ((u << 1) == 0) return double_of((unsigned long long)(u & 0x80000000u) << 32);   // +-0
+        return (double)f;
+    }
+    const unsigned hw = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+    return double_of(((unsigned long long)hw << 32) | (unsigned long long)(u << 29));
+}
+
+struct df;
+__host__ __device__ df df_split(double v);
+
 struct df {
     float hi, lo;
     __host__ __device__ df() : hi(0.f), lo(0.f) {}
     __host__ __device__ df(float h, float l) : hi(h), lo(l) {}
     __host__ __device__ df(int v) : hi((float)v), lo(0.f) {}
-    // exact split of a double into two floats (uses one FP64 subtraction)
-    __host__ __device__ df(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
-    __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+    // hi = fl32(v), lo = fl32(v - hi) (df_split)
+    __host__ __device__ df(double v);
+    // hi + lo, exact in FP64 (|lo| <= ulp(hi) / 2): one FP64 addition
+    __host__ __device__ explicit operator double() const { return f64_of(hi) + f64_of(lo); }
 };
+
+// the split of a double into hi = fl32(v) and lo = fl32(v - hi), without
+// FP64 arithmetic: with hi from f32_rn, v - hi = rem 2^(E-52) exactly, where
+// rem (|rem| <= 2^28) is the dropped 29-bit remainder, less 2^29 when hi was
+// rounded up; rem = a 2^13 + b in two exactly representable floats, one fma
+// rounds it once, and the power of two 2^(E-52) scales it exactly.  Biased
+// exponents e = 949 .. 1149 (|v| about 2^-74 .. 2^127) take this path.
+__host__ __device__ __forceinline__ df df_split(double v)
+{
+    const unsigned long long u = bits_of(v);
+    const unsigned hw = (unsigned)(u >> 32), lw = (unsigned)u;
+    const unsigned e = (hw >> 20) & 0x7FFu;
+    if (e - 949u > 200u) {
+        if ((u << 1) == 0) return df(float_of(hw & 0x80000000u), 0.f);   // +-0
+        const float h = (float)v;
+        return df(h, (float)(v - (double)h));
+    }
+    const unsigned m = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+    const unsigned rest = lw & 0x1FFFFFFFu;
+    const unsigned up = (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    const unsigned sign = hw & 0x80000000u;
+    const float hi = float_of(sign | (((e - 896u) << 23) + m + up));
+    const int rem = (int)rest - (int)(up << 29);
+    const int a = rem >> 13;                 // |a| <= 2^15
+    const unsigned b = (unsigned)rem & 0x1FFFu;
+    const float af = float_of(0x4B400000u + (unsigned)a) - 12582912.0f;   // 1.5 * 2^23 + a, exact
+    const float bf = float_of(0x4B000000u | b) - 8388608.0f;              // 2^23 + b, exact
+    const float lo = fmaf(af, 8192.0f, bf) * float_of((e - 948u) << 23);
+    // v - hi carries the sign of v, but an exact zero difference is +0
+    return df(hi, rem ? float_of(fbits_of(lo) ^ sign) : 0.f);
+}
+__host__ __device__ inline df::df(double v)
+{
+    const df t = df_split(v);
+    hi = t.hi;
+    lo = t.lo;
+}
 __host__ __device__ __forceinline__ df df_qts(float a, float b)   // |a| >= |b|
 {
     const float s = a + b;
@@ -180,6 +306,19 @@ __host__ __device__ __forceinline__ df fma(df a, df b, df c)
     return df_qts(s.hi, t + c.lo + e);
 }
 __host__ __device__ __forceinline__ bool isfinite(df a) { return isfinite(a.hi); }
+
+// a double in real type R (float: rounded to nearest even; df: split) and back
+template <class R>
+__host__ __device__ __forceinline__ R from_f64(double v);
+template <>
+__host__ __device__ __forceinline__ double from_f64<double>(double v) { return v; }
+template <>
+__host__ __device__ __forceinline__ float from_f64<float>(double v) { return f32_rn(v); }
+template <>
+__host__ __device__ __forceinline__ df from_f64<df>(double v) { return df_split(v); }
+__host__ __device__ __forceinline__ double to_f64(double v) { return v; }
+__host__ __device__ __forceinline__ double to_f64(float v) { return f64_of(v); }
+__host__ __device__ __forceinline__ double to_f64(df v) { return (double)v; }
 
 // ---------------------------------------------------------------------------
 // representations (Table 1) -- compile-time structure
@@ -274,7 +413,7 @@ struct St<HR_F32> {
     __device__ __forceinline__ static cx<R> ld(C v) { return {v.x, v.y}; }
     __device__ __forceinline__ static C st(cx<R> v) { return make_float2(v.re, v.im); }
     __device__ __forceinline__ static R ldr(Rs v) { return v; }
-    __host__ __device__ __forceinline__ static Rs str(double v) { return (float)v; }
+    __host__ __device__ __forceinline__ static Rs str(double v) { return f32_rn(v); }
 };
 template <>
 struct St<HR_F16> {

@@ -50,6 +50,7 @@ __host__ __device__ inline cx<R> gen_val(int N, int a, int e)
 
 // --- SYM / ASYM basis element n ---
 #define HR_RSQRT2 0.70710678118654752440
+#define HR_SQRT2 1.41421356237309504880
 __host__ __device__ constexpr int sb_i(int N, int rep, int n) { return sympair_i(N, n, rep == HR_ASYM); }
 __host__ __device__ constexpr int sb_j(int N, int rep, int n) { return sympair_j(N, n, rep == HR_ASYM); }
 __host__ __device__ constexpr int sb_nent(int N, int rep, int n) { return sb_i(N, rep, n) == sb_j(N, rep, n) ? 1 : 2; }
@@ -157,6 +158,116 @@ __host__ __device__ __forceinline__ void static_for(F &&f)
     }
 }
 
+// a b + sgn c d as one fma chain per part
+__host__ __device__ __forceinline__ cx<double> cx_pair(cx<double> a, cx<double> b, double sgn, cx<double> c, cx<double> d)
+{
+    const cx<double> sc = {sgn * c.re, sgn * c.im};
+    return {fma(a.re, b.re, fma(-a.im, b.im, fma(sc.re, d.re, -sc.im * d.im))),
+            fma(a.re, b.im, fma(a.im, b.re, fma(sc.re, d.im, sc.im * d.re)))};
+}
+
+// the 2 x 2 minor of U on rows (a, b) and columns (c, d): U_ac U_bd - U_ad U_bc
+template <int N, int a, int b, int c, int d>
+__host__ __device__ __forceinline__ cx<double> minor2(const cx<double> (&U)[N][N])
+{
+    return cx_pair(U[a][c], U[b][d], -1.0, U[a][d], U[b][c]);
+}
+
+// --- one entry R(U)_AB with every basis index a compile-time constant, so
+// that a kernel can form and store the entries one at a time with U alone in
+// registers.  The sums of represent() are folded where basis elements pair
+// up (the compiler merges the products shared by several entries):
+//   SYM:  R_(ii),(kk) = U_ik^2,  R_(ii),(kl) = sqrt2 U_ik U_il,
+//         R_(ij),(kk) = sqrt2 U_ik U_jk,  R_(ij),(kl) = U_ik U_jl + U_il U_jk;
+//   ASYM: R_(ij),(kl) = U_ik U_jl - U_il U_jk, a 2 x 2 minor of U;
+//   real-basis 2AS: with f_n = c_n S_n, S_n = (E_P - E_P^T + s_n (E_Q - E_Q^T))/2
+//         on the oriented pairs P, Q of n, sum w v U_ik U_jl =
+//         (M(P_n;P_m) + s_m M(P_n;Q_m) + s_n M(Q_n;P_m) + s_n s_m M(Q_n;Q_m)) / 2,
+//         M the minors of U;
+//   ADJ:  the generators on one index pair share two products U_jk conj(U_il)
+//         among the four entries of their block. ---
+template <int N, int REP, int A, int B>
+__host__ __device__ __forceinline__ cx<double> rep_entry(const cx<double> (&U)[N][N])
+{
+    if constexpr (REP == HR_FUND) {
+        return U[A][B];
+    } else if constexpr (REP == HR_ADJ) {
+        constexpr int NO = noff(N);
+        if constexpr (A < NO && B < NO) {
+            // T_a, T_b on the pairs (p, q), (r, s): with z1 = U_qr conj(U_ps),
+            // z2 = U_qs conj(U_pr) the four (symmetric, antisymmetric) entries are
+            // Re z1 + Re z2, Im z1 - Im z2, Im z1 + Im z2, Re z2 - Re z1
+            constexpr int p = pair_j(N, A / 2), q = pair_k(N, A / 2), r = pair_j(N, B / 2), t = pair_k(N, B / 2);
+            const cx<double> z1 = U[q][r] * conj(U[p][t]), z2 = U[q][t] * conj(U[p][r]);
+            if constexpr (!(A & 1) && !(B & 1)) return {z1.re + z2.re, 0.0};
+            if constexpr (!(A & 1) && (B & 1)) return {z1.im - z2.im, 0.0};
+            if constexpr ((A & 1) && !(B & 1)) return {z1.im + z2.im, 0.0};
+            return {z2.re - z1.re, 0.0};
+        } else if constexpr (A < NO) {
+            // T_a on (p, q), T_b = diag(b_f): 2 sum_f b_f (Re or Im) U_qf conj(U_pf)
+            constexpr int p = pair_j(N, A / 2), q = pair_k(N, A / 2), l = B - NO + 1;
+            double acc = 0.0;
+            static_for<0, l + 1>([&](auto FF) {
+                constexpr int f = decltype(FF)::value;
+                const double bf = gen_val<double>(N, B, f).re;
+                const cx<double> y = U[q][f] * conj(U[p][f]);
+                acc = fma(bf, (A & 1) ? y.im : y.re, acc);
+            });
+            return {2.0 * acc, 0.0};
+        } else if constexpr (B < NO) {
+            // T_a = diag(a_e), T_b on (r, s): 2 sum_e a_e (Re or Im) U_er conj(U_es)
+            constexpr int r = pair_j(N, B / 2), t = pair_k(N, B / 2), l = A - NO + 1;
+            double acc = 0.0;
+            static_for<0, l + 1>([&](auto EE) {
+                constexpr int e = decltype(EE)::value;
+                const double ae = gen_val<double>(N, A, e).re;
+                const cx<double> x = U[e][r] * conj(U[e][t]);
+                acc = fma(ae, (B & 1) ? x.im : x.re, acc);
+            });
+            return {2.0 * acc, 0.0};
+        } else {
+            // both diagonal: 2 sum_e sum_f a_e b_f |U_ef|^2
+            constexpr int la = A - NO + 1, lb = B - NO + 1;
+            double acc = 0.0;
+            static_for<0, la + 1>([&](auto EE) {
+                constexpr int e = decltype(EE)::value;
+                double row = 0.0;
+                static_for<0, lb + 1>([&](auto FF) {
+                    constexpr int f = decltype(FF)::value;
+                    const double n2 = fma(U[e][f].re, U[e][f].re, U[e][f].im * U[e][f].im);
+                    row = fma(gen_val<double>(N, B, f).re, n2, row);
+                });
+                acc = fma(gen_val<double>(N, A, e).re, row, acc);
+            });
+            return {2.0 * acc, 0.0};
+        }
+    } else if constexpr (REP == HR_ASYM_REAL) {
+        constexpr int kn = A / 2, km = B / 2;
+        constexpr double sn = rb_val(A, 2) * 2.0, sm = rb_val(B, 2) * 2.0;
+        constexpr int p0 = rb_p(kn, 0), p1 = rb_p(kn, 1), q0 = rb_q(kn, 0), q1 = rb_q(kn, 1);
+        constexpr int r0 = rb_p(km, 0), r1 = rb_p(km, 1), t0 = rb_q(km, 0), t1 = rb_q(km, 1);
+        const cx<double> m1 = minor2<N, p0, p1, r0, r1>(U), m2 = minor2<N, p0, p1, t0, t1>(U);
+        const cx<double> m3 = minor2<N, q0, q1, r0, r1>(U), m4 = minor2<N, q0, q1, t0, t1>(U);
+        const cx<double> s = {0.5 * ((m1.re + sm * m2.re) + sn * (m3.re + sm * m4.re)),
+                              0.5 * ((m1.im + sm * m2.im) + sn * (m3.im + sm * m4.im))};
+        return rb_cc(A, rb_c(B, s));
+    } else {
+        constexpr bool asym = REP == HR_ASYM;
+        constexpr int i = sb_i(N, REP, A), j = sb_j(N, REP, A), k = sb_i(N, REP, B), l = sb_j(N, REP, B);
+        if constexpr (asym) {
+            return minor2<N, i, j, k, l>(U);
+        } else if constexpr (i == j && k == l) {
+            return U[i][k] * U[i][k];
+        } else if constexpr (i == j || k == l) {
+            // one index pair is diagonal: sqrt2 U_ik U_jl (the other product is the same)
+            const cx<double> pr = U[i][k] * U[j][l];
+            return {HR_SQRT2 * pr.re, HR_SQRT2 * pr.im};
+        } else {
+            return cx_pair(U[i][k], U[j][l], 1.0, U[i][l], U[j][k]);
+        }
+    }
+}
+
 // --- action of R(F) on a colour vector without forming R(F) (in-kernel
 // rebuild): vector -> matrix, conjugate by F, matrix -> vector.  All basis
 // indices are compile-time constants (static_for), so X, Z stay in registers.
@@ -247,19 +358,17 @@ __device__ __forceinline__ void rep_act(const cx<R> (&F)[N][N], const cx<R> (&v)
                 out[n] = rb_cc(n, s);
             });
         } else {
-            // v'_n = sum_{(i,j,w) in e_n} w Y_ij,  Y = Z F^T: Y_ij = sum_k Z_ik F_jk
+            // v'_n = sum_{(i,j,w) in e_n} w Y_ij with Y = Z F^T = F X F^T, which is
+            // symmetric (SYM) or antisymmetric (2AS) like X: the two entries of an
+            // off-diagonal e_n contribute alike, v'_n = sqrt2 Y_ij (i < j), and
+            // only Y_ij = sum_k Z_ik F_jk of the upper triangle is formed
             static_for<0, D>([&](auto NN) {
                 constexpr int n = decltype(NN)::value;
-                cx<R> s = {0, 0};
-                static_for<0, sb_nent(N, REP, n)>([&](auto EE) {
-                    constexpr int e = decltype(EE)::value;
-                    constexpr int i = sb_row(N, REP, n, e), j = sb_col(N, REP, n, e);
-                    cx<R> y = {0, 0};
+                constexpr int i = sb_i(N, REP, n), j = sb_j(N, REP, n);
+                cx<R> y = {0, 0};
 #pragma unroll
-                    for (int k = 0; k < N; k++) cmac(y, Z[i][k], F[j][k]);
-                    rmac(s, (R)sb_val(N, REP, n, e), y);
-                });
-                out[n] = s;
+                for (int k = 0; k < N; k++) cmac(y, Z[i][k], F[j][k]);
+                out[n] = i == j ? y : cx<R>{(R)HR_SQRT2 * y.re, (R)HR_SQRT2 * y.im};
             });
         }
     }

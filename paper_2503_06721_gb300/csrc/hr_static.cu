@@ -67,8 +67,8 @@ __global__ void __launch_bounds__(STATIC_DOT_THREADS) k_dot_static(long nsites, 
         for (int s = 0; s < 4; s++)
 #pragma unroll
             for (int c = 0; c < D; c++) {
-                const double xr = (double)x[s][c].re, xi = (double)x[s][c].im;
-                const double yr = (double)y[s][c].re, yi = (double)y[s][c].im;
+                const double xr = to_f64(x[s][c].re), xi = to_f64(x[s][c].im);
+                const double yr = to_f64(y[s][c].re), yi = to_f64(y[s][c].im);
                 s0 += xr * yr + xi * yi;
                 s1 += xr * yi - xi * yr;
             }

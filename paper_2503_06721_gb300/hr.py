@@ -40,7 +40,7 @@ EXPORTS = ["hr_represent_gauge", "hr_gauge_update", "hr_gauge_set_link_mode", "h
            "hr_field_bytes", "hr_field_convert", "hr_field_dot", "hr_field_dot_static",
            "hr_dirac_apply", "hr_dirac_dagger",
            "hr_cg_solve", "hr_cg_solve_batched", "hr_cg_solve_force", "hr_cg_solve_multishift",
-           "hr_field_lincomb", "hr_rational_approx", "hr_dirac_force", "hr_gauge_action", "hr_gauge_force", "hr_link_update",
+           "hr_field_lincomb", "hr_rational_approx", "hr_dirac_force", "hr_dirac_force_prec", "hr_gauge_action", "hr_gauge_force", "hr_link_update",
            "hr_momenta_energy", "hr_md_trajectory", "hr_hmc_update", "hr_gauge_set_clover", "hr_rep_dim", "hr_generators",
            "hr_status_string", "hr_last_error", "hr_launch_count"]
 
@@ -124,6 +124,7 @@ def load():
                                     ctypes.POINTER(I), ctypes.POINTER(CgParams),
                                     ctypes.POINTER(CgResult), P]),
         "hr_dirac_force": (I, [P, I, P, P, D, P, P]),
+        "hr_dirac_force_prec": (I, [P, I, P, P, D, P, I, P]),
         "hr_cg_solve_multishift": (I, [P, I, P, P, I, ctypes.POINTER(D), I, ctypes.POINTER(CgParams),
                                        ctypes.POINTER(CgResult), P]),
         "hr_field_lincomb": (I, [LP, I, D, P, I, ctypes.POINTER(D), P, P, I, P]),
@@ -494,12 +495,14 @@ class Gauge:
                     status=STATUS.get(r.status, r.status)) for r in res]
         return x, [out[k * nrhs:(k + 1) * nrhs] for k in range(ns)], st
 
-    def force(self, sys: int, X, Y, coeff: float = 1.0, F=None, stream=None):
+    def force(self, sys: int, X, Y, coeff: float = 1.0, F=None, arith: int = F64, stream=None):
+        """F += coeff * the fermion force (hr_dirac_force_prec); arith F64 or
+        DF64 (float-float on the handle's DF64 links)."""
         if F is None:
             F = torch.zeros((self.lat.volume, 4, self.lat.N ** 2 - 1), dtype=torch.float64,
                             device=X.device)
-        _check(load().hr_dirac_force(self.handle, sys, _ptr(X), _ptr(Y), coeff, _ptr(F),
-                                     _stream(stream)))
+        _check(load().hr_dirac_force_prec(self.handle, sys, _ptr(X), _ptr(Y), coeff, _ptr(F), arith,
+                                          _stream(stream)))
         return F
 
 

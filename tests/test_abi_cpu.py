@@ -79,9 +79,8 @@ def test_argument_errors_without_gpu(lib):
     assert lib.hr_represent_gauge(ctypes.byref(d), ctypes.c_void_p(16), 1, 2, None,
                                   ctypes.byref(out)) == -7
     assert b"stored links only" in lib.hr_last_error()
-    d.rep = hr.SYM
-    d.N = 4
-    d.rep = hr.ADJ   # SU(4) adjoint (D = 15) is not compiled
+    d.N = 2
+    d.rep = hr.ASYM   # the SU(2) antisymmetric (D = 1, a singlet) is not compiled
     assert lib.hr_represent_gauge(ctypes.byref(d), ctypes.c_void_p(16), 1, 1, None,
                                   ctypes.byref(out)) == -7
     assert lib.hr_dirac_apply(None, 0, 0, None, None, 1, None) == -1
@@ -90,3 +89,4 @@ def test_argument_errors_without_gpu(lib):
     assert lib.hr_cg_solve(None, hr.EO_PRECOND, None, None, 1, ctypes.byref(p), ctypes.byref(r),
                            None) == -1
     assert lib.hr_dirac_force(None, hr.FULL, None, None, 1.0, None, None) == -1
+    assert lib.hr_dirac_force_prec(None, hr.FULL, None, None, 1.0, None, hr.DF64, None) == -1

@@ -145,6 +145,69 @@ def test_force_parity(hr, oracle_mod, N, rep):
     np.testing.assert_allclose(F.cpu().numpy(), 2.0 * Fo, atol=1e-12 * np.abs(Fo).max())
 
 
+@pytest.mark.parametrize("N,rep", [(3, "SYM"), (2, "ADJ"), (3, "ADJ"), (4, "ASYM"), (3, "FUND"), (4, "ASYM_REAL")])
+def test_force_parity_df64(hr, oracle_mod, N, rep):
+    """The float-float force (hr_dirac_force_prec, HR_DF64: about 48
+    significant bits on the DF64 links) against the oracle's FP64 force: every
+    component within 1e-12 of max |F|, the FP64 kernel's own bar; and it
+    refuses a handle without DF64 links."""
+    dims = (4, 4, 2, 6)
+    lat = hr.Lattice(N, rep, dims, (-1, 1, 1, 1), -0.1)
+    L = oracle_mod.lat(N, rep, dims, (-1, 1, 1, 1), -0.1)
+    UF = H.links(dims, N, 0.6, seed=37)
+    UR = oracle_mod.represent_field(L, UF)
+    g = hr.Gauge(lat, G.to_gpu(UF), precs=("f64", "df64"))
+    V = lat.volume
+    X = H.spinor(V, lat.D, 41)
+    Y = H.spinor(V, lat.D, 43)
+    Fo = oracle_mod.force(L, UR, X, Y)
+    F = g.force(hr.FULL, G.to_gpu(G.eo_full(oracle_mod, L, X)), G.to_gpu(G.eo_full(oracle_mod, L, Y)),
+                coeff=1.0, arith=hr.DF64)
+    e_full = np.abs(F.cpu().numpy() - Fo).max() / np.abs(Fo).max()
+    assert e_full <= 1e-12, e_full
+    Xe, Ye = X[: V // 2], Y[: V // 2]
+    Xp = oracle_mod.merge(L, Xe, oracle_mod.hop_parity(L, UR, 1, Xe))
+    Yp = oracle_mod.merge(L, Ye, oracle_mod.hop_parity(L, UR, 1, Ye, dagger=True))
+    Fo = -oracle_mod.force(L, UR, Xp, Yp)
+    F = g.force(hr.EO_PRECOND, G.to_gpu(Xe), G.to_gpu(Ye), coeff=2.0, arith=hr.DF64)
+    e_eo = np.abs(F.cpu().numpy() - 2.0 * Fo).max() / np.abs(2.0 * Fo).max()
+    assert e_eo <= 1e-12, e_eo
+    G.report("force_df64", N=N, rep=rep, full=e_full, eo=e_eo)
+    g64 = hr.Gauge(lat, G.to_gpu(UF), precs=("f64",))
+    with pytest.raises(hr.HrError) as e:
+        g64.force(hr.FULL, G.to_gpu(G.eo_full(oracle_mod, L, X)), G.to_gpu(G.eo_full(oracle_mod, L, Y)),
+                  arith=hr.DF64)
+    assert e.value.status == -1
+    g.close()
+    g64.close()
+
+
+@pytest.mark.parametrize("N,rep", [(3, "SYM"), (3, "ADJ"), (4, "ASYM_REAL")])
+def test_cg_solve_force_fused_df64(hr, oracle_mod, N, rep):
+    """With float-float residuals the fused solve + force runs the float-float
+    force: bit for bit hr_cg_solve + Y = Dhat x + hr_dirac_force_prec(DF64),
+    and within 1e-12 of max |F| of the FP64 force of the same x."""
+    dims = (8, 4, 4, 6)
+    lat = hr.Lattice(N, rep, dims, (-1, 1, 1, 1), -0.2)
+    UF = H.links(dims, N, 0.5, seed=31)
+    g = hr.Gauge(lat, G.to_gpu(UF), precs=("f64", "f32", "df64"))
+    b = G.to_gpu(H.spinor(lat.nsites(hr.EVEN), lat.D, 23))
+    x1, F1, Y1, res, st = g.cg_solve_force(hr.EO_PRECOND, b, tol=1e-10, inner=hr.F32, inner_tol=1e-4,
+                                           residual=hr.DF64, coeff=0.7, want_y=True)
+    assert st == 0 and res[0]["true_rel_residual"] <= 1e-10
+    x2, res2, st2 = g.cg_solve(hr.EO_PRECOND, b, tol=1e-10, inner=hr.F32, inner_tol=1e-4, residual=hr.DF64)
+    assert st2 == 0
+    Y2 = g.apply(hr.EO_PRECOND, hr.F64, x2)
+    F2 = g.force(hr.EO_PRECOND, x2, Y2, coeff=0.7, arith=hr.DF64)
+    F3 = g.force(hr.EO_PRECOND, x2, Y2, coeff=0.7)
+    torch.cuda.synchronize()
+    assert torch.equal(x1, x2)
+    assert torch.equal(Y1, Y2)
+    assert torch.equal(F1, F2)
+    assert ((F1 - F3).abs().max() / F3.abs().max()).item() <= 1e-12
+    g.close()
+
+
 @pytest.mark.parametrize("N,rep", [(3, "SYM"), (3, "ADJ"), (4, "FUND")])
 @pytest.mark.parametrize("sys", [3, 2], ids=["eo", "full"])
 @pytest.mark.parametrize("inner", [0, 1], ids=["f64", "f32"])

@@ -121,6 +121,52 @@ def test_field_convert_equals_host_storage(hr, oracle_mod, prec, D_pair):
     np.testing.assert_array_equal(back, want)
 
 
+def _conversion_values(n, seed):
+    """FP64 values that exercise every branch of an FP64 -> FP32 rounding:
+    magnitudes 2^-100 .. 2^100 (including results below the FP32 normal
+    range), exact ties at the last kept bit (both parities of that bit),
+    values whose rounding carries into the exponent, and signed zeros."""
+    rng = np.random.default_rng(seed)
+    v = np.ldexp(rng.uniform(1.0, 2.0, n), rng.integers(-100, 100, n)) * rng.choice([-1.0, 1.0], n)
+    k = rng.integers(0, 2 ** 22, 512)
+    e = rng.integers(-30, 30, 512)
+    v[:512] = np.ldexp(1.0 + (2 * k + 1) * 2.0 ** -24, e)        # ties, kept bit even or odd
+    v[512:1024] = -np.ldexp(1.0 + (2 * k + 1) * 2.0 ** -24, e)
+    v[1024:1536] = np.ldexp(2.0 - 2.0 ** -30, e)                  # rounds up to 2^(e+1)
+    v[1536:1544] = [0.0, -0.0, 1.0, -1.0, 2.0 ** -126, -2.0 ** -127, 2.0 ** -149, 3.0e38]
+    return v
+
+
+@pytest.mark.parametrize("prec", [1, 4], ids=["f32", "df64"])
+def test_field_convert_bits_equal_host_rounding(hr, prec):
+    """hr_field_convert F64 -> F32 rounds every part to the nearest FP32
+    number (ties to even) and F64 -> DF64 splits it into hi = fl32(v), lo =
+    fl32(v - hi), bit for bit as the host storage model does; the conversions
+    back to F64 return the stored values exactly."""
+    from oracle import storage as OS
+    lat = hr.Lattice(3, "SYM", DIMS)
+    ns, D = lat.volume // 2, lat.D
+    n = ns * 4 * D
+    v = _conversion_values(2 * n, 91 + prec)
+    a = (v[:n] + 1j * v[n:]).reshape(ns, 4, D)
+    dev = hr.field_convert(lat, hr.EVEN, G.to_gpu(a), hr.F64, prec)
+    torch.cuda.synchronize()
+    got = dev.cpu().numpy()
+    bits = lambda x: np.ascontiguousarray(x, dtype=np.float32).view(np.uint32)
+    if prec == hr.F32:
+        for g_, x in ((got.real, a.real), (got.imag, a.imag)):
+            assert np.array_equal(bits(g_), bits(OS.round_binary(x, "f32")))
+        want = OS.round_complex(a, "f32")
+    else:
+        rh, rl = OS.split_df64(a.real)
+        ih, il = OS.split_df64(a.imag)
+        assert np.array_equal(bits(got), bits(np.stack([rh, rl, ih, il], -1)))
+        want = (rh + rl) + 1j * (ih + il)
+    back = hr.field_convert(lat, hr.EVEN, dev, prec, hr.F64, dst=torch.empty_like(G.to_gpu(a)))
+    back = np.ascontiguousarray(back.cpu().numpy())
+    assert np.array_equal(back.view(np.uint64), np.ascontiguousarray(want, dtype=np.complex128).view(np.uint64))
+
+
 @pytest.mark.parametrize("mode", [0, 1], ids=["stored", "rebuild"])
 def test_asym_real_equivalent_to_asym(hr, oracle_mod, mode):
     """The library's SU(4) 2AS operator in the real basis (real links, 144 B per
