@@ -117,31 +117,42 @@ __global__ void __launch_bounds__(128) represent_kernel(const double2 *__restric
     };
     bool any_rep = false;
     static_for<0, HR_NPREC>([&](auto PP) { any_rep |= of.rep[decltype(PP)::value] != nullptr; });
-    // every entry is formed once, in FP64, and written at once to the forward
-    // and backward records of each precision present; entry indices and
-    // precisions are compile-time constants, so nothing leaves the registers
-    static_for<0, D>([&](auto RR) {
-        constexpr int r = decltype(RR)::value;
-        static_for<0, D>([&](auto QQ) {
-            constexpr int q = decltype(QQ)::value;
-            if (!any_rep) return;
-            cx<double> v;
-            if constexpr (REP == HR_FUND)
-                v = sg(uld(r, q));
-            else
-                v = sg(rep_entry<N, REP, r, q>(U));
-            static_for<0, HR_NPREC>([&](auto PP) {
-                constexpr int P = decltype(PP)::value;
-                if (!of.rep[P]) return;
-                constexpr int RS = link_row_stride(N, REP, P);
+    // every entry is formed once, in FP64, a row at a time, and the row is
+    // written to the forward and backward records of each precision present.
+    // The loop over rows is rolled: its body (one row, the stores of all
+    // precisions) fits the instruction caches, which the fully unrolled D x D
+    // entries with every precision's stores interleaved did not.
+    auto put_row = [&](int r, const cx<double> (&e)[D]) {
+        static_for<0, HR_NPREC>([&](auto PP) {
+            constexpr int P = decltype(PP)::value;
+            if (!of.rep[P]) return;
+            constexpr int RS = link_row_stride(N, REP, P);
+            char *fw = reinterpret_cast<char *>(of.rep[P]);
+            char *bw = reinterpret_cast<char *>(ob.rep[P]);
+            static_for<0, D>([&](auto QQ) {
+                constexpr int q = decltype(QQ)::value;
                 // the dagger: entry (q, r) of the backward slot
-                store_pair<P, REAL>(reinterpret_cast<char *>(of.rep[P]) +
-                                        link_offset(P, REAL, D * RS, tile, mu, lane, r * RS + q),
-                                    reinterpret_cast<char *>(ob.rep[P]) +
-                                        link_offset(P, REAL, D * RS, tb, 4 + mu, lb, q * RS + r), v);
+                store_pair<P, REAL>(fw + link_offset(P, REAL, D * RS, tile, mu, lane, r * RS + q),
+                                    bw + link_offset(P, REAL, D * RS, tb, 4 + mu, lb, q * RS + r), sg(e[q]));
             });
         });
-    });
+    };
+    if (any_rep) {
+        constexpr int NROLL = REP == HR_ADJ ? noff(N) : D;
+#pragma unroll 1
+        for (int r = 0; r < NROLL; r++) {
+            cx<double> e[D];
+            rep_row<N, REP>(r, uld, e);
+            put_row(r, e);
+        }
+        if constexpr (REP == HR_ADJ)
+            static_for<noff(N), D>([&](auto RR) {
+                constexpr int r = decltype(RR)::value;
+                cx<double> e[D];
+                static_for<0, D>([&](auto QQ) { e[decltype(QQ)::value] = rep_entry<N, REP, r, decltype(QQ)::value>(U); });
+                put_row(r, e);
+            });
+    }
     static_for<0, HR_NPREC>([&](auto PP) {
         constexpr int P = decltype(PP)::value;
         if (!of.fund[P]) return;
@@ -296,15 +307,19 @@ __device__ __forceinline__ df pair_sum(df v)
 {
     return v + df(__shfl_xor_sync(0xffffffffu, v.hi, 1), __shfl_xor_sync(0xffffffffu, v.lo, 1));
 }
+// ... and over the two pairs of a group of four lanes
+__device__ __forceinline__ df quad_sum(df v)
+{
+    return v + df(__shfl_xor_sync(0xffffffffu, v.hi, 2), __shfl_xor_sync(0xffffffffu, v.lo, 2));
+}
 __device__ __forceinline__ double to_double(double v) { return v; }
 __device__ __forceinline__ double to_double(df v) { return (double)v; }
 
-// LP = HR_F64: FP64 arithmetic on the FP64 links; LP = HR_DF64: float-float
-// arithmetic on the DF64 links (the FP64 spinors are projected in FP64 and
-// split into float-float pairs once; the FP32 units do the rest).
-template <int N, int REP, int LP>
+// FP64 arithmetic on the FP64 links, two threads per link
+template <int N, int REP>
 __global__ void __launch_bounds__(128) force_kernel(const ForceParams fp)
 {
+    constexpr int LP = HR_F64;
     constexpr int D = rep_dim(N, REP);
     constexpr int NG = N * N - 1;
     constexpr bool REAL = rep_real(REP);
@@ -347,19 +362,21 @@ __global__ void __launch_bounds__(128) force_kernel(const ForceParams fp)
         const long tile = i / HR_TILE;
         const int lane = (int)(i % HR_TILE);
         const uint4 *lp = LIO::slot_ptr(fp.links, tile, mu, lane);
+        auto link = [&](int a, int b) {
+            const int cc = a * RS + b;
+            const uint4 ch = __ldg(lp + (size_t)(cc / LIO::VPC) * HR_TILE);
+            if constexpr (REAL)
+                return cx<R>{LIO::runpack(ch, cc % LIO::VPC), R(0)};
+            else
+                return LIO::cunpack(ch, 0);
+        };
         cx<R> u[D], v[D];
 #pragma unroll
         for (int a = 0; a < D; a++) {
             cx<R> su = {R(0), R(0)}, sv = {R(0), R(0)};
 #pragma unroll
             for (int b = 0; b < D; b++) {
-                const int cc = a * RS + b;
-                const uint4 ch = __ldg(lp + (size_t)(cc / LIO::VPC) * HR_TILE);
-                cx<R> uab;
-                if constexpr (REAL)
-                    uab = {LIO::runpack(ch, cc % LIO::VPC), R(0)};
-                else
-                    uab = LIO::cunpack(ch, 0);
+                const cx<R> uab = link(a, b);
                 cmac(su, uab, hX[b]);
                 cmac(sv, uab, hY[b]);
             }
@@ -393,16 +410,116 @@ __global__ void __launch_bounds__(128) force_kernel(const ForceParams fp)
     });
 }
 
+// Float-float arithmetic on the DF64 links, four threads per link: thread
+// (r, k) forms one term of K_r -- k = 0: +(U hX_r) z_r^dag, k = 1: -w_r (U
+// hY_r)^dag -- so that a thread runs one matrix-vector product and one
+// pullback (float-float code is about three times the FP64 code; with both
+// terms in one thread the warps waited on instruction fetch).  The FP64
+// spinors are projected in FP64 and split into float-float pairs; the four
+// partial P are summed with shuffles.
+template <int N, int REP>
+__global__ void __launch_bounds__(128) force_df64_kernel(const ForceParams fp)
+{
+    constexpr int D = rep_dim(N, REP);
+    constexpr int NG = N * N - 1;
+    constexpr bool REAL = rep_real(REP);
+    using R = df;
+    using SIO = SpinorIO<HR_F64, D>;
+    constexpr int RS = link_row_stride(N, REP, HR_DF64);
+    using LIO = LinkIO<HR_DF64, REAL, D * RS>;
+    const Geom &g = fp.g;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = (int)(t & 1), r = (int)((t >> 1) & 1);
+    const long link = t >> 2;
+    const long i = link >> 2;
+    const int mu = (int)(link & 3);
+    const bool active = i < g.vh;   // the four lanes of a link agree
+    cx<R> P[N][N];
+#pragma unroll
+    for (int a = 0; a < N; a++)
+#pragma unroll
+        for (int b = 0; b < N; b++) P[a][b] = {R(0), R(0)};
+    if (active) {
+        Site s = site_of(g, i, fp.parity);
+        const long nb = neighbour(g, s, mu, +1);
+        const int q = 2 + eperm(mu, r), ph = ephase(mu, r);
+        // k = 0: h = hX = upper[(1 - g) X(x+mu)], o = z = upper[(1 - g) Y(x)]
+        // k = 1: h = hY = upper[(1 + g) Y(x+mu)], o = w = upper[(1 + g) X(x)]
+        const FieldView &fh = k ? fp.Y_nb : fp.X_nb;
+        const FieldView &fo = k ? fp.X_here : fp.Y_here;
+        // the sign -1 (k = 0) as a flip of the sign bits of i^ph psi_q
+        const unsigned flip = k ? 0u : 0x80000000u;
+        auto ld = [&](const FieldView &f, long site, int sp, int c, unsigned fl) {
+            const uint4 v = __ldg(SIO::site_ptr(f, 0, site) + (sp * D + c));
+            return cx<double>{__hiloint2double((int)(v.y ^ fl), (int)v.x), __hiloint2double((int)(v.w ^ fl), (int)v.z)};
+        };
+        auto cv = [](cx<double> v) { return cx<R>{R(v.re), R(v.im)}; };
+        cx<R> h[D], o[D];
+#pragma unroll
+        for (int c = 0; c < D; c++) {
+            h[c] = cv(ld(fh, nb, r, c, 0u) + ipow(ph, ld(fh, nb, q, c, flip)));
+            o[c] = cv(ld(fo, i, r, c, 0u) + ipow(ph, ld(fo, i, q, c, flip)));
+        }
+        const long tile = i / HR_TILE;
+        const int lane = (int)(i % HR_TILE);
+        const uint4 *lp = LIO::slot_ptr(fp.links, tile, mu, lane);
+        cx<R> m[D];
+#pragma unroll
+        for (int a = 0; a < D; a++) {
+            cx<R> sm = {R(0), R(0)};
+#pragma unroll
+            for (int b = 0; b < D; b++) {
+                const int cc = a * RS + b;
+                const uint4 ch = __ldg(lp + (size_t)(cc / LIO::VPC) * HR_TILE);
+                cx<R> uab;
+                if constexpr (REAL)
+                    uab = {LIO::runpack(ch, cc % LIO::VPC), R(0)};
+                else
+                    uab = LIO::cunpack(ch, 0);
+                cmac(sm, uab, h[b]);
+            }
+            m[a] = sm;
+        }
+        if (k == 0)
+            pullback_add<N, REP>(P, 1.0, m, o);
+        else
+            pullback_add<N, REP>(P, -1.0, o, m);
+    }
+#pragma unroll
+    for (int a = 0; a < N; a++)
+#pragma unroll
+        for (int b = 0; b < N; b++) {
+            P[a][b].re = pair_sum(P[a][b].re);
+            P[a][b].im = pair_sum(P[a][b].im);
+            P[a][b].re = quad_sum(P[a][b].re);
+            P[a][b].im = quad_sum(P[a][b].im);
+        }
+    if (!active || (t & 3) != 0) return;
+    const long lex = lex_of(g, site_of(g, i, fp.parity));
+    double *Fo = fp.F + ((size_t)lex * 4 + mu) * NG;
+    static_for<0, NG>([&](auto AA) {
+        constexpr int a = decltype(AA)::value;
+        cx<R> tr = {R(0), R(0)};
+        static_for<0, gen_nent(N, a)>([&](auto EE) {
+            constexpr int e = decltype(EE)::value;
+            cmac(tr, gen_val<R>(N, a, e), P[gen_col(N, a, e)][gen_row(N, a, e)]);
+        });
+        Fo[a] += -fp.coeff * to_double(tr.im);
+    });
+}
+
 template <int N, int REP>
 hr_status force_launch(const ForceParams &fp, cudaStream_t stream)
 {
-    const long threads = fp.g.vh * 8;   // two threads per link
-    const unsigned blocks = (unsigned)((threads + 127) / 128);
-    if (fp.arith == HR_DF64)
-        force_kernel<N, REP, HR_DF64><<<blocks, 128, 0, stream>>>(fp);
-    else
-        force_kernel<N, REP, HR_F64><<<blocks, 128, 0, stream>>>(fp);
-    HR_LAUNCH_CHECK("force_kernel");
+    if (fp.arith == HR_DF64) {
+        const long threads = fp.g.vh * 16;   // four threads per link
+        force_df64_kernel<N, REP><<<(unsigned)((threads + 127) / 128), 128, 0, stream>>>(fp);
+        HR_LAUNCH_CHECK("force_df64_kernel");
+    } else {
+        const long threads = fp.g.vh * 8;    // two threads per link
+        force_kernel<N, REP><<<(unsigned)((threads + 127) / 128), 128, 0, stream>>>(fp);
+        HR_LAUNCH_CHECK("force_kernel");
+    }
     return HR_OK;
 }
 

@@ -268,6 +268,110 @@ __host__ __device__ __forceinline__ cx<double> rep_entry(const cx<double> (&U)[N
     }
 }
 
+// --- row n of R(U), n known only at run time (the represent kernel's rolled
+// row loop, whose body stays small enough for the instruction caches); the
+// column indices are compile-time constants and ld(i, k) returns U_ik.  The
+// sums are those of rep_entry.  For ADJ only the rows of the off-diagonal
+// generators (n < N(N-1)) are formed here; rep_entry gives the diagonal ones. ---
+template <int N, int REP, class LD>
+__host__ __device__ __forceinline__ void rep_row(int n, LD &&ld, cx<double> (&e)[rep_dim(N, REP)])
+{
+    constexpr int D = rep_dim(N, REP);
+    if constexpr (REP == HR_FUND) {
+        static_for<0, N>([&](auto K) { e[decltype(K)::value] = ld(n, decltype(K)::value); });
+    } else if constexpr (REP == HR_SYM || REP == HR_ASYM) {
+        const int i = sb_i(N, REP, n), j = sb_j(N, REP, n);
+        cx<double> ui[N], uj[N];
+        static_for<0, N>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            ui[k] = ld(i, k);
+            uj[k] = ld(j, k);
+        });
+        if (REP == HR_SYM && i == j) {
+            static_for<0, D>([&](auto M) {
+                constexpr int m = decltype(M)::value, k = sb_i(N, REP, m), l = sb_j(N, REP, m);
+                if constexpr (k == l) {
+                    e[m] = ui[k] * ui[k];
+                } else {
+                    const cx<double> pr = ui[k] * ui[l];
+                    e[m] = {HR_SQRT2 * pr.re, HR_SQRT2 * pr.im};
+                }
+            });
+        } else {
+            static_for<0, D>([&](auto M) {
+                constexpr int m = decltype(M)::value, k = sb_i(N, REP, m), l = sb_j(N, REP, m);
+                if constexpr (REP == HR_ASYM) {
+                    e[m] = cx_pair(ui[k], uj[l], -1.0, ui[l], uj[k]);
+                } else if constexpr (k == l) {
+                    const cx<double> pr = ui[k] * uj[k];
+                    e[m] = {HR_SQRT2 * pr.re, HR_SQRT2 * pr.im};
+                } else {
+                    e[m] = cx_pair(ui[k], uj[l], 1.0, ui[l], uj[k]);
+                }
+            });
+        }
+    } else if constexpr (REP == HR_ASYM_REAL) {
+        const int kn = n >> 1;
+        const double sn = ((n & 1) ? -1.0 : 1.0) * (kn == 1 ? -1.0 : 1.0);
+        cx<double> up0[N], up1[N], uq0[N], uq1[N];
+        const int p0 = rb_p(kn, 0), p1 = rb_p(kn, 1), q0 = rb_q(kn, 0), q1 = rb_q(kn, 1);
+        static_for<0, N>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            up0[k] = ld(p0, k);
+            up1[k] = ld(p1, k);
+            uq0[k] = ld(q0, k);
+            uq1[k] = ld(q1, k);
+        });
+        static_for<0, D>([&](auto M) {
+            constexpr int m = decltype(M)::value, km = m / 2;
+            constexpr double sm = rb_val(m, 2) * 2.0;
+            constexpr int r0 = rb_p(km, 0), r1 = rb_p(km, 1), t0 = rb_q(km, 0), t1 = rb_q(km, 1);
+            const cx<double> m1 = cx_pair(up0[r0], up1[r1], -1.0, up0[r1], up1[r0]);
+            const cx<double> m2 = cx_pair(up0[t0], up1[t1], -1.0, up0[t1], up1[t0]);
+            const cx<double> m3 = cx_pair(uq0[r0], uq1[r1], -1.0, uq0[r1], uq1[r0]);
+            const cx<double> m4 = cx_pair(uq0[t0], uq1[t1], -1.0, uq0[t1], uq1[t0]);
+            const cx<double> sv = {0.5 * ((m1.re + sm * m2.re) + sn * (m3.re + sm * m4.re)),
+                                   0.5 * ((m1.im + sm * m2.im) + sn * (m3.im + sm * m4.im))};
+            e[m] = rb_cc(n, rb_c(m, sv));
+        });
+    } else {
+        // ADJ, off-diagonal generator on the pair (p, q), symmetric or antisymmetric
+        const int p = pair_j(N, n >> 1), q = pair_k(N, n >> 1);
+        const bool anti = n & 1;
+        cx<double> up[N], uq[N];
+        static_for<0, N>([&](auto K) {
+            constexpr int k = decltype(K)::value;
+            up[k] = ld(p, k);
+            uq[k] = ld(q, k);
+        });
+        constexpr int NO = noff(N);
+        static_for<0, D>([&](auto B) {
+            constexpr int b = decltype(B)::value;
+            if constexpr (b < NO) {
+                constexpr int r = pair_j(N, b / 2), t = pair_k(N, b / 2);
+                const cx<double> z1 = uq[r] * conj(up[t]), z2 = uq[t] * conj(up[r]);
+                double v;
+                if constexpr (!(b & 1))
+                    v = anti ? z1.im + z2.im : z1.re + z2.re;
+                else
+                    v = anti ? z2.re - z1.re : z1.im - z2.im;
+                e[b] = {v, 0.0};
+            } else {
+                constexpr int l = b - NO + 1;
+                double are = 0.0, aim = 0.0;
+                static_for<0, l + 1>([&](auto FF) {
+                    constexpr int f = decltype(FF)::value;
+                    const double bf = gen_val<double>(N, b, f).re;
+                    const cx<double> y = uq[f] * conj(up[f]);
+                    are = fma(bf, y.re, are);
+                    aim = fma(bf, y.im, aim);
+                });
+                e[b] = {2.0 * (anti ? aim : are), 0.0};
+            }
+        });
+    }
+}
+
 // --- action of R(F) on a colour vector without forming R(F) (in-kernel
 // rebuild): vector -> matrix, conjugate by F, matrix -> vector.  All basis
 // indices are compile-time constants (static_for), so X, Z stay in registers.
