@@ -29,6 +29,12 @@ __device__ __forceinline__ uint64_t policy_evict_first()
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
     return pol;
 }
+// bring `bytes` contiguous bytes at src into L2 (bulk prefetch, no
+// completion to wait for); src and bytes multiples of 16
+__device__ __forceinline__ void prefetch_l2_bulk(const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 // close the group of copies issued since the last commit (an empty group is allowed)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 // wait until at most N of this thread's committed groups are still in flight

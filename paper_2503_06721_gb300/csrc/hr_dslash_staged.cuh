@@ -209,6 +209,19 @@ __global__ void __launch_bounds__(128, MINB) hop_staged_kernel(const HopParams p
         return kk < 8 ? (int)neighbour(g, st, kk & 3, kk < 4 ? +1 : -1) : (int)ie;
     };
     const char *diag_base = prm.diag.data ? prm.diag.data + (size_t)rhs * prm.diag.rhs_stride : nullptr;
+    if constexpr (EPI == EPI_CG_UPDATE) {
+        // the fused update reads the warp's own r, x and p records only after
+        // the eight hops: start bringing them into L2 now (the warp's 32
+        // sites are contiguous records), so that the epilogue's gathers do not
+        // wait on DRAM
+        if (lane == 0 && wfirst < g.vh) {
+            const long nw = min((long)HR_TILE, g.vh - wfirst);
+            constexpr uint32_t RC = 16u * Sh::NCC, RP = 16u * NC;
+            prefetch_l2_bulk(prm.r.data + (size_t)rhs * prm.r.rhs_stride + (size_t)wfirst * RC, (uint32_t)nw * RC);
+            prefetch_l2_bulk(prm.x.data + (size_t)rhs * prm.x.rhs_stride + (size_t)wfirst * RC, (uint32_t)nw * RC);
+            prefetch_l2_bulk(prm.p.data + (size_t)rhs * prm.p.rhs_stride + (size_t)wfirst * RP, (uint32_t)nw * RP);
+        }
+    }
     // gathers 0 .. NST-2 in flight before the first hop
     R scale_q[NST];
 #pragma unroll
