@@ -524,7 +524,7 @@ hr_status hr_dirac_force(const hr_gauge *g, hr_parity sys, const void *X,
  *                    projected in FP64 and split into float-float pairs, the
  *                    matrix products run on the FP32 units, and F (FP64) is
  *                    accumulated in FP64.  Each component agrees with the
- *                    FP64 force to about 1e-13 of max |F|.
+ *                    FP64 force to about 1e-14 of max |F|.
  * The hops that form D_oe X and (D^dag)_oe Y for sys = HR_EO_PRECOND are
  * FP64 in both cases.  HR_ERR_INVALID for another arith or missing links. */
 hr_status hr_dirac_force_prec(const hr_gauge *g, hr_parity sys, const void *X,
