@@ -84,8 +84,10 @@ typedef enum {
  *   HR_LINKS_REBUILD  read the N x N fundamental links and rebuild the action
  *                     of U_R inside the kernel (fewer bytes, more flops)
  *   HR_LINKS_AUTO     per precision, whichever of the two hr_tune measured
- *                     faster on the handle's lattice (STORED until tuned);
- *                     needs both storages (hr_gauge_set_link_mode only) */
+ *                     faster on the handle's lattice (STORED until tuned;
+ *                     always STORED for F16 and BF16, whose rebuilt links
+ *                     carry about twice the rounding error of the stored
+ *                     ones); needs both storages (hr_gauge_set_link_mode only) */
 typedef enum { HR_LINKS_STORED = 0, HR_LINKS_REBUILD = 1, HR_LINKS_AUTO = 2 } hr_link_mode;
 
 typedef struct {

@@ -46,7 +46,13 @@ static hr_status tune_mode(hr_gauge *g, int P, int nrhs, cudaStream_t s, float *
 
 hr_status tune_hops(hr_gauge *g, int P, int nrhs, cudaStream_t s)
 {
-    const bool both = g->mode == HR_LINKS_AUTO && g->rep[P][0] && g->fund[P][0];
+    // the 16-bit precisions keep their stored links: rebuilt from 16-bit
+    // fundamental entries, U_R carries about twice their rounding error, and
+    // the inner solves then took more iterations and an extra FP64 correction
+    // although each launch was as fast (SU(3) sextet 32^3x64, F16 inner, to
+    // 1e-10: 62 iterations, 4 outer steps, 184 ms against 58, 3, 156 ms)
+    const bool half = P == HR_F16 || P == HR_BF16;
+    const bool both = g->mode == HR_LINKS_AUTO && g->rep[P][0] && g->fund[P][0] && !half;
     if (!both) {
         if (g->mode == HR_LINKS_AUTO) g->auto_mode[P] = g->rep[P][0] ? HR_LINKS_STORED : HR_LINKS_REBUILD;
         if (hop_variants_of(g, P) == 0x1u) return HR_OK;

@@ -133,13 +133,17 @@ def test_tuning_arguments_checked(hr):
 
 def test_auto_link_mode(hr, oracle_mod):
     """LINKS_AUTO: the tuner keeps, per precision, the faster of stored and
-    rebuilt links; solves in that mode still meet their tolerance, and the
-    mode needs both storages."""
+    rebuilt links (the 16-bit precisions always their stored links); solves
+    in that mode still meet their tolerance, and the mode needs both
+    storages."""
     lat, g = _gauge(hr, 3, "SYM", dims=(8, 8, 8, 8), rebuild=True)
     g.set_link_mode(hr.LINKS_AUTO)
     assert g.link_mode(hr.F32) == hr.LINKS_STORED   # until tuned
     g.tune(hr.F32)
     assert g.link_mode(hr.F32) in (hr.LINKS_STORED, hr.LINKS_REBUILD)
+    for half in (hr.F16, hr.BF16):
+        g.tune(half)
+        assert g.link_mode(half) == hr.LINKS_STORED
     b = H.spinor(lat.volume // 2, lat.D, 12)
     x, res, st = g.cg_solve(hr.EO_PRECOND, G.to_gpu(b), tol=1e-10, inner=hr.F32, inner_tol=1e-4)
     assert st == 0 and res[0]["true_rel_residual"] <= 1e-10
