@@ -111,12 +111,6 @@ __device__ __forceinline__ size_t cl_index(long ntiles, int E, int kind, int par
     return (((((size_t)kind * 2 + parity) * ntiles + tile) * 2 + blk) * E + e) * HR_TILE + lane;
 }
 
-__device__ __forceinline__ cx<double> cdiv(cx<double> a, cx<double> b)
-{
-    const double n = b.re * b.re + b.im * b.im;
-    return {(a.re * b.re + a.im * b.im) / n, (a.im * b.re - a.re * b.im) / n};
-}
-
 // one thread block per site x
 template <int N, int REP>
 __global__ void __launch_bounds__(CL_BUILD_THREADS) k_clover_build(const CloverBuildParams p)
@@ -129,6 +123,7 @@ __global__ void __launch_bounds__(CL_BUILD_THREADS) k_clover_build(const CloverB
     __shared__ cx<double> Cm[n][n];
     __shared__ cx<double> Tm[n][n];
     __shared__ int s_piv;
+    __shared__ cx<double> s_inv;
     __shared__ int s_bad;
     static_assert(sizeof(leaf) >= sizeof(cx<double>) * n * 2 * n, "augmented matrix must fit in the leaf buffer");
     cx<double>(*A)[2 * n] = reinterpret_cast<cx<double>(*)[2 * n]>(&leaf[0][0][0]);
@@ -160,7 +155,9 @@ __global__ void __launch_bounds__(CL_BUILD_THREADS) k_clover_build(const CloverB
         const int sgn[4][4] = {{1, 1, -1, -1}, {1, -1, -1, 1}, {-1, -1, 1, 1}, {-1, 1, 1, -1}};
         int q[4] = {c[0], c[1], c[2], c[3]};
         cx<double> P[N][N];
+#pragma unroll
         for (int i = 0; i < N; i++)
+#pragma unroll
             for (int j = 0; j < N; j++) P[i][j] = {i == j ? 1.0 : 0.0, 0.0};
         for (int st = 0; st < 4; st++) {
             const int dd = dirs[k][st], s = sgn[k][st];
@@ -169,23 +166,31 @@ __global__ void __launch_bounds__(CL_BUILD_THREADS) k_clover_build(const CloverB
             if (s < 0) from[dd] = (from[dd] - 1 + p.d[dd]) % p.d[dd];
             const cx<double> *u = p.U + ((size_t)lex(from) * 4 + dd) * N * N;
             cx<double> T[N][N];
+#pragma unroll
             for (int i = 0; i < N; i++)
+#pragma unroll
                 for (int j = 0; j < N; j++) {
                     cx<double> acc = {0, 0};
+#pragma unroll
                     for (int l = 0; l < N; l++) {
                         const cx<double> m = s > 0 ? u[l * N + j] : conj(u[j * N + l]);
                         cmac(acc, P[i][l], m);
                     }
                     T[i][j] = acc;
                 }
+#pragma unroll
             for (int i = 0; i < N; i++)
+#pragma unroll
                 for (int j = 0; j < N; j++) P[i][j] = T[i][j];
             q[dd] = s > 0 ? (q[dd] + 1) % p.d[dd] : from[dd];
         }
-        cx<double> R[D][D];
-        represent<N, REP>(P, R);
-        for (int i = 0; i < D; i++)
-            for (int j = 0; j < D; j++) leaf[tid][i][j] = R[i][j];
+        // R(leaf) entry by entry with the folded sums (compile-time indices)
+        static_for<0, D>([&](auto AA) {
+            static_for<0, D>([&](auto BB) {
+                leaf[tid][decltype(AA)::value][decltype(BB)::value] =
+                    rep_entry<N, REP, decltype(AA)::value, decltype(BB)::value>(P);
+            });
+        });
     }
     __syncthreads();
     // ---- F_mu_nu = (Q - Q^dag) / 8 ----
@@ -295,6 +300,10 @@ __global__ void __launch_bounds__(CL_BUILD_THREADS) k_clover_build(const CloverB
                 }
                 if (!(best > 0) || !isfinite(best)) s_bad = 1;
                 s_piv = piv;
+                // the pivot's reciprocal, one division per pivot
+                const cx<double> pv = A[piv][k];
+                const double in2 = 1.0 / (pv.re * pv.re + pv.im * pv.im);
+                s_inv = {pv.re * in2, -pv.im * in2};
             }
             __syncthreads();
             const int piv = s_piv;
@@ -305,15 +314,17 @@ __global__ void __launch_bounds__(CL_BUILD_THREADS) k_clover_build(const CloverB
                     A[piv][j] = t;
                 }
             __syncthreads();
-            const cx<double> pv = A[k][k];
-            __syncthreads();
-            for (int j = tid; j < 2 * n; j += blockDim.x) A[k][j] = cdiv(A[k][j], pv);
+            // the columns j < k of the left half are already unit columns, so
+            // row k is zero there: only the columns k .. 2n-1 change
+            const cx<double> inv = s_inv;
+            const int w = 2 * n - k;
+            for (int j = k + tid; j < 2 * n; j += blockDim.x) A[k][j] = A[k][j] * inv;
             __syncthreads();
             // factors of the other rows, taken before their column k changes
             for (int i = tid; i < n; i += blockDim.x) Tm[0][i] = i == k ? cx<double>{0, 0} : A[i][k];
             __syncthreads();
-            for (int t = tid; t < n * 2 * n; t += blockDim.x) {
-                const int i = t / (2 * n), j = t % (2 * n);
+            for (int t = tid; t < n * w; t += blockDim.x) {
+                const int i = t / w, j = k + t % w;
                 if (i == k) continue;
                 const cx<double> f = Tm[0][i];
                 A[i][j] = A[i][j] - f * A[k][j];
