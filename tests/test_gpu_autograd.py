@@ -79,7 +79,8 @@ def test_action_gradient_vs_oracle_force(hr, oracle_mod):
     # grad_phi = 2 A^{-1} phi (PyTorch convention for a real loss)
     np.testing.assert_allclose(G.from_eo_full(oracle_mod, L, gphi.cpu().numpy()), 2 * X,
                                atol=1e-9 * np.abs(X).max())
-    assert abs(float(S) - np.vdot(phi.ravel(), X.ravel()).real) < 1e-10 * abs(float(S))
+    s_val = float(S.detach())
+    assert abs(s_val - np.vdot(phi.ravel(), X.ravel()).real) < 1e-10 * abs(s_val)
 
 
 def test_dirac_and_solve_backward(hr, oracle_mod):
