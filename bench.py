@@ -444,7 +444,9 @@ def run_ours(args, rank, world, local_rank):
             "data": "synthetic (seeded Philox4x32-10 links exp(i 0.4 H) + Haar gauge transform, "
                     "Gaussian pseudofermion)",
             "config": {"workload": WORKLOAD_TEXT,
-                       "true_residual_arith": args.residual,
+                       "true_residual_arith": ("float-float intermediate, FP64 final (the reported residual)"
+                                               if res_prec == hr.DF64 else "FP64"),
+                       "force_arith": "float-float" if res_prec == hr.DF64 else "FP64",
                        "lattice": list(wl.dims), "N": wl.N, "rep": wl.rep, "m0": wl.m0,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (FP32 links 4.8 GB per parity)",
