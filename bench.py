@@ -1020,6 +1020,33 @@ def run_force(args, local_rank):
                       "note": "two force_kernel launches (one per parity) and two FP64 odd-half hops per call"}))
 
 
+def run_clover(args, local_rank):
+    """Clover build only (for profiler captures): W untimed and K timed
+    builds of C and C^-1 (FP64 and FP32 records) with c_sw = 1."""
+    import torch
+    from paper_2503_06721_gb300 import build, hr, synth
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    build.build()
+    wl = synth.WORKLOADS[args.workload]
+    lat = hr.Lattice(wl.N, wl.rep, wl.dims, wl.bc, wl.m0)
+    U = wl.links(device=dev)
+    g = hr.Gauge(lat, U, precs=("f64", "f32"))
+    for _ in range(max(args.warmup, 1)):
+        g.set_clover(U, csw=1.0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("hr_clover")
+    e0.record()
+    for _ in range(args.steps):
+        g.set_clover(U, csw=1.0)
+    e1.record()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "clover", "workload": args.workload,
+                      "ms_per_build": round(e0.elapsed_time(e1) / args.steps, 3)}))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -1040,8 +1067,9 @@ def main():
     ap.add_argument("--no-multishift", action="store_true",
                     help="skip the multi-shift-vs-sequential shifted solve comparison")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--mode", choices=["step", "deo", "force"], default="step",
-                    help="deo: only D_eo applications; force: only the fermion force (profiler captures)")
+    ap.add_argument("--mode", choices=["step", "deo", "force", "clover"], default="step",
+                    help="deo: only D_eo applications; force: only the fermion force; clover: only the "
+                         "clover build (profiler captures)")
     ap.add_argument("--prec", choices=["f64", "f32", "f16", "bf16", "df64"], default="f32")
     ap.add_argument("--residual", choices=["df64", "f64"], default="df64",
                     help="arithmetic of the defect-correction true residuals (df64: float-float, "
@@ -1066,6 +1094,8 @@ def main():
         run_deo(args, local_rank)
     elif args.mode == "force":
         run_force(args, local_rank)
+    elif args.mode == "clover":
+        run_clover(args, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 
