@@ -90,7 +90,9 @@ __host__ __device__ __forceinline__ cx<R> rb_c(int n, cx<R> v) { return (n & 1) 
 template <class R>
 __host__ __device__ __forceinline__ cx<R> rb_cc(int n, cx<R> v) { return (n & 1) ? cx<R>{v.im, -v.re} : v; }
 
-// --- R(U) as a dense D x D matrix (FP64), U given as N x N ---
+// --- R(U) as a dense D x D matrix (FP64), U given as N x N: the plain sums
+// over the basis elements, the definition that the folded per-entry and
+// per-row formulas below are checked against (tests/host/host_checks.cu) ---
 template <int N, int REP>
 __host__ __device__ inline void represent(const cx<double> (&U)[N][N], cx<double> (&Rm)[rep_dim(N, REP)][rep_dim(N, REP)])
 {
